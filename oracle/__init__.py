@@ -1,0 +1,143 @@
+"""CPU oracle for the single-device sort -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg may
+import this package.  It shares no code with the CUDA library, and the library
+never calls it.
+
+``ak_oracle.c`` is a plain top-down stable merge sort under Julia ``isless`` (the
+sort, sortperm and by-key sort of Sec. II-B, used as the rank-local sort of the
+sample sort in Sec. III-A).  ``learned.py`` restates the learned-CDF model in
+float64 numpy.  This module compiles the C file with gcc on first use and wraps
+it with ctypes over numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ak_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# dtype codes of ak_oracle.c
+_DTYPE_CODE = {
+    np.dtype(np.uint16): 0, np.dtype(np.int16): 1, np.dtype(np.uint32): 2,
+    np.dtype(np.int32): 3, np.dtype(np.uint64): 4, np.dtype(np.int64): 5,
+    np.dtype(np.float32): 6, np.dtype(np.float64): 7,
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (portable C, no -march flags)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            lib.oracle_sortperm.argtypes = [p, i64, i32, i32, p]
+            lib.oracle_sortperm_threaded.argtypes = [p, i64, i32, i32, p, i32]
+            lib.oracle_sortperm_segmented.argtypes = [p, p, i64, i64, i32, i32, p]
+            lib.oracle_gather.argtypes = [p, p, i64, i32, p]
+            lib.oracle_isless_pairs.argtypes = [p, p, i64, i32, p]
+            for f in (lib.oracle_sortperm, lib.oracle_sortperm_threaded,
+                      lib.oracle_sortperm_segmented, lib.oracle_gather,
+                      lib.oracle_isless_pairs):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _code(a: np.ndarray) -> int:
+    try:
+        return _DTYPE_CODE[a.dtype]
+    except KeyError:
+        raise TypeError(f"oracle: unsupported key dtype {a.dtype}") from None
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _desc(order) -> int:
+    if order in ("ascending", "asc", 0, False):
+        return 0
+    if order in ("descending", "desc", 1, True):
+        return 1
+    raise ValueError(order)
+
+
+def sortperm(keys: np.ndarray, order="ascending", threads: int = 1) -> np.ndarray:
+    """Stable sorting permutation (int64, 0-based)."""
+    k = np.ascontiguousarray(keys)
+    perm = np.empty(k.size, dtype=np.int64)
+    lib = _load()
+    if threads > 1:
+        rc = lib.oracle_sortperm_threaded(_ptr(k), k.size, _code(k), _desc(order), _ptr(perm), threads)
+    else:
+        rc = lib.oracle_sortperm(_ptr(k), k.size, _code(k), _desc(order), _ptr(perm))
+    if rc:
+        raise RuntimeError(f"oracle_sortperm failed ({rc})")
+    return perm
+
+
+def gather(src: np.ndarray, perm: np.ndarray) -> np.ndarray:
+    """src[perm], moving raw bits."""
+    s = np.ascontiguousarray(src)
+    p = np.ascontiguousarray(perm, dtype=np.int64)
+    out = np.empty(p.size, dtype=s.dtype)
+    if _load().oracle_gather(_ptr(s), _ptr(p), p.size, s.dtype.itemsize, _ptr(out)):
+        raise RuntimeError("oracle_gather failed")
+    return out
+
+
+def sort(keys: np.ndarray, order="ascending", threads: int = 1) -> np.ndarray:
+    return gather(keys, sortperm(keys, order, threads))
+
+
+def sort_pairs(keys: np.ndarray, vals: np.ndarray, order="ascending", threads: int = 1):
+    p = sortperm(keys, order, threads)
+    return gather(keys, p), gather(vals, p)
+
+
+def sortperm_segmented(keys: np.ndarray, offsets: np.ndarray, order="ascending") -> np.ndarray:
+    """Global-index permutation sorting each CSR segment on its own."""
+    k = np.ascontiguousarray(keys)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    perm = np.empty(k.size, dtype=np.int64)
+    rc = _load().oracle_sortperm_segmented(_ptr(k), _ptr(off), off.size - 1, k.size, _code(k),
+                                           _desc(order), _ptr(perm))
+    if rc:
+        raise RuntimeError(f"oracle_sortperm_segmented failed ({rc})")
+    return perm
+
+
+def sort_segmented(keys: np.ndarray, offsets: np.ndarray, order="ascending") -> np.ndarray:
+    return gather(keys, sortperm_segmented(keys, offsets, order))
+
+
+def isless(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Elementwise Julia isless(a[i], b[i]) as computed by the oracle."""
+    a = np.ascontiguousarray(a)
+    b = np.ascontiguousarray(b, dtype=a.dtype)
+    out = np.empty(a.size, dtype=np.uint8)
+    if _load().oracle_isless_pairs(_ptr(a), _ptr(b), a.size, _code(a), _ptr(out)):
+        raise RuntimeError("oracle_isless_pairs failed")
+    return out.astype(bool)

@@ -1,0 +1,222 @@
+/*
+ * ak_oracle.c -- CPU oracle for the single-device sort.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the bench's CPU
+ * baseline use this file.  It shares no code, header, table or helper with the
+ * CUDA library and must never be reached from the library's product path.
+ *
+ * What it computes (the definition, written out):
+ *   For keys k[0..n) the result is the unique STABLE permutation p such that for
+ *   every i < j either lt(k[p[i]], k[p[j]]) holds, or neither lt(k[p[i]], k[p[j]])
+ *   nor lt(k[p[j]], k[p[i]]) holds and p[i] < p[j].
+ *   lt is Julia's isless for ascending order and lt(a,b) = isless(b,a) for
+ *   descending order (Julia's rev=true, which keeps equal keys in input order).
+ *   sort        -> k o p            (the local sort of Sec. III-A)
+ *   sortperm    -> p                (Sec. II-B, "sortperm")
+ *   sort_pairs  -> (k o p, v o p)   (Sec. II-B, "merge_sort_by_key")
+ *   segmented   -> the same definition applied to every CSR segment alone.
+ *
+ * Julia isless on integers is <.  On IEEE floats: every NaN compares after every
+ * non-NaN and all NaNs are equivalent; -0.0 comes before +0.0; otherwise <.
+ *
+ * How: a textbook top-down merge sort on an index array.  The merge takes the
+ * right element only when it is strictly less than the left one, so ties keep
+ * input order.  A threaded variant sorts equal chunks in parallel and merges
+ * them pairwise with the same merge.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OD_U16 = 0, OD_I16, OD_U32, OD_I32, OD_U64, OD_I64, OD_F32, OD_F64, OD_COUNT };
+
+typedef struct {
+    const void *keys;
+    int dtype;
+    int descending;
+} oracle_ctx;
+
+/* Julia isless for floats of either width. */
+static int isless_double(double a, double b) {
+    if (isnan(a)) return 0;          /* NaN is never less than anything */
+    if (isnan(b)) return 1;          /* every non-NaN is less than NaN */
+    if (a < b) return 1;
+    if (a == b) return signbit(a) && !signbit(b);   /* -0.0 before +0.0 */
+    return 0;
+}
+
+static int isless_float(float a, float b) {
+    if (isnan(a)) return 0;
+    if (isnan(b)) return 1;
+    if (a < b) return 1;
+    if (a == b) return signbit(a) && !signbit(b);
+    return 0;
+}
+
+/* isless(key[i], key[j]) */
+static int key_isless(const oracle_ctx *c, int64_t i, int64_t j) {
+    switch (c->dtype) {
+    case OD_U16: return ((const uint16_t *)c->keys)[i] < ((const uint16_t *)c->keys)[j];
+    case OD_I16: return ((const int16_t *)c->keys)[i] < ((const int16_t *)c->keys)[j];
+    case OD_U32: return ((const uint32_t *)c->keys)[i] < ((const uint32_t *)c->keys)[j];
+    case OD_I32: return ((const int32_t *)c->keys)[i] < ((const int32_t *)c->keys)[j];
+    case OD_U64: return ((const uint64_t *)c->keys)[i] < ((const uint64_t *)c->keys)[j];
+    case OD_I64: return ((const int64_t *)c->keys)[i] < ((const int64_t *)c->keys)[j];
+    case OD_F32: return isless_float(((const float *)c->keys)[i], ((const float *)c->keys)[j]);
+    case OD_F64: return isless_double(((const double *)c->keys)[i], ((const double *)c->keys)[j]);
+    }
+    return 0;
+}
+
+/* the order's strict "comes before": isless, or isless with operands swapped */
+static int lt(const oracle_ctx *c, int64_t i, int64_t j) {
+    return c->descending ? key_isless(c, j, i) : key_isless(c, i, j);
+}
+
+/* Merge idx[lo,mid) and idx[mid,hi) (each already in order) through tmp. */
+static void merge_runs(const oracle_ctx *c, int64_t *idx, int64_t *tmp,
+                       int64_t lo, int64_t mid, int64_t hi) {
+    int64_t a = lo, b = mid, o = lo;
+    while (a < mid && b < hi) {
+        if (lt(c, idx[b], idx[a])) tmp[o++] = idx[b++];   /* right strictly first */
+        else tmp[o++] = idx[a++];                         /* ties: left first */
+    }
+    while (a < mid) tmp[o++] = idx[a++];
+    while (b < hi) tmp[o++] = idx[b++];
+    memcpy(idx + lo, tmp + lo, (size_t)(hi - lo) * sizeof(int64_t));
+}
+
+static void merge_sort(const oracle_ctx *c, int64_t *idx, int64_t *tmp, int64_t lo, int64_t hi) {
+    if (hi - lo < 2) return;
+    int64_t mid = lo + (hi - lo) / 2;
+    merge_sort(c, idx, tmp, lo, mid);
+    merge_sort(c, idx, tmp, mid, hi);
+    merge_runs(c, idx, tmp, lo, mid, hi);
+}
+
+static int check_args(const void *keys, int64_t n, int dtype, const int64_t *perm) {
+    if (n < 0 || dtype < 0 || dtype >= OD_COUNT) return -1;
+    if (n > 0 && (!keys || !perm)) return -1;
+    return 0;
+}
+
+/* perm[0..n) <- the stable sorting permutation of keys (0-based). */
+int oracle_sortperm(const void *keys, int64_t n, int dtype, int descending, int64_t *perm) {
+    if (check_args(keys, n, dtype, perm)) return -1;
+    oracle_ctx c = {keys, dtype, descending};
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    if (n < 2) return 0;
+    int64_t *tmp = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!tmp) return -2;
+    merge_sort(&c, perm, tmp, 0, n);
+    free(tmp);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- threaded -- */
+typedef struct {
+    const oracle_ctx *c;
+    int64_t *idx, *tmp;
+    int64_t lo, mid, hi;
+    int merge_only;
+} oracle_job;
+
+static void *oracle_job_run(void *p) {
+    oracle_job *j = (oracle_job *)p;
+    if (j->merge_only) merge_runs(j->c, j->idx, j->tmp, j->lo, j->mid, j->hi);
+    else merge_sort(j->c, j->idx, j->tmp, j->lo, j->hi);
+    return NULL;
+}
+
+/* Same result as oracle_sortperm: `nthreads` equal chunks sorted in parallel,
+ * then merged pairwise (left run first on ties), level by level. */
+int oracle_sortperm_threaded(const void *keys, int64_t n, int dtype, int descending,
+                             int64_t *perm, int nthreads) {
+    if (check_args(keys, n, dtype, perm)) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (n < 2 * (int64_t)nthreads || nthreads == 1)
+        return oracle_sortperm(keys, n, dtype, descending, perm);
+    oracle_ctx c = {keys, dtype, descending};
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    int64_t *tmp = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!tmp) return -2;
+    int64_t bounds[257];
+    for (int t = 0; t <= nthreads; ++t) bounds[t] = n * t / nthreads;
+    pthread_t th[256];
+    oracle_job jobs[256];
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = (oracle_job){&c, perm, tmp, bounds[t], 0, bounds[t + 1], 0};
+        pthread_create(&th[t], NULL, oracle_job_run, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    /* runs are bounds[r]..bounds[r+1]; merge neighbours until one run remains */
+    int runs = nthreads;
+    int64_t rb[257];
+    memcpy(rb, bounds, sizeof(int64_t) * (size_t)(nthreads + 1));
+    while (runs > 1) {
+        int pairs = runs / 2, nj = 0;
+        for (int r = 0; r < pairs; ++r) {
+            jobs[nj] = (oracle_job){&c, perm, tmp, rb[2 * r], rb[2 * r + 1], rb[2 * r + 2], 1};
+            pthread_create(&th[nj], NULL, oracle_job_run, &jobs[nj]);
+            ++nj;
+        }
+        for (int r = 0; r < nj; ++r) pthread_join(th[r], NULL);
+        int64_t nb[257];
+        int k = 0;
+        for (int r = 0; r < pairs; ++r) nb[k++] = rb[2 * r];
+        if (runs & 1) nb[k++] = rb[runs - 1];
+        nb[k] = rb[runs];
+        runs = k;
+        memcpy(rb, nb, sizeof(int64_t) * (size_t)(runs + 1));
+    }
+    free(tmp);
+    return 0;
+}
+
+/* Segmented: perm holds global indices; each CSR segment [off[s], off[s+1]) is
+ * sorted on its own.  Offsets must be non-decreasing, off[0] = 0, off[nseg] = n. */
+int oracle_sortperm_segmented(const void *keys, const int64_t *off, int64_t nseg, int64_t n,
+                              int dtype, int descending, int64_t *perm) {
+    if (check_args(keys, n, dtype, perm) || nseg < 0 || (nseg > 0 && !off)) return -1;
+    if (nseg > 0 && (off[0] != 0 || off[nseg] != n)) return -1;
+    for (int64_t s = 0; s < nseg; ++s)
+        if (off[s + 1] < off[s]) return -1;
+    oracle_ctx c = {keys, dtype, descending};
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    if (n < 2) return 0;
+    int64_t *tmp = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!tmp) return -2;
+    for (int64_t s = 0; s < nseg; ++s) merge_sort(&c, perm, tmp, off[s], off[s + 1]);
+    free(tmp);
+    return 0;
+}
+
+/* dst[i] = src[perm[i]] for elements of elem_bytes bytes (raw bits are moved). */
+int oracle_gather(const void *src, const int64_t *perm, int64_t n, int elem_bytes, void *dst) {
+    if (n < 0 || elem_bytes <= 0) return -1;
+    const unsigned char *s = (const unsigned char *)src;
+    unsigned char *d = (unsigned char *)dst;
+    for (int64_t i = 0; i < n; ++i)
+        memcpy(d + (size_t)i * (size_t)elem_bytes, s + (size_t)perm[i] * (size_t)elem_bytes,
+               (size_t)elem_bytes);
+    return 0;
+}
+
+/* isless(a[i], b[i]) for n pairs, exposed so tests can pin the comparator itself. */
+int oracle_isless_pairs(const void *a, const void *b, int64_t n, int dtype, uint8_t *out) {
+    if (n < 0 || dtype < 0 || dtype >= OD_COUNT) return -1;
+    size_t w = (dtype <= OD_I16) ? 2 : (dtype <= OD_I32 || dtype == OD_F32) ? 4 : 8;
+    unsigned char *buf = (unsigned char *)malloc(2 * w);
+    if (!buf) return -2;
+    oracle_ctx c = {buf, dtype, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        memcpy(buf, (const unsigned char *)a + (size_t)i * w, w);
+        memcpy(buf + w, (const unsigned char *)b + (size_t)i * w, w);
+        out[i] = (uint8_t)key_isless(&c, 0, 1);
+    }
+    free(buf);
+    return 0;
+}

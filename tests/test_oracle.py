@@ -1,0 +1,207 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things other than itself: Julia's documented
+isless facts (golden files), the brute-force definition of a stable sort,
+Python's stable Timsort, a counting sort, permutation closed forms and
+invariants.  A dropped NaN rule, a flipped sign test or an unstable merge fails
+at least one of these.
+"""
+import itertools
+import math
+import os
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+DTYPES = [np.uint16, np.int16, np.uint32, np.int32, np.uint64, np.int64, np.float32, np.float64]
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+@pytest.mark.parametrize("name,ut,ft", [("isless_f64.txt", np.uint64, np.float64),
+                                        ("isless_f32.txt", np.uint32, np.float32)])
+def test_isless_golden(name, ut, ft):
+    rows = _rows(name)
+    a = np.array([int(r[0], 16) for r in rows], dtype=ut).view(ft)
+    b = np.array([int(r[1], 16) for r in rows], dtype=ut).view(ft)
+    want = np.array([r[2] == "1" for r in rows])
+    assert np.array_equal(oracle.isless(a, b), want)
+
+
+def test_sorted_special_golden():
+    rows = _rows("sorted_special_f64.txt")
+    x, asc, desc = [np.array([int(t, 16) for t in r], dtype=np.uint64).view(np.float64) for r in rows]
+    assert np.array_equal(oracle.sort(x, "ascending").view(np.uint64), asc.view(np.uint64))
+    assert np.array_equal(oracle.sort(x, "descending").view(np.uint64), desc.view(np.uint64))
+
+
+def _py_key(v):
+    """Sort key for Python's sorted() giving Julia isless order (independent of the oracle)."""
+    if isinstance(v, float):
+        if math.isnan(v):
+            return (1, 0.0, 0)
+        return (0, v, 0 if math.copysign(1.0, v) < 0 else 1)
+    return (0, v, 0)
+
+
+def _is_stable_sorted(keys, perm, desc):
+    """Brute-force definition: for every i < j, key[p_i] comes strictly before
+    key[p_j], or they are equivalent and p_i < p_j."""
+    n = len(perm)
+    for i in range(n):
+        for j in range(i + 1, n):
+            a, b = keys[perm[i]:perm[i] + 1], keys[perm[j]:perm[j] + 1]
+            lt_ab = oracle.isless(b, a)[0] if desc else oracle.isless(a, b)[0]
+            lt_ba = oracle.isless(a, b)[0] if desc else oracle.isless(b, a)[0]
+            if lt_ab:
+                continue
+            if not lt_ba and perm[i] < perm[j]:
+                continue
+            return False
+    return True
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32, np.int32, np.uint16])
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 6])
+@pytest.mark.parametrize("desc", [False, True])
+def test_brute_force_unique_stable_permutation(dtype, n, desc):
+    pool = synth.special_values(dtype)
+    rng_idx = synth.splitmix64(100 + n, n) % np.uint64(pool.size)
+    keys = pool[rng_idx.astype(np.int64)]
+    if n >= 3:
+        keys[1] = keys[0]  # force a tie so stability matters
+    survivors = [p for p in itertools.permutations(range(n)) if _is_stable_sorted(keys, p, desc)]
+    assert len(survivors) == 1
+    got = oracle.sortperm(keys, "descending" if desc else "ascending")
+    assert tuple(got.tolist()) == survivors[0]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", ["bits", "dups", "narrow"])
+@pytest.mark.parametrize("desc", [False, True])
+def test_matches_python_timsort(dtype, mode, desc):
+    keys = synth.random_keys(3000, dtype, seed=7, mode=mode)
+    pyvals = [float(v) if np.dtype(dtype).kind == "f" else int(v) for v in keys]
+    want = sorted(range(keys.size), key=lambda i: _py_key(pyvals[i]), reverse=desc)
+    got = oracle.sortperm(keys, "descending" if desc else "ascending")
+    assert np.array_equal(got, np.array(want))
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.int16])
+@pytest.mark.parametrize("desc", [False, True])
+def test_counting_sort_16bit(dtype, desc):
+    """A counting sort (a different algorithm) on 16-bit keys."""
+    keys = synth.random_keys(20000, dtype, seed=11, mode="dups")
+    v = keys.astype(np.int64)
+    lo = int(v.min())
+    counts = np.bincount(v - lo, minlength=int(v.max()) - lo + 1)
+    if desc:
+        counts_rev = counts[::-1]
+        starts = np.concatenate([[0], np.cumsum(counts_rev)[:-1]])[::-1]
+    else:
+        starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    perm = np.empty(keys.size, dtype=np.int64)
+    nxt = starts.copy()
+    for i, key in enumerate(v - lo):
+        perm[nxt[key]] = i
+        nxt[key] += 1
+    assert np.array_equal(oracle.sortperm(keys, "descending" if desc else "ascending"), perm)
+
+
+@pytest.mark.parametrize("dtype", [np.int64, np.uint32, np.int16])
+def test_numpy_stable_argsort_on_ints(dtype):
+    keys = synth.random_keys(50000, dtype, seed=5, mode="dups")
+    assert np.array_equal(oracle.sortperm(keys), np.argsort(keys, kind="stable"))
+
+
+def test_inverse_permutation_closed_form():
+    n = 10007
+    pi = np.argsort(synth.splitmix64(9, n), kind="stable")   # a permutation
+    keys = np.empty(n, dtype=np.int64)
+    keys[pi] = np.arange(n)                                  # keys = pi^-1 ... shuffled iota
+    p = oracle.sortperm(keys)
+    assert np.array_equal(keys[p], np.arange(n))
+    assert np.array_equal(p, pi)
+
+
+def test_presorted_and_reversed():
+    x = np.sort(synth.u01_f64(4, 5000))
+    assert np.array_equal(oracle.sortperm(x), np.arange(x.size))
+    assert np.array_equal(oracle.sortperm(x[::-1].copy()), np.arange(x.size)[::-1])
+    assert np.array_equal(oracle.sortperm(x, "descending"), np.arange(x.size)[::-1])
+
+
+def test_descending_is_not_reverse_of_ascending_on_ties():
+    keys = np.array([2, 1, 2, 1], dtype=np.int32)
+    assert oracle.sortperm(keys, "descending").tolist() == [0, 2, 1, 3]
+    assert oracle.sortperm(keys, "ascending").tolist() == [1, 3, 0, 2]
+
+
+def test_nan_payloads_keep_input_order():
+    bits = np.array([0x7FC00003, 0x3F800000, 0xFFC00001, 0x7FC00002, 0x80000000, 0x00000000],
+                    dtype=np.uint32)
+    x = bits.view(np.float32)
+    out = oracle.sort(x).view(np.uint32)
+    assert out.tolist() == [0x80000000, 0x00000000, 0x3F800000, 0x7FC00003, 0xFFC00001, 0x7FC00002]
+    out = oracle.sort(x, "descending").view(np.uint32)
+    assert out.tolist() == [0x7FC00003, 0xFFC00001, 0x7FC00002, 0x3F800000, 0x00000000, 0x80000000]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.int64])
+def test_threaded_equals_single(dtype):
+    keys = synth.random_keys(200003, dtype, seed=3, mode="dups")
+    for order in ("ascending", "descending"):
+        assert np.array_equal(oracle.sortperm(keys, order), oracle.sortperm(keys, order, threads=7))
+
+
+def test_pairs_and_gather_move_raw_bits():
+    keys = synth.normal_f32_special(10000, seed=8, frac=0.01)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    k, v = oracle.sort_pairs(keys, vals)
+    assert np.array_equal(keys.view(np.uint32)[v], k.view(np.uint32))
+    # the multiset of raw bits is unchanged
+    assert np.array_equal(np.sort(k.view(np.uint32)), np.sort(keys.view(np.uint32)))
+
+
+def test_segmented_equals_per_segment_sort():
+    off = synth.lognormal_segments(200, seed=20, median=50.0, max_len=2000)
+    n = int(off[-1])
+    keys = synth.random_keys(n, np.float32, seed=21, mode="dups")
+    got = oracle.sortperm_segmented(keys, off)
+    for s in range(off.size - 1):
+        a, b = int(off[s]), int(off[s + 1])
+        assert np.array_equal(got[a:b], a + oracle.sortperm(keys[a:b]))
+
+
+def test_segmented_rejects_bad_offsets():
+    keys = np.arange(10, dtype=np.int32)
+    with pytest.raises(RuntimeError):
+        oracle.sortperm_segmented(keys, np.array([0, 6, 4, 10]))
+    with pytest.raises(RuntimeError):
+        oracle.sortperm_segmented(keys, np.array([0, 4, 9]))
+
+
+def test_generators_are_reproducible_and_shaped():
+    a = synth.normal_f32_special(100000, seed=3)
+    b = synth.normal_f32_special(100000, seed=3)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert np.isnan(a).sum() == 100
+    assert (a.view(np.uint32) == 0x80000000).sum() == 100
+    x = synth.normal_f64(3, 200000)
+    assert abs(x.mean()) < 0.01 and abs(x.std() - 1) < 0.01
+    off = synth.lognormal_segments()
+    lens = np.diff(off)
+    assert lens.size == 65536 and lens.min() >= 1 and lens.max() <= 1 << 20
+    assert abs(np.median(lens) - 2048) < 100
+    z = synth.zipf_mix_u32(1 << 20, seed=30)
+    top = synth.fmix32(np.array([0], dtype=np.uint32))[0]
+    frac = (z == top).mean()
+    assert 0.04 < frac < 0.08   # ~5.75% of keys equal the top rank
