@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Throughput of the single-device sort on GB300: keys GB/s sorted.
+
+Workload (one "step"): 268,435,456 int64 keys uniform over all 2^64 bit patterns
+and 268,435,456 float32 keys ~ N(0,1) with 0.1% NaN (random sign and payload)
+and 0.1% -0.0; each array goes through a stable ak_sortperm (UInt32 indices) and
+an in-place ak_sort, ascending -- the rank-local sort of the paper's sample sort
+(Sec. III-A) on its int64/float32 dtypes.  value = key bytes sorted per step (4
+calls) / device time, in GB/s (1e9 B/s), summed over ranks.
+
+Timing: 3+ warm-up steps; each call is bracketed by CUDA events on its stream;
+before every call the keys are restored from a pristine device copy and a 256 MiB
+buffer is written to flush L2 -- both outside the events.  The inputs (1-2 GiB)
+are larger than L2 as well.  SM clocks are sampled with nvidia-smi during the
+timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank sorts its own replica of the workload on its own GPU
+(the sort has no exchange step on one node here: replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FULL_N = 268_435_456
+METRIC = "keys GB/s sorted (device-timed, 1 GB300) and % of 2×bytes/8TB/s roofline; learned vs plain"
+NOMINAL_HBM_GBS = 8000.0
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of onesweep_pass per key and
+# pass, from the capture summarised in profiles/ (None until captured for the
+# current kernel).
+NCU_TRAFFIC = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=FULL_N, help="keys per array (default: the full workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(n: int) -> dict:
+    return {
+        "workload": (f"{n:,} int64 uniform(all bits) + {n:,} float32 N(0,1) with 0.1% NaN and 0.1% -0.0; "
+                     "ak_sortperm (stable, UInt32) + ak_sort each, ascending; plain radix path"),
+        "keys_per_array": n,
+        "calls_per_step": 4,
+        "key_bytes_per_step": 24 * n,
+        "l2": "256 MiB flush write before every call; inputs 1-2 GiB (> 129 MB L2)",
+        "timing": "sum of CUDA-event intervals around each ak_* call; input restore and L2 flush excluded",
+        "parallelism": "replicas (one independent sort per GPU)",
+    }
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, target: str | None):
+        self.proc = None
+        self.target = target
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.target:
+            cmd += ["-i", self.target]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_target(torch, dev: int):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+def onesweep_bytes(op: str, n: int, w: int, passes: int) -> list[int]:
+    """Algorithmic bytes of each digit pass (the dominant kernel) of one call."""
+    if op == "sort":
+        return [2 * n * w] * passes
+    out = []
+    for q in range(passes):
+        if q == 0:
+            out.append(2 * n * w + 4 * n)          # read keys, write keys + generated index
+        elif q == passes - 1:
+            out.append(n * w + 8 * n)              # read keys + perm, write perm only
+        else:
+            out.append(2 * n * w + 8 * n)
+    return out
+
+
+def cpu_oracle_rate(k64: np.ndarray, k32: np.ndarray, sample: int, threads: int) -> tuple[float, float]:
+    """Oracle (threaded merge sort) on `sample` keys of each array, the same four
+    calls as a step.  Returns (GB/s of keys, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    nbytes = 0
+    for arr in (k64[:sample], k32[:sample]):
+        oracle.sortperm(arr, threads=threads)                  # sortperm
+        oracle.gather(arr, oracle.sortperm(arr, threads=threads))  # sort
+        nbytes += 2 * arr.nbytes
+    dt = time.perf_counter() - t0
+    return nbytes / dt / 1e9, dt
+
+
+def base_line(args, world, cfg):
+    return {"metric": METRIC, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64+u32 radix keys (int64, float32 inputs)", "data": "synthetic (seeded splitmix64)",
+            "config": cfg}
+
+
+def run_reference(args):
+    """The oracle as it stands, on this host's cores, on bounded samples."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    threads = os.cpu_count() or 1
+    sample = min(args.n, 1 << 23)
+    k64 = synth.uniform_i64(sample, seed=2)
+    k32 = synth.normal_f32_special(sample, seed=3)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(k64, k32, min(sample, 1 << 16), threads)
+    secs = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(k64, k32, sample, threads)
+        secs.append(dt)
+    step_bytes = 24 * sample
+    value = step_bytes * len(secs) / sum(secs) / 1e9
+    line = base_line(args, world, workload_config(args.n))
+    line.update({"impl": "reference", "value": round(value, 4), "ms_per_step": round(1e3 * sum(secs) / len(secs), 3),
+                 "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                                  "sample": f"{sample:,} int64 + {sample:,} float32 keys per step (sortperm + sort each)"},
+                 "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                 "gpu_launches": 0})
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2507_16710_gb300 as ak
+    import synth
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+    cfg = workload_config(n)
+
+    k64 = synth.uniform_i64(n, seed=2)
+    k32 = synth.normal_f32_special(n, seed=3)
+    arrays = []
+    for host, kd, w in ((k64, ak.AK_I64, 8), (k32, ak.AK_F32, 4)):
+        pristine = torch.from_numpy(host).to(dev)
+        arrays.append({"pristine": pristine, "work": torch.empty_like(pristine), "kd": kd, "w": w})
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    tb = max(ak.temp_bytes(op, n, kd) for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM) for kd in (ak.AK_I64, ak.AK_F32))
+    temp = ak.workspace(tb, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = ak.load()
+
+    # per-pass profiling events (raw handles created by a first record)
+    pass_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * ak.AK_MAX_PASSES)]
+    for e in pass_ev:
+        e.record(stream)
+    ev_arr = (ctypes.c_void_p * len(pass_ev))(*[e.cuda_event for e in pass_ev])
+    opts = ak.Options()
+    opts.pass_events = ctypes.cast(ev_arr, ctypes.c_void_p)
+    calls = [("sortperm", 0), ("sort", 0), ("sortperm", 1), ("sort", 1)]
+
+    def call(op, a, with_events):
+        o = ctypes.byref(opts) if with_events else None
+        if op == "sort":
+            rc = lib.ak_sort(a["work"].data_ptr(), n, a["kd"], 0, temp.data_ptr(), temp.numel(),
+                             stream.cuda_stream, o)
+        else:
+            rc = lib.ak_sortperm(a["work"].data_ptr(), perm.data_ptr(), n, a["kd"], 0, temp.data_ptr(),
+                                 temp.numel(), stream.cuda_stream, o)
+        if rc:
+            raise ak.AkError(rc, op)
+
+    # warm-up (also learns how many digit passes move data per call)
+    passes = {}
+    for _ in range(args.warmup):
+        for op, i in calls:
+            arrays[i]["work"].copy_(arrays[i]["pristine"])
+            call(op, arrays[i], False)
+            passes[(op, i)] = ak.ak_last_info(temp)["radix_passes"]
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+
+    call_ms = []
+    per_call = {f"{op}_{'i64' if i == 0 else 'f32'}": [] for op, i in calls}
+    pass_ms, pass_bytes = [], []
+    sampler = ClockSampler(gpu_target(torch, dev.index))
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        evs = []
+        for op, i in calls:
+            a = arrays[i]
+            a["work"].copy_(a["pristine"])
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call(op, a, True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)  # pass events are reused by the next call
+            evs.append((e0, e1))
+            npass = a["w"]
+            pb = onesweep_bytes(op, n, a["w"], npass)
+            for p in range(npass):
+                pass_ms.append(pass_ev[2 * p].elapsed_time(pass_ev[2 * p + 1]))
+                pass_bytes.append(pb[p] if passes[(op, i)] == npass else 0)
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        for (op, i), t in zip(calls, ms):
+            per_call[f"{op}_{'i64' if i == 0 else 'f32'}"].append(t)
+        call_ms.append(sum(ms))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+
+    total_ms = sum(call_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    step_bytes = 24 * n
+    value = world * step_bytes * args.steps / (total_ms / 1e3) / 1e9
+
+    # dominant kernel: onesweep_pass (digit passes)
+    peak, peak_kind = load_peaks()
+    achieved = sum(pass_bytes) / (sum(pass_ms) / 1e3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC is not None:
+        traffic = NCU_TRAFFIC
+    roofline = {"bound": "hbm", "kernel": "onesweep_pass", "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": f"{peak_kind} (copy, burst)", "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "launches": len(pass_ms),
+                "avg_launch_ms": round(sum(pass_ms) / len(pass_ms), 4),
+                "share_of_call_time": round(sum(pass_ms) / total_ms, 4) if world == 1 else None,
+                "algorithmic_bytes_per_launch": int(sum(pass_bytes) / len(pass_bytes))}
+    extra = {"literal_2x_key_bytes_frac_of_8TBs": round(2 * value / world / NOMINAL_HBM_GBS, 4),
+             "literal_2x_key_bytes_frac_of_measured": round(2 * value / world / peak, 4),
+             "per_call_ms": {k: round(statistics.median(v), 4) for k, v in per_call.items()},
+             "wall_s_timed_region": round(wall, 3)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n)
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        sample = min(n, 1 << 24)
+        rate, dt = cpu_oracle_rate(k64, k32, sample, threads)
+        cpu = {"value": round(rate, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {sample:,} keys of each array, sortperm + sort each (threaded merge sort), {dt:.1f} s"}
+
+    launches_per_step = sum(3 + (8 if i == 0 else 4) for _, i in calls)
+    if rank == 0:
+        line = base_line(args, world, cfg)
+        line.update({"value": round(value, 3), "ms_per_step": round(total_ms / args.steps, 4),
+                     "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                     "gpu_launches": launches_per_step * args.steps, "extra": extra})
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n):
+    """Same four calls from pinned host buffers: H2D keys, sortperm, sort, D2H perm + sorted keys."""
+    hosts = [torch.from_numpy(k64).pin_memory(), torch.from_numpy(k32).pin_memory()]
+    outs_k = [torch.empty_like(h).pin_memory() for h in hosts]
+    outs_p = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in hosts]
+    dk = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in hosts]
+    dp = torch.empty(n, dtype=torch.int32, device=dev)
+    kds = [ak.AK_I64, ak.AK_F32]
+
+    def step():
+        for i in range(2):
+            dk[i].copy_(hosts[i], non_blocking=True)
+            rc = lib.ak_sortperm(dk[i].data_ptr(), dp.data_ptr(), n, kds[i], 0, temp.data_ptr(), temp.numel(),
+                                 stream.cuda_stream, None)
+            rc |= lib.ak_sort(dk[i].data_ptr(), n, kds[i], 0, temp.data_ptr(), temp.numel(), stream.cuda_stream,
+                              None)
+            if rc:
+                raise ak.AkError(rc, "e2e")
+            outs_p[i].copy_(dp, non_blocking=True)
+            outs_k[i].copy_(dk[i], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    steps = max(1, min(args.steps, 3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    h2d = sum(h.numel() * h.element_size() for h in hosts)
+    d2h = h2d + 2 * 4 * n
+    return {"value": round(24 * n / (ms / 1e3) / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3), "steps": steps}
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

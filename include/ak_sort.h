@@ -1,0 +1,234 @@
+/*
+ * ak_sort.h -- C ABI of a single-device GPU sort for NVIDIA GB300 (sm_103a).
+ *
+ * The library sorts large arrays of primitive numeric keys on one GPU: the
+ * rank-local sorting step that every accelerator runs inside the sample sort of
+ * the paper's distributed benchmark (Sec. III-A, "MPISort Algorithm"), with the
+ * operations of the paper's sorting building blocks (Sec. II-B: merge_sort,
+ * merge_sort_by_key, sortperm) and Julia Base ordering (Sec. II).
+ *
+ * Ordering.  Keys are ordered by Julia `isless`: integers by value; floats by
+ * value except that -0.0 sorts before +0.0 and every NaN sorts after +Inf, all
+ * NaNs being equivalent.  AK_DESCENDING is Julia's rev=true: the order relation is
+ * reversed (NaNs first) and equivalent keys still keep their input order.  Every
+ * operation is stable, and raw key bits are moved, so NaN payloads and signs
+ * survive in input order.
+ *
+ * Memory.  The caller owns every buffer.  The library never allocates or frees
+ * device memory: each call takes a caller workspace `d_temp` whose size is given
+ * ahead of time by ak_sort_temp_bytes (the "exposed temporaries" of Sec. II-B).
+ * All device pointers must be device-accessible (cudaMalloc or a torch CUDA
+ * tensor); `d_temp` must be 256-byte aligned.  Key, value and permutation
+ * pointers must be aligned to their element size; 16-byte alignment enables the
+ * bulk-copy tile loads (other alignments take plain loads).
+ *
+ * Asynchrony and errors.  Every call only enqueues work on `stream` (NULL = the
+ * legacy default stream) and returns.  Argument errors are returned directly and
+ * nothing is enqueued.  Faults found on the device (a bounded wait that expired)
+ * are written to a status word inside `d_temp` and read by ak_status_check.  No
+ * call synchronises the stream except ak_status_check and ak_last_info, and no
+ * call allocates, so the sort calls can be captured into a CUDA graph.
+ * Concurrent calls must use distinct `d_temp` buffers.
+ */
+#ifndef AK_SORT_H
+#define AK_SORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ak_stream_t; /* same handle as cudaStream_t */
+
+/* Key element types: the paper's FFI list (Sec. III: int16, int32, int64,
+ * float, double) with unsigned variants; __int128 is not supported. */
+typedef enum ak_dtype {
+    AK_U16 = 0, AK_I16 = 1, AK_U32 = 2, AK_I32 = 3,
+    AK_U64 = 4, AK_I64 = 5, AK_F32 = 6, AK_F64 = 7
+} ak_dtype;
+
+typedef enum ak_order { AK_ASCENDING = 0, AK_DESCENDING = 1 } ak_order;
+
+typedef enum ak_status {
+    AK_OK = 0,
+    AK_ERR_INVALID_ARG = 1,         /* NULL pointer with n > 0, bad enum, bad size */
+    AK_ERR_UNSUPPORTED = 2,         /* valid request this build does not serve */
+    AK_ERR_WORKSPACE_TOO_SMALL = 3, /* d_temp NULL or temp_bytes too small */
+    AK_ERR_CUDA = 4,                /* a CUDA runtime call or launch failed */
+    AK_ERR_TIMEOUT = 5,             /* a device-side wait exceeded its bound */
+    AK_ERR_INDEX_OVERFLOW = 6       /* sortperm with n >= 2^32 (UInt32 indices) */
+} ak_status;
+
+typedef enum ak_op {
+    AK_OP_SORT = 0, AK_OP_SORTPERM = 1, AK_OP_SORT_PAIRS = 2, AK_OP_SORT_SEGMENTED = 3
+} ak_op;
+
+typedef enum ak_path {
+    AK_PATH_AUTO = 0,     /* library choice (autotune cache, then size rules) */
+    AK_PATH_RADIX = 1,    /* onesweep LSD radix: histogram + one kernel per digit */
+    AK_PATH_LEARNED = 2,  /* learned-CDF bucketing + per-bucket shared-memory sort */
+    AK_PATH_BLOCK = 3     /* one-launch shared-memory sort (small n only) */
+} ak_path;
+
+/* Optional tuning knobs.  Pass NULL for defaults; zero fields mean "default". */
+typedef struct ak_options {
+    int32_t path;          /* ak_path */
+    int32_t tile_config;   /* onesweep tile variant: 0 = default, 1..AK_TILE_CONFIGS */
+    int32_t bucket_bits;   /* learned path: log2(bucket count incl. NaN bucket), 0 = auto */
+    uint32_t seed;         /* learned path: seed of the sample index stream */
+    uint64_t timeout_ns;   /* bound on every device-side wait, 0 = 1 s */
+    int32_t train_steps;   /* learned path: Adam steps of the residual MLP, 0 = default,
+                              -1 = no MLP (piecewise-linear CDF only) */
+    int32_t debug_flags;   /* test hooks, 0 in normal use (AK_DEBUG_*) */
+    void **pass_events;    /* optional: 2*AK_MAX_PASSES cudaEvent_t created by the caller;
+                              the radix path records [2p] before and [2p+1] after the
+                              launch of digit pass p on the call's stream (profiling) */
+    int32_t reserved[4];   /* must be zero */
+} ak_options;
+
+#define AK_MAX_PASSES 8
+
+/* Test hook: no CTA owns the first tile of any radix pass, so every look-back
+ * that reaches it waits until timeout_ns and the call ends with AK_ERR_TIMEOUT
+ * (the keys are then unspecified).  Exercises the bounded-wait error path. */
+#define AK_DEBUG_SKIP_FIRST_TILE 1
+
+#define AK_TILE_CONFIGS 3
+
+/* Diagnostics written by the device for the most recent call on a d_temp. */
+typedef struct ak_info {
+    int32_t status;          /* ak_status of the device side */
+    int32_t path;            /* ak_path actually executed (learned may fall back to radix) */
+    int32_t radix_passes;    /* digit passes that moved data (trivial passes skipped) */
+    int32_t buckets;         /* learned: bucket count used */
+    int64_t overfull_keys;   /* learned: keys in buckets above the shared-memory capacity */
+    int64_t max_bucket;      /* learned: largest bucket */
+    float loss_before;       /* learned: training loss of the piecewise-linear CDF alone */
+    float loss_after;        /* learned: training loss after the MLP residual is trained */
+    int64_t sample_size;     /* learned: sample keys drawn */
+    int64_t reserved[4];
+} ak_info;
+
+/*
+ * Workspace bytes for one call.
+ *   op        ak_op
+ *   n         number of keys (>= 0)
+ *   kd        key dtype
+ *   val_bytes AK_OP_SORT_PAIRS: bytes per value (1, 2, 4 or 8); ignored otherwise
+ *   nseg      AK_OP_SORT_SEGMENTED: number of segments; ignored otherwise
+ *   opt       options (NULL = defaults); the path changes the size
+ *   bytes     out: required size of d_temp
+ * Returns AK_ERR_INVALID_ARG for a negative n/nseg, a bad enum or a NULL `bytes`.
+ */
+ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int64_t nseg,
+                             const ak_options *opt, size_t *bytes);
+
+/*
+ * In-place stable sort of d_keys[0..n) (Sec. II-B "merge_sort"; the local sort of
+ * Sec. III-A).  n = 0 is a no-op.
+ */
+ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order,
+                  void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt);
+
+/*
+ * Stable sorting permutation (Sec. II-B "sortperm"): d_perm[i] is the 0-based
+ * index of the key that belongs at position i.  d_keys is read only.  Indices are
+ * UInt32, so n >= 2^32 returns AK_ERR_INDEX_OVERFLOW.  d_perm must not overlap
+ * d_keys or d_temp.
+ */
+ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
+                      void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt);
+
+/*
+ * In-place stable key-value sort (Sec. II-B "merge_sort_by_key"): keys and the
+ * values d_vals[0..n) (val_bytes = 1, 2, 4 or 8 each) are permuted together.
+ */
+ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak_dtype kd,
+                        ak_order order, void *d_temp, size_t temp_bytes, ak_stream_t stream,
+                        const ak_options *opt);
+
+/*
+ * Segmented in-place stable sort: every CSR segment d_keys[off[s], off[s+1]),
+ * s < nseg, is sorted on its own, all in one batch of launches.  d_offsets is a
+ * device array of nseg+1 int64 values, non-decreasing, off[0] = 0 and
+ * off[nseg] = n.  The offsets are read on the device only; offsets that break
+ * these rules give an unspecified key order (never an out-of-bounds access:
+ * every offset is clamped to [0, n]).
+ */
+ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg, int64_t n,
+                            ak_dtype kd, ak_order order, void *d_temp, size_t temp_bytes,
+                            ak_stream_t stream, const ak_options *opt);
+
+/*
+ * Synchronises `stream` and returns the device-side status of the last call that
+ * used d_temp (AK_OK, or e.g. AK_ERR_TIMEOUT).  AK_ERR_CUDA if the copy fails.
+ */
+ak_status ak_status_check(const void *d_temp, ak_stream_t stream);
+
+/* Synchronises `stream` and copies the diagnostics of the last call on d_temp. */
+ak_status ak_last_info(const void *d_temp, ak_stream_t stream, ak_info *info);
+
+/* Static English description of a status code. */
+const char *ak_status_string(ak_status s);
+
+/* ------------------------------------------------------------------------- */
+/* Learned-CDF model kernels, exposed for checking against a CPU restatement. */
+/* The sample-sort splitter step (Sec. III-A) draws the sample these act on.  */
+
+#define AK_LEARNED_KNOTS 64
+#define AK_LEARNED_PARAMS 321
+
+/*
+ * Knot counts of the piecewise-linear CDF: d_counts[j] = #{i : d_xs[i] <= fp32(j/63)}
+ * for j < 64, over an ascending float32 sample d_xs[0..m) in [0, 1] (an
+ * interpolated histogram of the sample, Sec. III-A).  One small launch.
+ */
+ak_status ak_learned_knot_counts(const float *d_xs, int64_t m, int32_t *d_counts,
+                                 ak_stream_t stream);
+
+/*
+ * Loss and gradient of the residual MLP (1 -> 16 -> 16 -> 1, ReLU) for the model
+ * F(x) = PL(x) + r(x): d_loss[0] = mean_i (F(x_i) - y_i)^2 and d_grad = dLoss/dparams,
+ * computed by the same forward/backward kernels the learned path trains with.
+ *   d_x, d_y   m float32 inputs and targets
+ *   d_c        64 float32 knot values of PL at fp32(j/63)
+ *   d_params   321 float32: W1[16], b1[16], W2[16][16] (row j feeds hidden unit j),
+ *              b2[16], w3[16], b3
+ *   d_grad     321 float32 out; d_loss 1 float32 out
+ *   d_temp     workspace of at least ak_learned_grad_temp_bytes(m) bytes
+ * The reduction order is fixed, so results are deterministic.
+ */
+ak_status ak_learned_loss_grad(const float *d_x, const float *d_y, int64_t m, const float *d_c,
+                               const float *d_params, float *d_grad, float *d_loss,
+                               void *d_temp, size_t temp_bytes, ak_stream_t stream);
+size_t ak_learned_grad_temp_bytes(int64_t m);
+
+/* ------------------------------------------------------------------------- */
+/* Autotuner: times the onesweep tile variants and learned/radix paths on the
+ * caller's buffers (their contents are overwritten) and caches the fastest
+ * per (op, dtype, log2 n, order, value bytes).  AK_PATH_AUTO consults the cache. */
+
+/*
+ * Tunes one call shape.  d_keys/d_vals/d_perm are scratch of the call's sizes
+ * (d_vals only for pairs, d_perm only for sortperm); d_temp must hold the
+ * largest variant (ak_sort_temp_bytes with path AK_PATH_LEARNED).  Synchronises
+ * `stream`.  best (optional) receives the chosen options.
+ */
+ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order order,
+                      void *d_keys, void *d_vals, uint32_t *d_perm, void *d_temp,
+                      size_t temp_bytes, ak_stream_t stream, ak_options *best);
+/* JSON persistence of the tuning cache (one object per line). */
+ak_status ak_autotune_save(const char *path);
+ak_status ak_autotune_load(const char *path);
+void ak_autotune_clear(void);
+
+/* Library version string. */
+const char *ak_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AK_SORT_H */

@@ -1,0 +1,257 @@
+// ak_api.cu -- the C ABI: argument checks, workspace layout, path choice and the
+// launch sequence on the caller's stream.  No allocation, no stream sync.
+#include <string.h>
+
+#include <type_traits>
+
+#include "internal.h"
+#include "onesweep.cuh"
+
+namespace ak {
+
+int device_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
+  if (dev >= 0 && dev < 64) cache[dev] = sms;
+  return sms;
+}
+
+int radix_tile_keys(int key_bytes, int cfg) {
+  static const int B[3] = {256, 256, 512};
+  static const int I16[3] = {16, 8, 16}, I32[3] = {15, 8, 12}, I64[3] = {10, 6, 8};
+  if (cfg < 0 || cfg > 2) cfg = 0;
+  const int *I = key_bytes == 2 ? I16 : key_bytes == 4 ? I32 : I64;
+  return B[cfg] * I[cfg];
+}
+
+int radix_min_tile_keys(int key_bytes) {
+  int m = radix_tile_keys(key_bytes, 0);
+  for (int c = 1; c < AK_TILE_CONFIGS; ++c) m = m < radix_tile_keys(key_bytes, c) ? m : radix_tile_keys(key_bytes, c);
+  return m;
+}
+
+static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct KeyInfo {
+  int bytes;
+  int kind;
+};
+
+static bool key_info(int kd, KeyInfo *ki) {
+  switch (kd) {
+    case AK_U16: *ki = {2, KIND_UINT}; return true;
+    case AK_I16: *ki = {2, KIND_SINT}; return true;
+    case AK_U32: *ki = {4, KIND_UINT}; return true;
+    case AK_I32: *ki = {4, KIND_SINT}; return true;
+    case AK_U64: *ki = {8, KIND_UINT}; return true;
+    case AK_I64: *ki = {8, KIND_SINT}; return true;
+    case AK_F32: *ki = {4, KIND_FLOAT}; return true;
+    case AK_F64: *ki = {8, KIND_FLOAT}; return true;
+  }
+  return false;
+}
+
+// Workspace of the radix path.
+struct RadixLayout {
+  size_t hdr, counts, plan, status0, status1, k_alt0, k_alt1, v_alt, total;
+  int status_wide;
+};
+
+static RadixLayout radix_layout(int op, int64_t n, int key_bytes, int val_bytes, int tile_keys) {
+  RadixLayout L{};
+  size_t off = 0;
+  L.hdr = off;
+  off += align256(sizeof(DevHeader));
+  L.counts = off;
+  off += align256(sizeof(unsigned long long) * MAX_PASSES * RADIX);
+  L.plan = off;
+  off += align256(sizeof(RadixPlan));
+  const int64_t tiles = (n + tile_keys - 1) / tile_keys;
+  // A pass that moves data has every digit count below n, so 30-bit look-back
+  // counts hold any n <= 2^30.
+  L.status_wide = n > (int64_t(1) << 30);
+  const size_t sw = L.status_wide ? 8 : 4;
+  L.status0 = off;
+  off += align256(size_t(tiles) * RADIX * sw);
+  L.status1 = off;
+  off += align256(size_t(tiles) * RADIX * sw);
+  L.k_alt0 = off;
+  off += align256(size_t(n) * key_bytes);
+  if (op == AK_OP_SORTPERM) {
+    L.k_alt1 = off;
+    off += align256(size_t(n) * key_bytes);
+    L.v_alt = off;
+    off += align256(size_t(n) * 4);
+  } else if (op == AK_OP_SORT_PAIRS) {
+    L.v_alt = off;
+    off += align256(size_t(n) * val_bytes);
+  }
+  L.total = off;
+  return L;
+}
+
+static ak_options resolve_options(const ak_options *opt) {
+  ak_options o{};
+  if (opt) o = *opt;
+  if (o.timeout_ns == 0) o.timeout_ns = 1000000000ull;
+  return o;
+}
+
+static cudaError_t radix_dispatch(int key_bytes, const RadixCall &c) {
+  switch (key_bytes) {
+    case 2: return radix_launch_u16(c);
+    case 4: return radix_launch_u32(c);
+    default: return radix_launch_u64(c);
+  }
+}
+
+static bool valid_order(int order) { return order == AK_ASCENDING || order == AK_DESCENDING; }
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Shared tail of sort / sortperm / pairs on the radix path.
+static ak_status run_radix(int op, const void *k_in, void *k_final, const void *v_in, void *v_final,
+                           int val_bytes, int64_t n, const KeyInfo &ki, int order, void *d_temp,
+                           size_t temp_bytes, cudaStream_t stream, const ak_options &o) {
+  // Look-back arrays are sized for the smallest tile of any configuration, so
+  // every configuration the launcher may pick fits.
+  const RadixLayout L = radix_layout(op, n, ki.bytes, val_bytes, radix_min_tile_keys(ki.bytes));
+  if (d_temp == nullptr || temp_bytes < L.total) return AK_ERR_WORKSPACE_TOO_SMALL;
+  uint8_t *t = static_cast<uint8_t *>(d_temp);
+  if (cudaMemsetAsync(t, 0, L.plan, stream) != cudaSuccess) return AK_ERR_CUDA;
+  RadixCall c{};
+  c.mode = (op == AK_OP_SORTPERM) ? MODE_PERM : MODE_INPLACE;
+  c.k_in = k_in;
+  c.k_final = k_final;
+  c.k_alt0 = t + L.k_alt0;
+  c.k_alt1 = (op == AK_OP_SORTPERM) ? t + L.k_alt1 : nullptr;
+  c.v_in = v_in;
+  c.v_final = v_final;
+  c.v_alt = L.v_alt ? t + L.v_alt : nullptr;
+  c.val_bytes = (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
+  c.n = n;
+  c.kind = ki.kind;
+  c.descending = order == AK_DESCENDING;
+  c.tile_config = (o.tile_config >= 1 && o.tile_config <= AK_TILE_CONFIGS) ? o.tile_config - 1 : 0;
+  c.hdr = reinterpret_cast<DevHeader *>(t + L.hdr);
+  c.counts = reinterpret_cast<unsigned long long *>(t + L.counts);
+  c.plan = reinterpret_cast<RadixPlan *>(t + L.plan);
+  c.status[0] = t + L.status0;
+  c.status[1] = t + L.status1;
+  c.status_wide = L.status_wide;
+  c.timeout_ns = o.timeout_ns;
+  c.path_tag = AK_PATH_RADIX;
+  c.debug_flags = o.debug_flags;
+  c.pass_events = o.pass_events;
+  c.stream = stream;
+  return radix_dispatch(ki.bytes, c) == cudaSuccess ? AK_OK : AK_ERR_CUDA;
+}
+
+}  // namespace ak
+
+using namespace ak;
+
+extern "C" {
+
+const char *ak_version(void) { return "ak_sort 0.1 (sm_103a)"; }
+
+const char *ak_status_string(ak_status s) {
+  switch (s) {
+    case AK_OK: return "ok";
+    case AK_ERR_INVALID_ARG: return "invalid argument";
+    case AK_ERR_UNSUPPORTED: return "unsupported request";
+    case AK_ERR_WORKSPACE_TOO_SMALL: return "workspace missing or too small";
+    case AK_ERR_CUDA: return "CUDA error";
+    case AK_ERR_TIMEOUT: return "device-side wait timed out";
+    case AK_ERR_INDEX_OVERFLOW: return "n too large for UInt32 indices";
+  }
+  return "unknown status";
+}
+
+ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int64_t nseg,
+                             const ak_options *opt, size_t *bytes) {
+  KeyInfo ki;
+  if (!bytes || n < 0 || !key_info(kd, &ki)) return AK_ERR_INVALID_ARG;
+  if (op < AK_OP_SORT || op > AK_OP_SORT_SEGMENTED) return AK_ERR_INVALID_ARG;
+  if (op == AK_OP_SORT_PAIRS && val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8)
+    return AK_ERR_INVALID_ARG;
+  if (op == AK_OP_SORT_SEGMENTED && nseg < 0) return AK_ERR_INVALID_ARG;
+  const ak_options o = resolve_options(opt);
+  if (op == AK_OP_SORT_SEGMENTED) return AK_ERR_UNSUPPORTED;
+  (void)o;
+  *bytes = radix_layout(op, n, ki.bytes, val_bytes, radix_min_tile_keys(ki.bytes)).total;
+  return AK_OK;
+}
+
+ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_temp, size_t temp_bytes,
+                  ak_stream_t stream, const ak_options *opt) {
+  KeyInfo ki;
+  if (n < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  if (n == 0) return AK_OK;
+  if (!d_keys || !aligned(d_keys, ki.bytes)) return AK_ERR_INVALID_ARG;
+  if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
+  const ak_options o = resolve_options(opt);
+  return run_radix(AK_OP_SORT, d_keys, d_keys, nullptr, nullptr, 0, n, ki, order, d_temp, temp_bytes,
+                   reinterpret_cast<cudaStream_t>(stream), o);
+}
+
+ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
+                      void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt) {
+  KeyInfo ki;
+  if (n < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  if (n == 0) return AK_OK;
+  if (n > int64_t(0xFFFFFFFFll)) return AK_ERR_INDEX_OVERFLOW;
+  if (!d_keys || !d_perm || !aligned(d_keys, ki.bytes) || !aligned(d_perm, 4)) return AK_ERR_INVALID_ARG;
+  if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
+  const ak_options o = resolve_options(opt);
+  return run_radix(AK_OP_SORTPERM, d_keys, nullptr, nullptr, d_perm, 4, n, ki, order, d_temp, temp_bytes,
+                   reinterpret_cast<cudaStream_t>(stream), o);
+}
+
+ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak_dtype kd, ak_order order,
+                        void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt) {
+  KeyInfo ki;
+  if (n < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  if (val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8) return AK_ERR_INVALID_ARG;
+  if (n == 0) return AK_OK;
+  if (!d_keys || !d_vals || !aligned(d_keys, ki.bytes) || !aligned(d_vals, val_bytes)) return AK_ERR_INVALID_ARG;
+  if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
+  const ak_options o = resolve_options(opt);
+  return run_radix(AK_OP_SORT_PAIRS, d_keys, d_keys, d_vals, d_vals, val_bytes, n, ki, order, d_temp,
+                   temp_bytes, reinterpret_cast<cudaStream_t>(stream), o);
+}
+
+ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg, int64_t n, ak_dtype kd,
+                            ak_order order, void *d_temp, size_t temp_bytes, ak_stream_t stream,
+                            const ak_options *opt) {
+  (void)d_keys; (void)d_offsets; (void)nseg; (void)n; (void)kd; (void)order;
+  (void)d_temp; (void)temp_bytes; (void)stream; (void)opt;
+  return AK_ERR_UNSUPPORTED;
+}
+
+ak_status ak_status_check(const void *d_temp, ak_stream_t stream) {
+  if (!d_temp) return AK_ERR_INVALID_ARG;
+  uint32_t s = 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&s, d_temp, sizeof(s), cudaMemcpyDeviceToHost, st) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return AK_ERR_CUDA;
+  return static_cast<ak_status>(s);
+}
+
+ak_status ak_last_info(const void *d_temp, ak_stream_t stream, ak_info *info) {
+  if (!d_temp || !info) return AK_ERR_INVALID_ARG;
+  DevHeader h;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&h, d_temp, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return AK_ERR_CUDA;
+  *info = h.info;
+  info->status = int32_t(h.status);
+  return AK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+"""Parity of the onesweep radix path (ak_sort / ak_sortperm / ak_sort_pairs)
+against the CPU oracle, bit-exact, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_util import (assert_bits_equal, check_perm_properties, oracle_perm, to_dev,
+                            to_host)
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = [np.uint16, np.int16, np.uint32, np.int32, np.uint64, np.int64, np.float32, np.float64]
+# sizes around the tile boundaries of every tile configuration plus ragged tails
+SIZES = [1, 2, 31, 33, 1000, 1535, 1536, 2048, 2560, 3839, 3840, 3841, 4096, 6144, 7681, 100003]
+
+
+@pytest.fixture(scope="module")
+def ak():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_16710_gb300 import _build
+    _build.build()
+    import paper_2507_16710_gb300 as m
+    return m
+
+
+def _run_sort(ak, keys, desc, options=None):
+    t, u = to_dev(keys)
+    ak.ak_sort(t, "descending" if desc else "ascending", options=options, unsigned=u)
+    torch.cuda.synchronize()
+    return to_host(t, keys.dtype)
+
+
+def _run_perm(ak, keys, desc, options=None):
+    t, u = to_dev(keys)
+    p = ak.ak_sortperm(t, "descending" if desc else "ascending", options=options, unsigned=u)
+    torch.cuda.synchronize()
+    assert_bits_equal(to_host(t, keys.dtype), keys, "sortperm modified keys")
+    return to_host(p, np.uint32)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("desc", [False, True])
+@pytest.mark.parametrize("mode", ["bits", "dups", "narrow"])
+def test_sort_matches_oracle(ak, dtype, desc, mode):
+    for n in (SIZES if mode == "bits" else [3841, 100003]):
+        keys = synth.random_keys(n, dtype, seed=1000 + n, mode=mode)
+        want = oracle.gather(keys, oracle_perm(keys, desc))
+        assert_bits_equal(_run_sort(ak, keys, desc), want, f"sort n={n}")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("desc", [False, True])
+@pytest.mark.parametrize("mode", ["bits", "dups"])
+def test_sortperm_matches_oracle(ak, dtype, desc, mode):
+    for n in ([1, 3840, 3841, 100003] if mode == "bits" else [5000, 100003]):
+        keys = synth.random_keys(n, dtype, seed=2000 + n, mode=mode)
+        want = oracle_perm(keys, desc).astype(np.uint32)
+        assert np.array_equal(_run_perm(ak, keys, desc), want), f"sortperm n={n}"
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.float64, np.int16, np.float32])
+@pytest.mark.parametrize("vdtype", [np.uint8, np.uint16, np.uint32, np.uint64])
+@pytest.mark.parametrize("desc", [False, True])
+def test_pairs_match_oracle(ak, dtype, vdtype, desc):
+    n = 50001
+    keys = synth.random_keys(n, dtype, seed=3000, mode="dups")
+    vals = synth.splitmix64(3001, n).astype(vdtype)
+    p = oracle_perm(keys, desc)
+    kt, ku = to_dev(keys)
+    vt, _ = to_dev(vals)
+    ak.ak_sort_pairs(kt, vt, "descending" if desc else "ascending", unsigned=ku)
+    torch.cuda.synchronize()
+    assert_bits_equal(to_host(kt, keys.dtype), oracle.gather(keys, p), "pair keys")
+    assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), "pair values")
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+@pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float32, np.uint16])
+def test_every_tile_config(ak, cfg, dtype):
+    opts = {"tile_config": cfg}
+    for n in (1, 1536, 6145, 200001):
+        keys = synth.random_keys(n, dtype, seed=4000 + n, mode="dups")
+        for desc in (False, True):
+            p = oracle_perm(keys, desc)
+            assert_bits_equal(_run_sort(ak, keys, desc, opts), oracle.gather(keys, p), f"cfg {cfg} n={n}")
+            assert np.array_equal(_run_perm(ak, keys, desc, opts), p.astype(np.uint32))
+
+
+def test_trivial_passes_and_all_equal(ak):
+    # every key equal: all passes trivial; sortperm must be the identity
+    keys = np.full(70000, 7, dtype=np.int64)
+    assert np.array_equal(_run_perm(ak, keys, False), np.arange(70000, dtype=np.uint32))
+    assert np.array_equal(_run_perm(ak, keys, True), np.arange(70000, dtype=np.uint32))
+    # NaNs only, different payloads: input order must survive
+    nan = (np.uint32(0x7FC00000) | (np.arange(5000, dtype=np.uint32) * 7919 % 4093)).view(np.float32)
+    assert_bits_equal(_run_sort(ak, nan, False), nan, "all-NaN sort")
+    # an odd number of moving passes (copy-back): only byte 1 varies
+    k = (synth.splitmix64(5, 30000) % np.uint64(256)).astype(np.uint32) << np.uint32(8)
+    k |= np.uint32(0x11000000)
+    info_keys, u = to_dev(k)
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, k.size, ak.AK_U32), info_keys.device)
+    ak.ak_sort(info_keys, temp=temp, unsigned=u)
+    info = ak.ak_last_info(temp)
+    assert info["radix_passes"] == 1 and info["status"] == 0
+    assert_bits_equal(to_host(info_keys, k.dtype), np.sort(k), "copy-back")
+
+
+def test_special_values_every_dtype(ak):
+    for dt in DTYPES:
+        sv = synth.special_values(dt)
+        keys = np.tile(sv, 300)[: 4000]
+        for desc in (False, True):
+            p = oracle_perm(keys, desc)
+            assert_bits_equal(_run_sort(ak, keys, desc), oracle.gather(keys, p), f"{dt}")
+
+
+def test_unaligned_pointers_take_plain_loads(ak):
+    # key pointer offset by one element: no 16-byte alignment, still exact
+    base = synth.random_keys(100001, np.uint32, seed=77, mode="bits")
+    t, _ = to_dev(base)
+    sub = t[1:]
+    ak.ak_sort(sub, unsigned=True)
+    torch.cuda.synchronize()
+    want = oracle.sort(base[1:])
+    assert_bits_equal(to_host(sub, np.uint32), want, "unaligned")
+    assert to_host(t, np.uint32)[0] == base[0]
+
+
+def test_empty_and_errors(ak):
+    t = torch.empty(0, dtype=torch.float32, device="cuda")
+    ak.ak_sort(t)
+    assert ak.ak_sortperm(t).numel() == 0
+    with pytest.raises(ak.AkError):
+        ak.ak_sort(torch.zeros(10, device="cuda"), temp=torch.empty(16, dtype=torch.uint8, device="cuda"))
+
+
+def test_lookback_timeout_reports_status(ak):
+    """The test hook leaves tile 0 of every pass unowned: tile 1's look-back
+    must give up after timeout_ns and the status word must say so."""
+    keys = synth.random_keys(20000, np.uint32, seed=9, mode="bits")
+    t, u = to_dev(keys)
+    opts = {"timeout_ns": 2_000_000, "debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE}
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, keys.size, ak.AK_U32, options=opts), t.device)
+    ak.ak_sort(t, temp=temp, options=opts, unsigned=u)
+    assert ak.ak_status_check(temp) == 5
+    # the context is still usable and a normal call clears the status
+    ak.ak_sort(t, temp=temp, unsigned=u)
+    assert ak.ak_status_check(temp) == 0
+    assert_bits_equal(to_host(t, np.uint32), np.sort(keys), "after timeout")
+
+
+def test_stream_and_graph_capture(ak):
+    keys = synth.random_keys(300000, np.float32, seed=12, mode="bits")
+    t, _ = to_dev(keys)
+    pristine = t.clone()
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, keys.size, ak.AK_F32), t.device)
+    s = torch.cuda.Stream()
+    ak.ak_sort(t, temp=temp, stream=s)  # warm up (sets kernel attributes outside capture)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ak.ak_sort(t, temp=temp, stream=s)
+    for _ in range(3):
+        t.copy_(pristine)
+        g.replay()
+    torch.cuda.synchronize()
+    assert_bits_equal(to_host(t, np.float32), oracle.sort(keys), "graph replay")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("which", ["i64", "f32"])
+def test_full_size_268M(ak, which):
+    """268,435,456 keys: int64 uniform over all bit patterns and float32 N(0,1)
+    with 0.1% NaN and 0.1% -0.0; sortperm verified by the stable-sortperm
+    properties, then sort compared bit-exactly with keys[perm]."""
+    n = 268_435_456
+    keys = synth.uniform_i64(n, seed=2) if which == "i64" else synth.normal_f32_special(n, seed=3)
+    for desc in (False,):
+        t, u = to_dev(keys)
+        p = ak.ak_sortperm(t, "descending" if desc else "ascending", unsigned=u)
+        torch.cuda.synchronize()
+        perm = to_host(p, np.uint32)
+        del p
+        check_perm_properties(keys, perm, desc)
+        ak.ak_sort(t, "descending" if desc else "ascending", unsigned=u)
+        torch.cuda.synchronize()
+        assert_bits_equal(to_host(t, keys.dtype), keys[perm.astype(np.int64)], "full-size sort")
+        del t
+        torch.cuda.empty_cache()
