@@ -21,17 +21,11 @@ int device_sm_count() {
   return sms;
 }
 
-int radix_tile_keys(int key_bytes, int cfg) {
-  static const int B[3] = {256, 256, 512};
-  static const int I16[3] = {16, 8, 16}, I32[3] = {15, 8, 12}, I64[3] = {10, 6, 8};
-  if (cfg < 0 || cfg > 2) cfg = 0;
-  const int *I = key_bytes == 2 ? I16 : key_bytes == 4 ? I32 : I64;
-  return B[cfg] * I[cfg];
-}
-
-int radix_min_tile_keys(int key_bytes) {
-  int m = radix_tile_keys(key_bytes, 0);
-  for (int c = 1; c < AK_TILE_CONFIGS; ++c) m = m < radix_tile_keys(key_bytes, c) ? m : radix_tile_keys(key_bytes, c);
+// Smallest tile of any configuration for these widths (sizes the look-back
+// arrays so that every configuration fits).
+static int min_tile_keys(int key_bytes, int val_bytes) {
+  int m = tile_keys(key_bytes, val_bytes, 0);
+  for (int c = 1; c < AK_TILE_CONFIGS; ++c) m = m < tile_keys(key_bytes, val_bytes, c) ? m : tile_keys(key_bytes, val_bytes, c);
   return m;
 }
 
@@ -104,9 +98,15 @@ static ak_options resolve_options(const ak_options *opt) {
 
 static cudaError_t radix_dispatch(int key_bytes, const RadixCall &c) {
   switch (key_bytes) {
-    case 2: return radix_launch_u16(c);
-    case 4: return radix_launch_u32(c);
-    default: return radix_launch_u64(c);
+    case 2: return c.kind == KIND_SINT ? radix_launch_u16_sint(c) : radix_launch_u16_uint(c);
+    case 4:
+      return c.kind == KIND_FLOAT  ? radix_launch_u32_float(c)
+             : c.kind == KIND_SINT ? radix_launch_u32_sint(c)
+                                   : radix_launch_u32_uint(c);
+    default:
+      return c.kind == KIND_FLOAT  ? radix_launch_u64_float(c)
+             : c.kind == KIND_SINT ? radix_launch_u64_sint(c)
+                                   : radix_launch_u64_uint(c);
   }
 }
 
@@ -120,7 +120,8 @@ static ak_status run_radix(int op, const void *k_in, void *k_final, const void *
                            size_t temp_bytes, cudaStream_t stream, const ak_options &o) {
   // Look-back arrays are sized for the smallest tile of any configuration, so
   // every configuration the launcher may pick fits.
-  const RadixLayout L = radix_layout(op, n, ki.bytes, val_bytes, radix_min_tile_keys(ki.bytes));
+  const int vb = (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
+  const RadixLayout L = radix_layout(op, n, ki.bytes, val_bytes, min_tile_keys(ki.bytes, vb));
   if (d_temp == nullptr || temp_bytes < L.total) return AK_ERR_WORKSPACE_TOO_SMALL;
   uint8_t *t = static_cast<uint8_t *>(d_temp);
   if (cudaMemsetAsync(t, 0, L.plan, stream) != cudaSuccess) return AK_ERR_CUDA;
@@ -184,7 +185,8 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
   const ak_options o = resolve_options(opt);
   if (op == AK_OP_SORT_SEGMENTED) return AK_ERR_UNSUPPORTED;
   (void)o;
-  *bytes = radix_layout(op, n, ki.bytes, val_bytes, radix_min_tile_keys(ki.bytes)).total;
+  const int vb = (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
+  *bytes = radix_layout(op, n, ki.bytes, val_bytes, min_tile_keys(ki.bytes, vb)).total;
   return AK_OK;
 }
 

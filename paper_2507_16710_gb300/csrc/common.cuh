@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/ak_sort.h"
 
 namespace ak {
@@ -47,6 +49,24 @@ __device__ __forceinline__ U radix_key(U u, int kind, U flip) {
     r = u;
   }
   return U(r ^ flip);
+}
+
+// Same transform with the key kind fixed at compile time (no per-key branches).
+template <int KIND, typename U>
+__device__ __forceinline__ U radix_key_t(U u, U flip) {
+  constexpr U SIGN = U(U(1) << (8 * sizeof(U) - 1));
+  if constexpr (KIND == KIND_FLOAT) {
+    // negative -> ~u, non-negative -> u ^ SIGN: xor with (arithmetic sign mask | SIGN)
+    using S = typename std::make_signed<U>::type;
+    const U neg = U(S(u) >> (8 * sizeof(U) - 1));
+    U r = U(u ^ (neg | SIGN));
+    r = (U(u & U(~SIGN)) > FloatBits<U>::EXP) ? U(~U(0)) : r;
+    return U(r ^ flip);
+  } else if constexpr (KIND == KIND_SINT) {
+    return U(u ^ SIGN ^ flip);
+  } else {
+    return U(u ^ flip);
+  }
 }
 
 template <typename U>

@@ -40,13 +40,36 @@ struct RadixCall {
 
 // Launch the whole sequence (histogram, plan, passes, finish) on c.stream.
 // The header region (status, counters, histogram counts) must be zeroed first.
-cudaError_t radix_launch_u16(const RadixCall &c);
-cudaError_t radix_launch_u32(const RadixCall &c);
-cudaError_t radix_launch_u64(const RadixCall &c);
+// One entry point per key word width and key kind (unsigned/signed/float).
+cudaError_t radix_launch_u16_uint(const RadixCall &c);
+cudaError_t radix_launch_u16_sint(const RadixCall &c);
+cudaError_t radix_launch_u32_uint(const RadixCall &c);
+cudaError_t radix_launch_u32_sint(const RadixCall &c);
+cudaError_t radix_launch_u32_float(const RadixCall &c);
+cudaError_t radix_launch_u64_uint(const RadixCall &c);
+cudaError_t radix_launch_u64_sint(const RadixCall &c);
+cudaError_t radix_launch_u64_float(const RadixCall &c);
 
-// Keys per tile of a tile configuration (for workspace sizing).
-int radix_tile_keys(int key_bytes, int tile_config);
-int radix_min_tile_keys(int key_bytes);
+// Tile shapes of the digit-pass kernel.  Configuration c has CFG_BLOCK[c]
+// threads and stages CFG_STAGES[c] tile buffers of about CFG_BYTES[c] bytes of
+// keys+values each; keys per thread are clamped to [2, 16].  Persistent
+// configurations launch one wave of CTAs that loop over tiles with bulk copies
+// in flight ahead of use; the others launch one CTA per tile.
+constexpr int CFG_BLOCK[3] = {512, 256, 512};
+constexpr int CFG_BYTES[3] = {32768, 16384, 32768};
+constexpr int CFG_STAGES[3] = {1, 1, 2};
+constexpr bool CFG_PERSIST[3] = {false, false, true};
+
+constexpr int tile_items(int key_bytes, int val_bytes, int cfg) {
+  return (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) < 2   ? 2
+         : (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) > 16 ? 16
+                                                                               : CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes));
+}
+constexpr int tile_keys(int key_bytes, int val_bytes, int cfg) {
+  return CFG_BLOCK[cfg] * tile_items(key_bytes, val_bytes, cfg);
+}
+// 64-bit look-back words (n > 2^30) are only built for configuration 0.
+constexpr int effective_cfg(int cfg, bool status_wide) { return status_wide ? 0 : cfg; }
 
 int device_sm_count();
 

@@ -136,60 +136,93 @@ static __global__ void __launch_bounds__(RADIX) plan_kernel(const unsigned long 
 }
 
 // ---------------------------------------------------------------- digit pass
-template <typename U, typename V, int BLOCK, int ITEMS, bool HAS_V>
+// Persistent CTAs walk tiles in increasing id order (ids from an atomic counter).
+// A ring of STAGES shared-memory tile buffers is filled by the bulk-copy engine
+// ahead of use, so loads of later tiles overlap the ranking, look-back and
+// write-out of the current one.  Forward progress of the look-back: every CTA
+// processes the tiles it holds in increasing order, so the holder of the
+// smallest unfinished tile only waits on finished tiles.
+template <typename U, typename V, bool HAS_V, int BLOCK, int ITEMS, int STAGES>
 struct PassSmem {
   static constexpr int TILE = BLOCK * ITEMS;
   static constexpr int NW = BLOCK / 32;
+  static constexpr int HROW = RADIX + 2;  // u16 per warp row: digits + the invalid-key slot
   static constexpr size_t KEYS = size_t(TILE) * sizeof(U);
   static constexpr size_t VALS = HAS_V ? size_t(TILE) * sizeof(V) : 0;
-  static constexpr size_t OFF_V = KEYS;                                  // 16-aligned
-  static constexpr size_t OFF_HIST = (OFF_V + VALS + 15) / 16 * 16;
-  static constexpr size_t OFF_DELTA = OFF_HIST + size_t(NW) * RADIX * 4;  // int64[RADIX]
-  static constexpr size_t OFF_START = OFF_DELTA + RADIX * 8;              // u32[RADIX]
-  static constexpr size_t OFF_SCR = OFF_START + RADIX * 4;                // u32[NW+1]
-  static constexpr size_t OFF_BAR = (OFF_SCR + (NW + 1) * 4 + 15) / 16 * 16;
-  static constexpr size_t OFF_TILE = OFF_BAR + 8;
-  static constexpr size_t BYTES = OFF_TILE + 8;
+  static constexpr size_t STAGE = (KEYS + VALS + 127) / 128 * 128;
+  static constexpr size_t OFF_OUT = STAGE * STAGES;  // the tile in digit order
+  static constexpr size_t OFF_HIST = OFF_OUT + STAGE;
+  static constexpr size_t OFF_MASK = (OFF_HIST + size_t(NW) * HROW * 2 + 15) / 16 * 16;    // u32[NW][HROW]
+  static constexpr size_t OFF_KPTR = OFF_MASK + size_t(NW) * HROW * 4;                      // u64[RADIX]
+  static constexpr size_t OFF_VPTR = OFF_KPTR + RADIX * 8;                                  // u64[RADIX]
+  static constexpr size_t OFF_SCR = OFF_VPTR + (HAS_V ? RADIX * 8 : 0);                     // u32[NW+1]
+  static constexpr size_t OFF_BAR = (OFF_SCR + (NW + 1) * 4 + 15) / 16 * 16;             // u64[STAGES]
+  static constexpr size_t OFF_TILE = OFF_BAR + 8 * STAGES;                                // u32[STAGES]
+  static constexpr size_t OFF_FLAG = OFF_TILE + 4 * STAGES;                               // u32
+  static constexpr size_t BYTES = OFF_FLAG + 16;
+  static_assert(TILE < 65536, "warp bases are u16");
 };
 
-template <typename U, typename V, typename S, int BLOCK, int ITEMS, bool HAS_V>
-__global__ void __launch_bounds__(BLOCK) onesweep_pass(PassArgs<U, V> a) {
-  using L = PassSmem<U, V, BLOCK, ITEMS, HAS_V>;
+constexpr int LOOKBACK_WINDOW = 8;  // predecessor words probed per round trip
+
+// Lanes of the warp holding the same digit.  AK_WARP_MATCH selects match.any
+// (0), a bit-sliced match from ballots (1: the peers of a lane are the lanes
+// agreeing on every bit; 9 bits when the padding digit RADIX can occur), or a
+// shared-memory mask per digit that every lane ORs its bit into (2, default:
+// fixed cost, no per-bit work).
+#ifndef AK_WARP_MATCH
+#define AK_WARP_MATCH 2
+#endif
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d, bool nine_bits) {
+#if AK_WARP_MATCH == 0
+  (void)nine_bits;
+  return __match_any_sync(0xffffffffu, d);
+#else
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+    peers &= ((d >> b) & 1u) ? bal : ~bal;
+  }
+  if (nine_bits) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, (d >> 8) & 1u);
+    peers &= ((d >> 8) & 1u) ? bal : ~bal;
+  }
+  return peers;
+#endif
+}
+
+template <typename U, typename V, bool HAS_V, int KIND, typename S, int BLOCK, int ITEMS, int STAGES,
+          bool PERSIST>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U, V> a) {
+  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS, STAGES>;
   constexpr int TILE = L::TILE;
   constexpr int NW = L::NW;
+  constexpr int HROW = L::HROW;
   static_assert(BLOCK >= RADIX, "one digit per thread in the look-back");
+  static_assert(PERSIST ? STAGES >= 2 : STAGES == 1, "stage ring");
   extern __shared__ __align__(128) uint8_t smem[];
-  U *sk = reinterpret_cast<U *>(smem);
-  V *sv = reinterpret_cast<V *>(smem + L::OFF_V);
-  uint32_t *whist = reinterpret_cast<uint32_t *>(smem + L::OFF_HIST);
-  long long *s_delta = reinterpret_cast<long long *>(smem + L::OFF_DELTA);
-  uint32_t *s_start = reinterpret_cast<uint32_t *>(smem + L::OFF_START);
+  uint16_t *whist = reinterpret_cast<uint16_t *>(smem + L::OFF_HIST);
+  uint32_t *wmask = reinterpret_cast<uint32_t *>(smem + L::OFF_MASK);
+  // per digit: address of the destination of tile position 0 (base + delta,
+  // kept as an integer; base + delta + i is inside the buffer for every key)
+  unsigned long long *s_kptr = reinterpret_cast<unsigned long long *>(smem + L::OFF_KPTR);
+  unsigned long long *s_vptr = reinterpret_cast<unsigned long long *>(smem + L::OFF_VPTR);
   uint32_t *s_scr = reinterpret_cast<uint32_t *>(smem + L::OFF_SCR);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::OFF_BAR);
   uint32_t *s_tile = reinterpret_cast<uint32_t *>(smem + L::OFF_TILE);
+  uint32_t *s_flag = reinterpret_cast<uint32_t *>(smem + L::OFF_FLAG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // The next pass's look-back words: each launch of this kernel has exactly
-  // num_tiles CTAs, so block b clears row b.
+  // Clear the next pass's look-back rows (the grid covers rows blockIdx.x + k*gridDim.x).
   if (a.status_next) {
-    S *nx = reinterpret_cast<S *>(a.status_next) + int64_t(blockIdx.x) * RADIX;
-    for (int i = tid; i < RADIX; i += BLOCK) nx[i] = S(0);
+    S *nx = reinterpret_cast<S *>(a.status_next);
+    for (int64_t r = blockIdx.x; r < a.num_tiles; r += gridDim.x)
+      for (int i = tid; i < RADIX; i += BLOCK) nx[r * RADIX + i] = S(0);
   }
   const uint32_t q = a.plan->q[a.pass];
   if (q == INACTIVE) return;
   const uint32_t m = a.plan->m;
-
-  for (int i = tid; i < NW * RADIX; i += BLOCK) whist[i] = 0;
-  if (tid == 0) {
-    *s_tile = atomicAdd(&a.hdr->tile_counter[a.pass], 1u) + (a.debug_skip ? 1u : 0u);
-    mbar_init(bar, 1);
-  }
-  __syncthreads();
-  const int64_t tile = *s_tile;
-  __syncthreads();  // s_tile is reused below as the bulk-copy verdict
-  if (tile >= a.num_tiles) return;  // only under the test hook
-  const int64_t base = tile * TILE;
-  const int tile_n = int((a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE));
 
   // source / destination of this active pass
   const U *ksrc;
@@ -213,142 +246,232 @@ __global__ void __launch_bounds__(BLOCK) onesweep_pass(PassArgs<U, V> a) {
     if (q == 0) gen_index = true;
     else vsrc = vbuf(q - 1);
   }
-
-  // ---- stage the tile in shared memory
   const bool load_v = HAS_V && !gen_index;
-  const bool bulk = (tile_n == TILE) &&
-                    ((reinterpret_cast<uintptr_t>(ksrc + base) & 15) == 0) &&
-                    (!load_v || ((reinterpret_cast<uintptr_t>(vsrc + base) & 15) == 0));
-  if (bulk) {
-    // one thread issues and waits (bounded); the verdict is shared so that the
-    // whole CTA takes the same branch
-    if (tid == 0) {
-      mbar_expect_tx(bar, uint32_t(L::KEYS + (load_v ? L::VALS : 0)));
-      bulk_g2s(sk, ksrc + base, uint32_t(L::KEYS), bar);
-      if (load_v) bulk_g2s(sv, vsrc + base, uint32_t(L::VALS), bar);
-      uint32_t ok = mbar_wait_bounded(bar, 0, a.timeout_ns) ? 1u : 0u;
-      if (!ok) {
+  const bool aligned = ((reinterpret_cast<uintptr_t>(ksrc) & 15) == 0) &&
+                       (!load_v || ((reinterpret_cast<uintptr_t>(vsrc) & 15) == 0));
+  const int64_t full_tiles = a.n / TILE;  // tiles that need no bounds checks
+  auto is_bulk = [&](int64_t t) { return aligned && t < full_tiles; };
+  const uint32_t tx_bytes = uint32_t(L::KEYS + (load_v ? L::VALS : 0));
+  auto stage_keys = [&](int s) { return reinterpret_cast<U *>(smem + size_t(s) * L::STAGE); };
+  auto stage_vals = [&](int s) { return reinterpret_cast<V *>(smem + size_t(s) * L::STAGE + L::KEYS); };
+  auto next_tile = [&]() -> int64_t {
+    return int64_t(atomicAdd(&a.hdr->tile_counter[a.pass], 1u)) + (a.debug_skip ? 1 : 0);
+  };
+  auto issue = [&](int s, int64_t t) {  // thread 0 only
+    if (t < a.num_tiles && is_bulk(t)) {
+      mbar_expect_tx(&bar[s], tx_bytes);
+      bulk_g2s(stage_keys(s), ksrc + t * TILE, uint32_t(L::KEYS), &bar[s]);
+      if (load_v) bulk_g2s(stage_vals(s), vsrc + t * TILE, uint32_t(L::VALS), &bar[s]);
+    }
+  };
+
+  for (int i = tid; i < NW * HROW; i += BLOCK) wmask[i] = 0u;
+  uint32_t phase_bits = 0;  // thread 0: parity to wait for, per stage
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      const int64_t t = next_tile();
+      s_tile[s] = uint32_t(t < a.num_tiles ? t : a.num_tiles);
+      issue(s, t);
+    }
+    *s_flag = 0;
+    // the first stage must be resident before the loop starts
+    const int64_t t0 = s_tile[0];
+    if (t0 < a.num_tiles && is_bulk(t0)) {
+      if (!mbar_wait_bounded(&bar[0], 0, a.timeout_ns)) {
         set_error(a.hdr, AK_ERR_TIMEOUT);
-        mbar_wait_bounded(bar, 0, a.timeout_ns);  // let the copy land before exiting
+        *s_flag = 1;
       }
-      *s_tile = ok;  // tile id already read by every thread
+      phase_bits ^= 1u;
     }
-    __syncthreads();
-    if (*s_tile == 0) return;
-    while (!mbar_try_wait(bar, 0)) {
-    }  // phase already complete: observes the async-proxy writes
-  } else {
-    for (int i = tid; i < tile_n; i += BLOCK) sk[i] = ksrc[base + i];
-    if (load_v)
-      for (int i = tid; i < tile_n; i += BLOCK) sv[i] = vsrc[base + i];
-    __syncthreads();
   }
+  __syncthreads();
 
-  // ---- warp multisplit ranking (warp-striped: item i of lane l is at wbase+32i+l)
   const int shift = a.pass * RADIX_BITS;
-  const int wbase = warp * 32 * ITEMS;
-  U keys[ITEMS];
-  uint32_t rank[ITEMS];
-  V vals[HAS_V ? ITEMS : 1];
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int idx = wbase + i * 32 + lane;
-    keys[i] = (idx < tile_n) ? sk[idx] : U(0);
-    if (HAS_V) {
-      if (gen_index) vals[i] = V(base + idx);
-      else vals[i] = (idx < tile_n) ? sv[idx] : V(0);
-    }
-  }
-  uint32_t *wh = whist + warp * RADIX;
   const uint32_t lt_mask = lanemask_lt();
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int idx = wbase + i * 32 + lane;
-    const bool valid = idx < tile_n;
-    const uint32_t d = valid ? digit_of(radix_key(keys[i], a.kind, a.flip), shift) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const int leader = 31 - __clz(peers);
-    uint32_t cnt = 0;
-    if (lane == leader && valid) {
-      cnt = wh[d];
-      wh[d] = cnt + __popc(peers);
-    }
-    __syncwarp();
-    cnt = __shfl_sync(0xffffffffu, cnt, leader);
-    rank[i] = cnt + __popc(peers & lt_mask);
-  }
-  __syncthreads();
-
-  // ---- per-digit tile counts, publish, tile-local digit starts
-  uint32_t my_cnt = 0;
+  const uint32_t gt_mask = ~(lt_mask | (1u << lane));
+  uint16_t *wh = whist + warp * HROW;
+  uint32_t *wm = wmask + warp * HROW;
   S *st = reinterpret_cast<S *>(a.status_cur);
-  if (tid < RADIX) {
-    uint32_t run = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      const uint32_t c = whist[w * RADIX + tid];
-      whist[w * RADIX + tid] = run;
-      run += c;
-    }
-    my_cnt = run;
-    const S word = (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt);
-    st_relaxed(&st[tile * RADIX + tid], word);
-  }
-  uint32_t total;
-  const uint32_t start = block_exclusive_scan<BLOCK>(tid < RADIX ? my_cnt : 0u, s_scr, &total);
-  if (tid < RADIX) s_start[tid] = start;
-  __syncthreads();
 
-  // ---- scatter into shared memory in digit order (all reads of sk/sv are done)
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int idx = wbase + i * 32 + lane;
-    if (idx < tile_n) {
-      const uint32_t d = digit_of(radix_key(keys[i], a.kind, a.flip), shift);
-      const uint32_t pos = s_start[d] + wh[d] + rank[i];
-      sk[pos] = keys[i];
-      if (HAS_V) sv[pos] = vals[i];
+  for (int it = 0;; ++it) {
+    const int s = it % STAGES;
+    const int64_t tile = s_tile[s];
+    if (tile >= a.num_tiles || *s_flag) break;  // uniform: read after a barrier
+    const int64_t base = tile * TILE;
+    const int tile_n = int((a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE));
+    U *sk = stage_keys(s);
+    V *sv = stage_vals(s);
+    if (!is_bulk(tile)) {  // ragged last tile or unaligned source: plain loads
+      for (int i = tid; i < tile_n; i += BLOCK) sk[i] = ksrc[base + i];
+      if (load_v)
+        for (int i = tid; i < tile_n; i += BLOCK) sv[i] = vsrc[base + i];
+      __syncthreads();
     }
-  }
 
-  // ---- decoupled look-back: exclusive prefix of this digit over earlier tiles
-  if (tid < RADIX) {
-    unsigned long long excl = 0;
-    if (tile > 0) {
-      int64_t j = tile - 1;
-      uint64_t t0 = 0;
-      uint32_t spins = 0;
-      while (true) {
-        const S v = ld_relaxed(&st[j * RADIX + tid]);
-        const uint32_t flag = uint32_t(v >> StatusWord<S>::SHIFT);
-        if (flag == 0) {
-          if ((++spins & 63u) == 0) {
-            const uint64_t now = globaltimer_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > a.timeout_ns) {
-              set_error(a.hdr, AK_ERR_TIMEOUT);
-              break;
-            }
-          }
-          continue;
-        }
-        excl += (unsigned long long)(v & StatusWord<S>::MASK);
-        if (flag == FLAG_INC || j == 0) break;
-        --j;
+    // ---- warp multisplit ranking (item i of lane l sits at wbase + 32 i + l)
+    for (int i = lane; i < HROW / 2; i += 32) reinterpret_cast<uint32_t *>(wh)[i] = 0u;
+    __syncwarp();
+    const int wbase = warp * 32 * ITEMS;
+    uint32_t dr[ITEMS];  // rank << 9 | digit (digit RADIX marks a padding slot)
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int idx = wbase + i * 32 + lane;
+      dr[i] = (idx < tile_n) ? digit_of(radix_key_t<KIND>(sk[idx], a.flip), shift) : uint32_t(RADIX);
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const uint32_t d = dr[i];
+#if AK_WARP_MATCH == 2
+      atomicOr(&wm[d], 1u << lane);
+      __syncwarp();
+      const uint32_t peers = wm[d];
+      const uint32_t cnt = wh[d];  // running count of this digit in the warp
+      __syncwarp();
+      if ((peers & gt_mask) == 0) {  // highest lane of the group updates and resets
+        wh[d] = uint16_t(cnt + __popc(peers));
+        wm[d] = 0u;
       }
-      const S word = (S(FLAG_INC) << StatusWord<S>::SHIFT) | S(excl + my_cnt);
+      __syncwarp();
+#else
+      const uint32_t peers = warp_peers(d, tile_n != TILE);
+      const bool leader = (peers & gt_mask) == 0;  // highest lane of the group
+      uint32_t cnt = 0;
+      if (leader) cnt = wh[d];
+      if (leader) wh[d] = uint16_t(cnt + __popc(peers));
+      cnt = __shfl_sync(0xffffffffu, cnt, 31 - __clz(peers));
+      __syncwarp();
+#endif
+      dr[i] = ((cnt + __popc(peers & lt_mask)) << 9) | d;
+    }
+    __syncthreads();  // A: every warp row complete
+
+    // ---- per-digit tile counts, publish, warp bases = tile digit start + earlier warps
+    uint32_t my_cnt = 0;
+    if (tid < RADIX) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = whist[w * HROW + tid];
+        whist[w * HROW + tid] = uint16_t(run);
+        run += c;
+      }
+      my_cnt = run;
+      const S word = (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt);
       st_relaxed(&st[tile * RADIX + tid], word);
     }
-    s_delta[tid] = (long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)s_start[tid];
-  }
-  __syncthreads();
+    uint32_t total;
+    const uint32_t start = block_exclusive_scan<BLOCK>(tid < RADIX ? my_cnt : 0u, s_scr, &total);
+    if (tid < RADIX) {
+#pragma unroll
+      for (int w = 0; w < NW; ++w) whist[w * HROW + tid] = uint16_t(whist[w * HROW + tid] + start);
+    }
+    __syncthreads();  // B
 
-  // ---- write the tile out: consecutive threads store consecutive keys of a digit run
-  for (int i = tid; i < tile_n; i += BLOCK) {
-    const U k = sk[i];
-    const long long g = s_delta[digit_of(radix_key(k, a.kind, a.flip), shift)] + i;
-    if (write_keys) kdst[g] = k;
-    if (HAS_V) vdst[g] = sv[i];
+    // ---- scatter the stage into the output buffer in digit order
+    U *ok = reinterpret_cast<U *>(smem + L::OFF_OUT);
+    V *ov = reinterpret_cast<V *>(smem + L::OFF_OUT + L::KEYS);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const uint32_t d = dr[i] & 511u;
+      if (d < RADIX) {
+        const int idx = wbase + i * 32 + lane;
+        const uint32_t pos = uint32_t(wh[d]) + (dr[i] >> 9);
+        ok[pos] = sk[idx];
+        if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
+      }
+    }
+
+    // ---- decoupled look-back over a window of predecessors per probe
+    if (tid < RADIX) {
+      unsigned long long excl = 0;
+      if (tile > 0) {
+        int64_t j = tile - 1;
+        uint64_t t0 = 0;
+        uint32_t spins = 0;
+        bool done = false;
+        while (!done) {
+          S w4[LOOKBACK_WINDOW];
+#pragma unroll
+          for (int k = 0; k < LOOKBACK_WINDOW; ++k)
+            w4[k] = (j - k >= 0) ? ld_relaxed(&st[(j - k) * RADIX + tid]) : S(0);
+          int used = 0;
+#pragma unroll
+          for (int k = 0; k < LOOKBACK_WINDOW; ++k) {
+            if (done || used != k) break;
+            const uint32_t flag = uint32_t(w4[k] >> StatusWord<S>::SHIFT);
+            if (flag == 0) break;
+            excl += (unsigned long long)(w4[k] & StatusWord<S>::MASK);
+            ++used;
+            if (flag == FLAG_INC || j - k == 0) done = true;
+          }
+          j -= used;
+          if (!done && used == 0) {
+            __nanosleep(64);  // predecessor not published yet: yield issue slots
+            if ((++spins & 31u) == 0) {
+              const uint64_t now = globaltimer_ns();
+              if (t0 == 0) t0 = now;
+              else if (now - t0 > a.timeout_ns) {
+                set_error(a.hdr, AK_ERR_TIMEOUT);
+                done = true;
+              }
+            }
+          }
+        }
+        const S word = (S(FLAG_INC) << StatusWord<S>::SHIFT) | S(excl + my_cnt);
+        st_relaxed(&st[tile * RADIX + tid], word);
+      }
+      const long long delta = (long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start;
+      s_kptr[tid] = reinterpret_cast<unsigned long long>(kdst) + (unsigned long long)(delta * (long long)sizeof(U));
+      if (HAS_V)
+        s_vptr[tid] = reinterpret_cast<unsigned long long>(vdst) + (unsigned long long)(delta * (long long)sizeof(V));
+    }
+    __syncthreads();  // C
+
+    // ---- write the tile out: consecutive threads store consecutive keys of a digit run
+    if (tile_n == TILE) {
+#pragma unroll 4
+      for (int r = 0; r < ITEMS; ++r) {
+        const int i = r * BLOCK + tid;
+        const U k = ok[i];
+        const uint32_t d = digit_of(radix_key_t<KIND>(k, a.flip), shift);
+        if (write_keys) reinterpret_cast<U *>(s_kptr[d])[i] = k;
+        if (HAS_V) reinterpret_cast<V *>(s_vptr[d])[i] = ov[i];
+      }
+    } else {
+      for (int i = tid; i < tile_n; i += BLOCK) {
+        const U k = ok[i];
+        const uint32_t d = digit_of(radix_key_t<KIND>(k, a.flip), shift);
+        if (write_keys) reinterpret_cast<U *>(s_kptr[d])[i] = k;
+        if (HAS_V) reinterpret_cast<V *>(s_vptr[d])[i] = ov[i];
+      }
+    }
+
+    if (!PERSIST) break;  // one tile per CTA
+
+    // ---- make the next stage resident, then recycle this one
+    if (tid == 0) {
+      const int sn = (it + 1) % STAGES;
+      const int64_t tn = s_tile[sn];
+      if (tn < a.num_tiles && is_bulk(tn)) {
+        if (!mbar_wait_bounded(&bar[sn], (phase_bits >> sn) & 1u, a.timeout_ns)) {
+          set_error(a.hdr, AK_ERR_TIMEOUT);
+          *s_flag = 1;
+        }
+        phase_bits ^= 1u << sn;
+      }
+    }
+    __syncthreads();  // D: stage s is free, the next stage is resident
+    if (tid == 0 && !*s_flag) {
+      const int64_t t = next_tile();
+      s_tile[s] = uint32_t(t < a.num_tiles ? t : a.num_tiles);
+      issue(s, t);
+    }
+    // s_tile[s] is next read STAGES-1 iterations later, after barriers
+  }
+  // a copy left in flight by a timed-out wait must land before the CTA exits
+  if (tid == 0 && *s_flag) {
+    for (int s = 0; s < STAGES; ++s) mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u, a.timeout_ns);
   }
 }
 

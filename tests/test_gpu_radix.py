@@ -146,7 +146,9 @@ def test_lookback_timeout_reports_status(ak):
     temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, keys.size, ak.AK_U32, options=opts), t.device)
     ak.ak_sort(t, temp=temp, options=opts, unsigned=u)
     assert ak.ak_status_check(temp) == 5
-    # the context is still usable and a normal call clears the status
+    # the context is still usable and a normal call clears the status (the
+    # failed call left unspecified keys behind, so restore them first)
+    t.copy_(to_dev(keys)[0])
     ak.ak_sort(t, temp=temp, unsigned=u)
     assert ak.ak_status_check(temp) == 0
     assert_bits_equal(to_host(t, np.uint32), np.sort(keys), "after timeout")
