@@ -154,8 +154,9 @@ ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak
  * s < nseg, is sorted on its own, all in one batch of launches.  d_offsets is a
  * device array of nseg+1 int64 values, non-decreasing, off[0] = 0 and
  * off[nseg] = n.  The offsets are read on the device only; offsets that break
- * these rules give an unspecified key order (never an out-of-bounds access:
- * every offset is clamped to [0, n]).
+ * these rules leave the keys of the affected segments unspecified (never an
+ * out-of-bounds access: every offset is clamped to [0, n]).  n and nseg above
+ * 2^32 - 1 return AK_ERR_UNSUPPORTED.
  */
 ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg, int64_t n,
                             ak_dtype kd, ak_order order, void *d_temp, size_t temp_bytes,

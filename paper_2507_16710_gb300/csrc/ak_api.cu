@@ -110,6 +110,106 @@ static cudaError_t radix_dispatch(int key_bytes, const RadixCall &c) {
   }
 }
 
+static cudaError_t seg_dispatch(int key_bytes, const SegCall &c) {
+  switch (key_bytes) {
+    case 2: return c.kind == KIND_SINT ? seg_launch_u16_sint(c) : seg_launch_u16_uint(c);
+    case 4:
+      return c.kind == KIND_FLOAT  ? seg_launch_u32_float(c)
+             : c.kind == KIND_SINT ? seg_launch_u32_sint(c)
+                                   : seg_launch_u32_uint(c);
+    default:
+      return c.kind == KIND_FLOAT  ? seg_launch_u64_float(c)
+             : c.kind == KIND_SINT ? seg_launch_u64_sint(c)
+                                   : seg_launch_u64_uint(c);
+  }
+}
+
+// Workspace of the segmented / one-launch block path.
+struct SegLayout {
+  size_t hdr, counters, order, alt_k, alt_v, key_copy, total;
+};
+
+static SegLayout seg_layout(int op, int64_t n, int64_t nseg, int key_bytes, int vb) {
+  SegLayout L{};
+  size_t off = 0;
+  L.hdr = off;
+  off += align256(sizeof(DevHeader));
+  L.counters = off;
+  off += 256;
+  L.order = off;
+  off += align256(size_t(nseg > 0 ? nseg : 1) * 4);
+  // segments above the shared capacity use a workspace copy
+  L.alt_k = off;
+  off += align256(size_t(n) * key_bytes);
+  L.alt_v = off;
+  off += align256(size_t(n) * vb);
+  if (op == AK_OP_SORTPERM) {  // the keys are read-only: sort a copy
+    L.key_copy = off;
+    off += align256(size_t(n) * key_bytes);
+  }
+  L.total = off;
+  return L;
+}
+
+__global__ void iota_u32_kernel(uint32_t *p, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = uint32_t(i);
+}
+
+// Which path serves a sort/sortperm/pairs call.
+static int choose_path(int op, int64_t n, int key_bytes, int vb, const ak_options &o) {
+  if (o.path == AK_PATH_RADIX || o.path == AK_PATH_BLOCK) return o.path;
+  (void)op;
+  return n <= seg_cap(key_bytes, vb) ? AK_PATH_BLOCK : AK_PATH_RADIX;
+}
+
+static int value_bytes(int op, int val_bytes) {
+  return (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
+}
+
+static size_t temp_for(int op, int64_t n, int key_bytes, int val_bytes, int64_t nseg, const ak_options &o) {
+  const int vb = value_bytes(op, val_bytes);
+  if (op == AK_OP_SORT_SEGMENTED) return seg_layout(op, n, nseg, key_bytes, 0).total;
+  if (choose_path(op, n, key_bytes, vb, o) == AK_PATH_BLOCK) return seg_layout(op, n, 1, key_bytes, vb).total;
+  return radix_layout(op, n, key_bytes, val_bytes, min_tile_keys(key_bytes, vb)).total;
+}
+
+// Segmented sort, or the one-launch block sort of a single segment (off NULL).
+static ak_status run_seg(int op, void *keys, const int64_t *off, int64_t nseg, int64_t n, const void *k_in,
+                         void *vals, int val_bytes, const KeyInfo &ki, int order, void *d_temp, size_t temp_bytes,
+                         cudaStream_t stream) {
+  const int vb = value_bytes(op, val_bytes);
+  const SegLayout L = seg_layout(op, n, off ? nseg : 1, ki.bytes, vb);
+  if (d_temp == nullptr || temp_bytes < L.total) return AK_ERR_WORKSPACE_TOO_SMALL;
+  uint8_t *t = static_cast<uint8_t *>(d_temp);
+  if (cudaMemsetAsync(t, 0, L.order, stream) != cudaSuccess) return AK_ERR_CUDA;
+  void *sort_keys = keys;
+  if (op == AK_OP_SORTPERM) {
+    sort_keys = t + L.key_copy;
+    if (cudaMemcpyAsync(sort_keys, k_in, size_t(n) * ki.bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+      return AK_ERR_CUDA;
+    const int g = int((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    iota_u32_kernel<<<g, 256, 0, stream>>>(static_cast<uint32_t *>(vals), n);
+  }
+  SegCall c{};
+  c.keys = sort_keys;
+  c.vals = vals;
+  c.alt_k = t + L.alt_k;
+  c.alt_v = t + L.alt_v;
+  c.val_bytes = vb;
+  c.off = off;
+  c.nseg = off ? nseg : 1;
+  c.n = n;
+  c.kind = ki.kind;
+  c.descending = order == AK_DESCENDING;
+  c.order = reinterpret_cast<uint32_t *>(t + L.order);
+  c.counters = reinterpret_cast<uint32_t *>(t + L.counters);
+  c.hdr = reinterpret_cast<DevHeader *>(t + L.hdr);
+  c.path_tag = AK_PATH_BLOCK;
+  c.stream = stream;
+  return seg_dispatch(ki.bytes, c) == cudaSuccess ? AK_OK : AK_ERR_CUDA;
+}
+
 static bool valid_order(int order) { return order == AK_ASCENDING || order == AK_DESCENDING; }
 
 static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -183,10 +283,7 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
     return AK_ERR_INVALID_ARG;
   if (op == AK_OP_SORT_SEGMENTED && nseg < 0) return AK_ERR_INVALID_ARG;
   const ak_options o = resolve_options(opt);
-  if (op == AK_OP_SORT_SEGMENTED) return AK_ERR_UNSUPPORTED;
-  (void)o;
-  const int vb = (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
-  *bytes = radix_layout(op, n, ki.bytes, val_bytes, min_tile_keys(ki.bytes, vb)).total;
+  *bytes = temp_for(op, n, ki.bytes, val_bytes, nseg, o);
   return AK_OK;
 }
 
@@ -198,8 +295,10 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_
   if (!d_keys || !aligned(d_keys, ki.bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
   const ak_options o = resolve_options(opt);
-  return run_radix(AK_OP_SORT, d_keys, d_keys, nullptr, nullptr, 0, n, ki, order, d_temp, temp_bytes,
-                   reinterpret_cast<cudaStream_t>(stream), o);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (choose_path(AK_OP_SORT, n, ki.bytes, 0, o) == AK_PATH_BLOCK)
+    return run_seg(AK_OP_SORT, d_keys, nullptr, 1, n, nullptr, nullptr, 0, ki, order, d_temp, temp_bytes, st);
+  return run_radix(AK_OP_SORT, d_keys, d_keys, nullptr, nullptr, 0, n, ki, order, d_temp, temp_bytes, st, o);
 }
 
 ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
@@ -211,8 +310,10 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
   if (!d_keys || !d_perm || !aligned(d_keys, ki.bytes) || !aligned(d_perm, 4)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
   const ak_options o = resolve_options(opt);
-  return run_radix(AK_OP_SORTPERM, d_keys, nullptr, nullptr, d_perm, 4, n, ki, order, d_temp, temp_bytes,
-                   reinterpret_cast<cudaStream_t>(stream), o);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (choose_path(AK_OP_SORTPERM, n, ki.bytes, 4, o) == AK_PATH_BLOCK)
+    return run_seg(AK_OP_SORTPERM, nullptr, nullptr, 1, n, d_keys, d_perm, 4, ki, order, d_temp, temp_bytes, st);
+  return run_radix(AK_OP_SORTPERM, d_keys, nullptr, nullptr, d_perm, 4, n, ki, order, d_temp, temp_bytes, st, o);
 }
 
 ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak_dtype kd, ak_order order,
@@ -224,16 +325,26 @@ ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak
   if (!d_keys || !d_vals || !aligned(d_keys, ki.bytes) || !aligned(d_vals, val_bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
   const ak_options o = resolve_options(opt);
-  return run_radix(AK_OP_SORT_PAIRS, d_keys, d_keys, d_vals, d_vals, val_bytes, n, ki, order, d_temp,
-                   temp_bytes, reinterpret_cast<cudaStream_t>(stream), o);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (choose_path(AK_OP_SORT_PAIRS, n, ki.bytes, val_bytes, o) == AK_PATH_BLOCK)
+    return run_seg(AK_OP_SORT_PAIRS, d_keys, nullptr, 1, n, nullptr, d_vals, val_bytes, ki, order, d_temp,
+                   temp_bytes, st);
+  return run_radix(AK_OP_SORT_PAIRS, d_keys, d_keys, d_vals, d_vals, val_bytes, n, ki, order, d_temp, temp_bytes,
+                   st, o);
 }
 
 ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg, int64_t n, ak_dtype kd,
                             ak_order order, void *d_temp, size_t temp_bytes, ak_stream_t stream,
                             const ak_options *opt) {
-  (void)d_keys; (void)d_offsets; (void)nseg; (void)n; (void)kd; (void)order;
-  (void)d_temp; (void)temp_bytes; (void)stream; (void)opt;
-  return AK_ERR_UNSUPPORTED;
+  KeyInfo ki;
+  if (n < 0 || nseg < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  if (n == 0 || nseg == 0) return AK_OK;
+  if (n > int64_t(0xFFFFFFFFll) || nseg > int64_t(0xFFFFFFFFll)) return AK_ERR_UNSUPPORTED;
+  if (!d_keys || !d_offsets || !aligned(d_keys, ki.bytes) || !aligned(d_offsets, 8)) return AK_ERR_INVALID_ARG;
+  if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
+  (void)opt;
+  return run_seg(AK_OP_SORT_SEGMENTED, d_keys, d_offsets, nseg, n, nullptr, nullptr, 0, ki, order, d_temp,
+                 temp_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 ak_status ak_status_check(const void *d_temp, ak_stream_t stream) {

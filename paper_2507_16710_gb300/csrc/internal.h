@@ -71,6 +71,32 @@ constexpr int tile_keys(int key_bytes, int val_bytes, int cfg) {
 // 64-bit look-back words (n > 2^30) are only built for configuration 0.
 constexpr int effective_cfg(int cfg, bool status_wide) { return status_wide ? 0 : cfg; }
 
+// One segmented sort (or a single segment when off == NULL) on device buffers.
+struct SegCall {
+  void *keys, *vals;       // in place; vals NULL for keys only
+  void *alt_k, *alt_v;     // workspace regions of n elements (segments above the shared capacity)
+  int val_bytes;           // 0 = keys only
+  const int64_t *off;      // nseg + 1 device offsets, or NULL for one segment [0, n)
+  int64_t nseg, n;
+  int kind, descending;
+  uint32_t *order;         // nseg work-order entries (workspace)
+  uint32_t *counters;      // 2 zeroed counters (workspace)
+  DevHeader *hdr;          // zeroed header (work counter)
+  int path_tag;            // written to ak_info.path
+  cudaStream_t stream;
+};
+// Shared-memory capacity (elements) of one segment buffer: about 24 KB of
+// keys+values, a multiple of 32 elements.
+constexpr int seg_cap(int key_bytes, int val_bytes) { return (24576 / (key_bytes + val_bytes)) / 32 * 32; }
+cudaError_t seg_launch_u16_uint(const SegCall &c);
+cudaError_t seg_launch_u16_sint(const SegCall &c);
+cudaError_t seg_launch_u32_uint(const SegCall &c);
+cudaError_t seg_launch_u32_sint(const SegCall &c);
+cudaError_t seg_launch_u32_float(const SegCall &c);
+cudaError_t seg_launch_u64_uint(const SegCall &c);
+cudaError_t seg_launch_u64_sint(const SegCall &c);
+cudaError_t seg_launch_u64_float(const SegCall &c);
+
 int device_sm_count();
 
 }  // namespace ak

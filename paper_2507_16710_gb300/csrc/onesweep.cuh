@@ -161,6 +161,9 @@ struct PassSmem {
   static constexpr size_t OFF_FLAG = OFF_TILE + 4 * STAGES;                               // u32
   static constexpr size_t BYTES = OFF_FLAG + 16;
   static_assert(TILE < 65536, "warp bases are u16");
+  static_assert(KEYS % 16 == 0 && STAGE % 128 == 0 && OFF_MASK % 16 == 0 && OFF_KPTR % 8 == 0 &&
+                    OFF_BAR % 8 == 0,
+                "shared-memory arrays aligned to their element size (bulk copies: 16 bytes)");
 };
 
 constexpr int LOOKBACK_WINDOW = 8;  // predecessor words probed per round trip

@@ -1,0 +1,396 @@
+// segsort.cuh -- segmented sort: many independent CSR segments in one
+// persistent launch (and the one-launch small-n sort, a single segment).
+//
+// classify_kernel  builds the work order: segments above the shared-memory
+//                  capacity first (they take longest), then the rest
+// segsort_kernel   persistent CTAs pop segments from a device work counter.
+//   * L <= CAP: the segment is loaded into shared memory; the radix bits that
+//     vary inside it are found (OR of r ^ r0); LSD passes over only those bits
+//     run between two shared buffers, chunk by chunk with stable warp ranks and
+//     running digit offsets; the result is written back once.
+//   * L > CAP: one stable MSD pass through global memory on the top 8 varying
+//     bits (workspace copy of the segment), then each of the 256 buckets is
+//     sorted in shared memory like a small segment -- or, if a bucket is still
+//     above CAP, by chunked LSD passes through global memory.
+// Every pass is stable, so every segment ends in the stable order of the key
+// transform of common.cuh.  Raw key bits (and values) are moved.
+#pragma once
+
+#include "common.cuh"
+
+namespace ak {
+
+struct SegArgsBase {
+  const int64_t *off;     // nseg + 1 offsets (clamped to [0, n] on read); NULL: one segment [0, n)
+  int64_t nseg;
+  int64_t n;
+  const uint32_t *order;  // work order (segment ids), nseg entries (NULL with off == NULL)
+  DevHeader *hdr;
+  int path_tag;           // written to ak_info.path by block 0
+};
+
+template <typename U, typename V>
+struct SegArgs : SegArgsBase {
+  U *keys;     // in place
+  V *vals;     // in place (HAS_V)
+  U *alt_k;    // workspace copy region, indexed like keys
+  V *alt_v;
+  U flip;
+  int64_t seg_base;  // added to every offset (0 for the batch API)
+};
+
+// ------------------------------------------------------------- classification
+// Work order: segments longer than `cap` from the front, the others from the back.
+static __global__ void classify_kernel(const int64_t *off, int64_t nseg, int64_t n, int64_t cap, uint32_t *order,
+                                       uint32_t *counters) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  int64_t lo = off[s], hi = off[s + 1];
+  lo = lo < 0 ? 0 : (lo > n ? n : lo);
+  hi = hi < 0 ? 0 : (hi > n ? n : hi);
+  if (hi - lo > cap) order[atomicAdd(&counters[0], 1u)] = uint32_t(s);
+  else order[nseg - 1 - atomicAdd(&counters[1], 1u)] = uint32_t(s);
+}
+
+// Clamp an offset into [0, n].
+__device__ __forceinline__ int64_t clamp_off(int64_t v, int64_t n) { return v < 0 ? 0 : (v > n ? n : v); }
+
+// Reduction helpers over the CTA.
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long cta_or(unsigned long long v, unsigned long long *scr) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) scr[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+#pragma unroll
+  for (int w = 0; w < BLOCK / 32; ++w) r |= scr[w];
+  __syncthreads();
+  return r;
+}
+
+template <typename U, typename V, bool HAS_V, int KIND, int BLOCK, int ITEMS, int CAP>
+struct SegSmem {
+  static constexpr int NW = BLOCK / 32;
+  static constexpr int CH = BLOCK * ITEMS;  // keys ranked per chunk
+  static constexpr int HROW = RADIX + 2;
+  // a segment buffer: CAP keys, then (16-byte aligned) CAP values
+  static constexpr size_t VOFF = (size_t(CAP) * sizeof(U) + 15) / 16 * 16;
+  static constexpr size_t BUF = (VOFF + (HAS_V ? size_t(CAP) * sizeof(V) : 0) + 127) / 128 * 128;
+  static constexpr size_t OFF_A = 0;
+  static constexpr size_t OFF_B = BUF;
+  static constexpr size_t OFF_HIST = 2 * BUF;                                        // u16[NW][HROW]
+  static constexpr size_t OFF_MASK = (OFF_HIST + size_t(NW) * HROW * 2 + 15) / 16 * 16;  // u32[NW][HROW]
+  static constexpr size_t OFF_CNT = OFF_MASK + size_t(NW) * HROW * 4;               // u32[RADIX] digit hist
+  static constexpr size_t OFF_RUN = OFF_CNT + RADIX * 4;                            // u32[RADIX] running offsets
+  static constexpr size_t OFF_CST = OFF_RUN + RADIX * 4;                            // u32[RADIX] chunk starts
+  static constexpr size_t OFF_CCNT = OFF_CST + RADIX * 4;                           // u32[RADIX] chunk counts
+  static constexpr size_t OFF_BST = OFF_CCNT + RADIX * 4;                           // u32[RADIX] bucket starts
+  static constexpr size_t OFF_BCNT = OFF_BST + RADIX * 4;                           // u32[RADIX] bucket counts
+  static constexpr size_t OFF_SCR = OFF_BCNT + RADIX * 4;                           // u64[NW+1]
+  static constexpr size_t OFF_MISC = OFF_SCR + (NW + 1) * 8;                        // u32[8]
+  static constexpr size_t BYTES = OFF_MISC + 32;
+  static_assert(CH <= CAP, "a chunk fits in a segment buffer");
+  static_assert(VOFF % 16 == 0 && BUF % 128 == 0 && OFF_MASK % 16 == 0 && OFF_SCR % 8 == 0,
+                "shared-memory arrays aligned to their element size");
+  static_assert(CAP < 65536, "16-bit warp bases");
+};
+
+// One CTA sorts segments.  Generic pointers address shared or global buffers.
+template <typename U, typename V, bool HAS_V, int KIND, int BLOCK, int ITEMS, int CAP>
+struct SegCta {
+  using L = SegSmem<U, V, HAS_V, KIND, BLOCK, ITEMS, CAP>;
+  static constexpr int NW = L::NW, CH = L::CH, HROW = L::HROW;
+  uint8_t *smem;
+  int tid, warp, lane;
+  uint32_t lt_mask, gt_mask;
+  U flip;
+  uint16_t *whist, *wh;
+  uint32_t *wmask, *wm, *s_cnt, *s_run, *s_cst, *s_ccnt, *s_bst, *s_bcnt, *s_misc;
+  unsigned long long *s_scr;
+
+  __device__ void init(uint8_t *sm, U fl) {
+    smem = sm;
+    tid = threadIdx.x;
+    warp = tid >> 5;
+    lane = tid & 31;
+    lt_mask = lanemask_lt();
+    gt_mask = ~(lt_mask | (1u << lane));
+    flip = fl;
+    whist = reinterpret_cast<uint16_t *>(smem + L::OFF_HIST);
+    wh = whist + warp * HROW;
+    wmask = reinterpret_cast<uint32_t *>(smem + L::OFF_MASK);
+    wm = wmask + warp * HROW;
+    s_cnt = reinterpret_cast<uint32_t *>(smem + L::OFF_CNT);
+    s_run = reinterpret_cast<uint32_t *>(smem + L::OFF_RUN);
+    s_cst = reinterpret_cast<uint32_t *>(smem + L::OFF_CST);
+    s_ccnt = reinterpret_cast<uint32_t *>(smem + L::OFF_CCNT);
+    s_bst = reinterpret_cast<uint32_t *>(smem + L::OFF_BST);
+    s_bcnt = reinterpret_cast<uint32_t *>(smem + L::OFF_BCNT);
+    s_scr = reinterpret_cast<unsigned long long *>(smem + L::OFF_SCR);
+    s_misc = reinterpret_cast<uint32_t *>(smem + L::OFF_MISC);
+    for (int i = tid; i < NW * HROW; i += BLOCK) wmask[i] = 0u;
+    __syncthreads();
+  }
+
+  __device__ U *buf_k(int which) { return reinterpret_cast<U *>(smem + (which ? L::OFF_B : L::OFF_A)); }
+  __device__ V *buf_v(int which) { return reinterpret_cast<V *>(smem + (which ? L::OFF_B : L::OFF_A) + L::VOFF); }
+  __device__ U rk(U k) const { return radix_key_t<KIND>(k, flip); }
+
+  // OR over the segment of (radix key ^ radix key of the first element).
+  __device__ unsigned long long vary_bits(const U *src, int64_t len) {
+    const U r0 = rk(src[0]);
+    unsigned long long v = 0;
+    for (int64_t i = tid; i < len; i += BLOCK) v |= (unsigned long long)(rk(src[i]) ^ r0);
+    return cta_or<BLOCK>(v, s_scr);
+  }
+
+  // Copy len elements (keys and values) between generic buffers, coalesced.
+  __device__ void copy(U *dk, V *dv, const U *sk, const V *sv, int64_t len) {
+    for (int64_t i = tid; i < len; i += BLOCK) {
+      dk[i] = sk[i];
+      if (HAS_V) dv[i] = sv[i];
+    }
+  }
+
+  // Rank one chunk [c0, c0 + cn) of src by digit (shift) with warp multisplit;
+  // afterwards wh rows hold chunk digit start + earlier-warp counts, s_cst the
+  // chunk digit starts and s_ccnt the chunk digit counts.
+  __device__ void rank_chunk(const U *src, int cn, int shift, uint32_t (&dr)[ITEMS]) {
+    for (int i = lane; i < HROW / 2; i += 32) reinterpret_cast<uint32_t *>(wh)[i] = 0u;
+    __syncwarp();
+    const int wbase = warp * 32 * ITEMS;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int idx = wbase + i * 32 + lane;
+      dr[i] = (idx < cn) ? digit_of(rk(src[idx]), shift) : uint32_t(RADIX);
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const uint32_t d = dr[i];
+      atomicOr(&wm[d], 1u << lane);
+      __syncwarp();
+      const uint32_t peers = wm[d];
+      const uint32_t cnt = wh[d];
+      __syncwarp();
+      if ((peers & gt_mask) == 0) {
+        wh[d] = uint16_t(cnt + __popc(peers));
+        wm[d] = 0u;
+      }
+      __syncwarp();
+      dr[i] = ((cnt + __popc(peers & lt_mask)) << 9) | d;
+    }
+    __syncthreads();
+    uint32_t my = 0;
+    if (tid < RADIX) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = whist[w * HROW + tid];
+        whist[w * HROW + tid] = uint16_t(run);
+        run += c;
+      }
+      my = run;
+      s_ccnt[tid] = run;
+    }
+    unsigned long long total;
+    const uint32_t start =
+        uint32_t(block_exclusive_scan<BLOCK>((unsigned long long)(tid < RADIX ? my : 0u), s_scr, &total));
+    if (tid < RADIX) {
+      s_cst[tid] = start;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) whist[w * HROW + tid] = uint16_t(whist[w * HROW + tid] + start);
+    }
+    __syncthreads();
+  }
+
+  // Digit histogram of src[0, len) into s_cnt, exclusive scan into s_run.
+  __device__ void digit_offsets(const U *src, int64_t len, int shift) {
+    for (int i = tid; i < RADIX; i += BLOCK) s_cnt[i] = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < len; i += BLOCK) atomicAdd(&s_cnt[digit_of(rk(src[i]), shift)], 1u);
+    __syncthreads();
+    unsigned long long total;
+    const uint32_t c = tid < RADIX ? s_cnt[tid] : 0u;
+    const uint32_t ex = uint32_t(block_exclusive_scan<BLOCK>((unsigned long long)c, s_scr, &total));
+    if (tid < RADIX) s_run[tid] = ex;
+    __syncthreads();
+  }
+
+  // One stable LSD pass src -> dst (both shared memory), len <= CAP.
+  __device__ void pass_smem(const U *sk, const V *sv, U *dk, V *dv, int len, int shift) {
+    if (len > CH) digit_offsets(sk, len, shift);
+    for (int c0 = 0; c0 < len; c0 += CH) {
+      const int cn = (len - c0) < CH ? (len - c0) : CH;
+      uint32_t dr[ITEMS];
+      rank_chunk(sk + c0, cn, shift, dr);
+      const int wbase = warp * 32 * ITEMS;
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = dr[i] & 511u;
+        if (d < RADIX) {
+          const int idx = wbase + i * 32 + lane;
+          uint32_t pos = uint32_t(wh[d]) + (dr[i] >> 9);
+          if (len > CH) pos += s_run[d] - s_cst[d];
+          dk[pos] = sk[c0 + idx];
+          if (HAS_V) dv[pos] = sv[c0 + idx];
+        }
+      }
+      __syncthreads();
+      if (len > CH && tid < RADIX) s_run[tid] += s_ccnt[tid];
+      __syncthreads();
+    }
+  }
+
+  // One stable pass src -> dst in global memory (len > CAP possible), chunks
+  // staged through buffer A so that every warp stores digit runs.  If
+  // `buckets`, s_bst/s_bcnt receive the digit starts/counts.
+  __device__ void pass_global(const U *sk, const V *sv, U *dk, V *dv, int64_t len, int shift, bool buckets) {
+    digit_offsets(sk, len, shift);
+    if (buckets && tid < RADIX) {
+      s_bst[tid] = s_run[tid];
+      s_bcnt[tid] = s_cnt[tid];
+    }
+    U *stk = buf_k(0);
+    V *stv = buf_v(0);
+    for (int64_t c0 = 0; c0 < len; c0 += CH) {
+      const int cn = int((len - c0) < CH ? (len - c0) : CH);
+      uint32_t dr[ITEMS];
+      rank_chunk(sk + c0, cn, shift, dr);
+      const int wbase = warp * 32 * ITEMS;
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = dr[i] & 511u;
+        if (d < RADIX) {
+          const int idx = wbase + i * 32 + lane;
+          const uint32_t pos = uint32_t(wh[d]) + (dr[i] >> 9);
+          stk[pos] = sk[c0 + idx];
+          if (HAS_V) stv[pos] = sv[c0 + idx];
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < cn; i += BLOCK) {
+        const U k = stk[i];
+        const uint32_t d = digit_of(rk(k), shift);
+        const int64_t g = int64_t(s_run[d]) + (i - int64_t(s_cst[d]));
+        dk[g] = k;
+        if (HAS_V) dv[g] = stv[i];
+      }
+      __syncthreads();
+      if (tid < RADIX) s_run[tid] += s_ccnt[tid];
+      __syncthreads();
+    }
+  }
+
+  // Passes over the varying bits [lo, hi] of a range held in shared buffer
+  // `which`; returns the buffer holding the result.
+  __device__ int lsd_smem(int which, int len, int lo, int hi) {
+    for (int sh = lo; sh <= hi; sh += RADIX_BITS) {
+      pass_smem(buf_k(which), buf_v(which), buf_k(which ^ 1), buf_v(which ^ 1), len, sh);
+      which ^= 1;
+    }
+    return which;
+  }
+
+  // Sort gk/gv[0, len) (global) into dk/dv (global, may alias gk/gv), len <= CAP.
+  __device__ void sort_small(const U *gk, const V *gv, U *dk, V *dv, int len) {
+    copy(buf_k(0), buf_v(0), gk, gv, len);
+    __syncthreads();
+    const unsigned long long vary = vary_bits(buf_k(0), len);
+    if (vary == 0) {  // every key equivalent: stable order is the input order
+      if (dk != gk) {
+        copy(dk, dv, buf_k(0), buf_v(0), len);
+        __syncthreads();
+      }
+      return;
+    }
+    const int lo = __ffsll((long long)vary) - 1;
+    const int hi = 63 - __clzll((long long)vary);
+    const int res = lsd_smem(0, len, lo, hi);
+    copy(dk, dv, buf_k(res), buf_v(res), len);
+    __syncthreads();
+  }
+
+  // Chunked LSD through global memory over bits [lo, hi]: src -> alternating
+  // buffers, result left in dk/dv.
+  __device__ void lsd_global(U *k0, V *v0, U *k1, V *v1, int64_t len, int lo, int hi, U *dk, V *dv) {
+    // k0 holds the data; passes alternate k0 -> k1 -> k0 ...
+    int which = 0;
+    for (int sh = lo; sh <= hi; sh += RADIX_BITS) {
+      if (which == 0) pass_global(k0, v0, k1, v1, len, sh, false);
+      else pass_global(k1, v1, k0, v0, len, sh, false);
+      which ^= 1;
+    }
+    U *rk_ = which ? k1 : k0;
+    V *rv_ = which ? v1 : v0;
+    if (rk_ != dk) {
+      copy(dk, dv, rk_, rv_, len);
+      __syncthreads();
+    }
+  }
+
+  // Segment above CAP: MSD split on the top 8 varying bits, then each bucket.
+  __device__ void sort_large(U *gk, V *gv, U *ak, V *av, int64_t len) {
+    const unsigned long long vary = vary_bits(gk, len);
+    if (vary == 0) return;
+    const int lo = __ffsll((long long)vary) - 1;
+    const int hi = 63 - __clzll((long long)vary);
+    const int top = (hi - RADIX_BITS + 1) > lo ? (hi - RADIX_BITS + 1) : lo;
+    pass_global(gk, gv, ak, av, len, top, true);  // keys now in ak in top-digit order
+    if (top == lo) {  // that pass covered every varying bit
+      copy(gk, gv, ak, av, len);
+      __syncthreads();
+      return;
+    }
+    for (int b = 0; b < RADIX; ++b) {
+      const int64_t bs = s_bst[b], bl = s_bcnt[b];
+      if (bl == 0) continue;
+      if (bl <= CAP) {
+        sort_small(ak + bs, HAS_V ? av + bs : nullptr, gk + bs, HAS_V ? gv + bs : nullptr, int(bl));
+      } else {
+        // still too large: chunked LSD over the bits below the top digit
+        const unsigned long long bv = vary_bits(ak + bs, bl);
+        if (bv == 0) {
+          copy(gk + bs, HAS_V ? gv + bs : nullptr, ak + bs, HAS_V ? av + bs : nullptr, bl);
+          __syncthreads();
+          continue;
+        }
+        const int blo = __ffsll((long long)bv) - 1;
+        const int bhi = 63 - __clzll((long long)bv);
+        lsd_global(ak + bs, HAS_V ? av + bs : nullptr, gk + bs, HAS_V ? gv + bs : nullptr, bl, blo, bhi,
+                   gk + bs, HAS_V ? gv + bs : nullptr);
+      }
+    }
+  }
+};
+
+template <typename U, typename V, bool HAS_V, int KIND, int BLOCK, int ITEMS, int CAP>
+__global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
+  using C = SegCta<U, V, HAS_V, KIND, BLOCK, ITEMS, CAP>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  C c;
+  c.init(smem, a.flip);
+  uint32_t *s_work = c.s_misc;
+  if (blockIdx.x == 0 && c.tid == 0 && a.path_tag) a.hdr->info.path = a.path_tag;
+  while (true) {
+    if (c.tid == 0) s_work[0] = atomicAdd(&a.hdr->work_counter[0], 1u);
+    __syncthreads();
+    const int64_t w = s_work[0];
+    __syncthreads();
+    if (w >= a.nseg) break;
+    const int64_t s = a.order ? a.order[w] : w;
+    const int64_t lo = a.off ? clamp_off(a.off[s], a.n) : 0;
+    const int64_t hi0 = a.off ? clamp_off(a.off[s + 1], a.n) : a.n;
+    const int64_t hi = hi0 < lo ? lo : hi0;
+    const int64_t len = hi - lo;
+    if (len <= 1) continue;
+    const int64_t g = a.seg_base + lo;
+    if (len <= CAP) {
+      c.sort_small(a.keys + g, HAS_V ? a.vals + g : nullptr, a.keys + g, HAS_V ? a.vals + g : nullptr, int(len));
+    } else {
+      c.sort_large(a.keys + g, HAS_V ? a.vals + g : nullptr, a.alt_k + g, HAS_V ? a.alt_v + g : nullptr, len);
+    }
+  }
+}
+
+}  // namespace ak

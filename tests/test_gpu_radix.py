@@ -48,7 +48,7 @@ def test_sort_matches_oracle(ak, dtype, desc, mode):
     for n in (SIZES if mode == "bits" else [3841, 100003]):
         keys = synth.random_keys(n, dtype, seed=1000 + n, mode=mode)
         want = oracle.gather(keys, oracle_perm(keys, desc))
-        assert_bits_equal(_run_sort(ak, keys, desc), want, f"sort n={n}")
+        assert_bits_equal(_run_sort(ak, keys, desc, {"path": ak.AK_PATH_RADIX}), want, f"sort n={n}")
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -58,7 +58,7 @@ def test_sortperm_matches_oracle(ak, dtype, desc, mode):
     for n in ([1, 3840, 3841, 100003] if mode == "bits" else [5000, 100003]):
         keys = synth.random_keys(n, dtype, seed=2000 + n, mode=mode)
         want = oracle_perm(keys, desc).astype(np.uint32)
-        assert np.array_equal(_run_perm(ak, keys, desc), want), f"sortperm n={n}"
+        assert np.array_equal(_run_perm(ak, keys, desc, {"path": ak.AK_PATH_RADIX}), want), f"sortperm n={n}"
 
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.float64, np.int16, np.float32])
@@ -71,7 +71,7 @@ def test_pairs_match_oracle(ak, dtype, vdtype, desc):
     p = oracle_perm(keys, desc)
     kt, ku = to_dev(keys)
     vt, _ = to_dev(vals)
-    ak.ak_sort_pairs(kt, vt, "descending" if desc else "ascending", unsigned=ku)
+    ak.ak_sort_pairs(kt, vt, "descending" if desc else "ascending", options={"path": ak.AK_PATH_RADIX}, unsigned=ku)
     torch.cuda.synchronize()
     assert_bits_equal(to_host(kt, keys.dtype), oracle.gather(keys, p), "pair keys")
     assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), "pair values")
@@ -80,7 +80,7 @@ def test_pairs_match_oracle(ak, dtype, vdtype, desc):
 @pytest.mark.parametrize("cfg", [1, 2, 3])
 @pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float32, np.uint16])
 def test_every_tile_config(ak, cfg, dtype):
-    opts = {"tile_config": cfg}
+    opts = {"tile_config": cfg, "path": ak.AK_PATH_RADIX}
     for n in (1, 1536, 6145, 200001):
         keys = synth.random_keys(n, dtype, seed=4000 + n, mode="dups")
         for desc in (False, True):
@@ -101,8 +101,9 @@ def test_trivial_passes_and_all_equal(ak):
     k = (synth.splitmix64(5, 30000) % np.uint64(256)).astype(np.uint32) << np.uint32(8)
     k |= np.uint32(0x11000000)
     info_keys, u = to_dev(k)
-    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, k.size, ak.AK_U32), info_keys.device)
-    ak.ak_sort(info_keys, temp=temp, unsigned=u)
+    rad = {"path": ak.AK_PATH_RADIX}
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, k.size, ak.AK_U32, options=rad), info_keys.device)
+    ak.ak_sort(info_keys, temp=temp, options=rad, unsigned=u)
     info = ak.ak_last_info(temp)
     assert info["radix_passes"] == 1 and info["status"] == 0
     assert_bits_equal(to_host(info_keys, k.dtype), np.sort(k), "copy-back")
