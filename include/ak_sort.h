@@ -163,6 +163,28 @@ ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg
                             ak_stream_t stream, const ak_options *opt);
 
 /*
+ * ak_sort without a caller workspace, for callers that cannot allocate device
+ * memory: code running inside a CUDA stream-capture region (cudaMalloc is not
+ * allowed there), latency-critical loops where cudaMalloc's implicit device
+ * synchronisation is unacceptable, and hosts whose device memory is owned by a
+ * framework pool that forbids foreign allocations.  There is no counterpart in
+ * the paper; it exists for these callers only.
+ *
+ * The workspace is a static device array of AK_STATIC_SCRATCH_BYTES inside this
+ * library; every GPU that loads the library holds it until the process exits.
+ * Requests whose ak_sort workspace (ak_sort_temp_bytes with AK_OP_SORT) exceeds
+ * it return AK_ERR_WORKSPACE_TOO_SMALL with nothing enqueued.  The call allocates
+ * nothing.  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it, so make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  Results,
+ * ordering and stability are those of ak_sort; device-side timeouts are recorded
+ * only in the shared array and are not returned.
+ */
+#define AK_STATIC_SCRATCH_BYTES (32u << 20)
+ak_status ak_sort_static_scratch(void *d_keys, int64_t n, ak_dtype kd, ak_order order, ak_stream_t stream);
+
+/*
  * Synchronises `stream` and returns the device-side status of the last call that
  * used d_temp (AK_OK, or e.g. AK_ERR_TIMEOUT).  AK_ERR_CUDA if the copy fails.
  */

@@ -31,7 +31,7 @@ EXPORTED = (
     "ak_sort_temp_bytes", "ak_sort", "ak_sortperm", "ak_sort_pairs", "ak_sort_segmented",
     "ak_status_check", "ak_last_info", "ak_status_string", "ak_learned_knot_counts",
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
-    "ak_autotune_load", "ak_autotune_clear", "ak_version",
+    "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
 )
 
 
@@ -92,6 +92,7 @@ def load() -> ctypes.CDLL:
                 "ak_autotune_load": ([ctypes.c_char_p], i32),
                 "ak_autotune_clear": ([], None),
                 "ak_version": ([], ctypes.c_char_p),
+                "ak_sort_static_scratch": ([p, i64, i32, i32, p], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -244,6 +245,16 @@ def ak_sort_segmented(keys: torch.Tensor, offsets: torch.Tensor, order="ascendin
 
 def ak_sort_temp_bytes(op: int, n: int, kd: int, val_bytes: int = 0, nseg: int = 0, options=None) -> int:
     return temp_bytes(op, n, kd, val_bytes, nseg, options)
+
+
+def ak_sort_static_scratch(keys: torch.Tensor, order="ascending", *, stream=None,
+                           unsigned: bool = False) -> torch.Tensor:
+    """ak_sort with the library's built-in static workspace (no allocation)."""
+    _contig_cuda(keys, "keys")
+    kd = dtype_code(keys, unsigned)
+    _check(load().ak_sort_static_scratch(keys.data_ptr(), keys.numel(), kd, order_code(order),
+                                         _stream_ptr(stream)), "ak_sort_static_scratch")
+    return keys
 
 
 def ak_status_check(temp: torch.Tensor, stream=None) -> int:
