@@ -204,19 +204,19 @@ const char *ak_status_string(ak_status s);
 #define AK_LEARNED_PARAMS 321
 
 /*
- * Knot counts of the piecewise-linear CDF: d_counts[j] = #{i : d_xs[i] <= fp32(j/63)}
- * for j < 64, over an ascending float32 sample d_xs[0..m) in [0, 1] (an
- * interpolated histogram of the sample, Sec. III-A).  One small launch.
+ * Knots of the piecewise-linear CDF: d_knots[j] = d_xs[round(j (m-1) / 63)],
+ * j < 64, for an ascending float32 sample d_xs[0..m) of x-hat values in [0, 1]:
+ * the sample order statistics that the sample sort's splitter step picks
+ * (Sec. III-A), through which PL interpolates (xi_j, j/63).  m >= 1.
  */
-ak_status ak_learned_knot_counts(const float *d_xs, int64_t m, int32_t *d_counts,
-                                 ak_stream_t stream);
+ak_status ak_learned_knots(const float *d_xs, int64_t m, float *d_knots, ak_stream_t stream);
 
 /*
- * Loss and gradient of the residual MLP (1 -> 16 -> 16 -> 1, ReLU) for the model
- * F(x) = PL(x) + r(x): d_loss[0] = mean_i (F(x_i) - y_i)^2 and d_grad = dLoss/dparams,
+ * Loss and gradient of the residual MLP (1 -> 16 -> 16 -> 1, ReLU, output scaled
+ * by 1/1024) for the model F(x) = PL(x) + r(x): d_loss[0] = mean_i (F(x_i) - y_i)^2 and d_grad = dLoss/dparams,
  * computed by the same forward/backward kernels the learned path trains with.
  *   d_x, d_y   m float32 inputs and targets
- *   d_c        64 float32 knot values of PL at fp32(j/63)
+ *   d_c        64 float32 PL knots xi_j (non-decreasing), PL(xi_j) = j/63
  *   d_params   321 float32: W1[16], b1[16], W2[16][16] (row j feeds hidden unit j),
  *              b2[16], w3[16], b3
  *   d_grad     321 float32 out; d_loss 1 float32 out

@@ -6,9 +6,10 @@ replaces the splitters by a tiny model of the key CDF trained on that sample:
 
   x-hat   min-max normalised order-preserving integer image of a key (the
           "radix key"; see ``radix_key``), lo/hi = sample minimum/maximum
-  PL(x)   64-knot piecewise-linear CDF: knots u_j = fp32(j/63), values
-          c_j = #{sample x-hat <= u_j} / m  (the interpolated histogram)
-  r(x)    MLP residual 1 -> 16 -> 16 -> 1 with ReLU
+  PL(x)   64-knot piecewise-linear CDF through (xi_j, j/63), xi_j the sorted
+          sample's order statistic of rank round(j (m-1) / 63): the splitters
+          of the sample sort, interpolated; 0 below xi_0, 1 from xi_63 on
+  r(x)    MLP residual 1 -> 16 -> 16 -> 1 with ReLU, output scaled by 1/1024
   F(x)    PL(x) + r(x), trained by mean squared error on (x_i, (i+0.5)/m) over
           the sorted sample
 
@@ -28,6 +29,7 @@ HIDDEN = 16
 # W2[j, k] multiplies h1[k] into h2[j]), b2[16], w3[16], b3[1]
 P_W1, P_B1, P_W2, P_B2, P_W3, P_B3 = 0, 16, 32, 288, 304, 320
 N_PARAMS = 321
+OUT_SCALE = 1.0 / 1024.0  # r = OUT_SCALE * (b3 + w3 . h2)
 
 
 def radix_key(keys: np.ndarray) -> np.ndarray:
@@ -50,24 +52,34 @@ def radix_key(keys: np.ndarray) -> np.ndarray:
     return out
 
 
-def knots_u() -> np.ndarray:
-    """Knot abscissae fp32(j/63), as float64."""
-    return (np.arange(N_KNOTS, dtype=np.float64) / (N_KNOTS - 1)).astype(np.float32).astype(np.float64)
+def knot_ranks(m: int) -> np.ndarray:
+    """Ranks round(j (m-1) / 63) of the 64 knots (round half up, integers)."""
+    j = np.arange(N_KNOTS, dtype=np.int64)
+    return (j * (m - 1) + (N_KNOTS - 1) // 2) // (N_KNOTS - 1)
 
 
-def pl_knot_counts(x_sorted: np.ndarray) -> np.ndarray:
-    """#{i : x_i <= u_j} for each knot, on an ascending sample (integers)."""
-    xs = np.asarray(x_sorted, dtype=np.float64)
-    return np.searchsorted(xs, knots_u(), side="right").astype(np.int64)
+def pl_knots(x_sorted: np.ndarray) -> np.ndarray:
+    """The 64 knots: sample order statistics at knot_ranks (exact sample values)."""
+    xs = np.asarray(x_sorted)
+    return xs[knot_ranks(xs.size)]
 
 
-def pl_eval(x: np.ndarray, c: np.ndarray) -> np.ndarray:
-    """Piecewise-linear interpolation through (u_j, c_j), x clamped to [0, 1]."""
-    x = np.clip(np.asarray(x, dtype=np.float64), 0.0, 1.0)
-    t = x * (N_KNOTS - 1)
-    j = np.minimum(np.floor(t).astype(np.int64), N_KNOTS - 2)
-    f = t - j
-    return c[j] + f * (c[j + 1] - c[j])
+def pl_eval(x: np.ndarray, xi: np.ndarray) -> np.ndarray:
+    """Piecewise-linear interpolation through (xi_j, j/63); 0 below xi_0, 1 from
+    xi_63 on.  In an interval [xi_j, xi_(j+1)) with xi_j < xi_(j+1) the value
+    rises linearly from j/63 to (j+1)/63."""
+    x = np.asarray(x, dtype=np.float64)
+    xi = np.asarray(xi, dtype=np.float64)
+    out = np.empty(x.shape)
+    for i, v in enumerate(x.ravel()):
+        if not v >= xi[0]:
+            out.flat[i] = 0.0
+        elif v >= xi[-1]:
+            out.flat[i] = 1.0
+        else:
+            j = int(np.searchsorted(xi, v, side="right")) - 1   # xi[j] <= v < xi[j+1]
+            out.flat[i] = (j + (v - xi[j]) / (xi[j + 1] - xi[j])) / (N_KNOTS - 1)
+    return out
 
 
 def unpack(p: np.ndarray):
@@ -84,7 +96,7 @@ def mlp_forward(p: np.ndarray, x: np.ndarray):
     h1 = np.maximum(a1, 0.0)
     a2 = h1 @ W2.T + b2[None, :]
     h2 = np.maximum(a2, 0.0)
-    r = h2 @ w3 + b3
+    r = OUT_SCALE * (h2 @ w3 + b3)
     return r, (x, a1, h1, a2, h2)
 
 
@@ -95,7 +107,7 @@ def loss_and_grad(p: np.ndarray, x: np.ndarray, y: np.ndarray, c: np.ndarray):
     m = xx.size
     e = pl_eval(xx, c) + r - np.asarray(y, dtype=np.float64)
     loss = float(np.mean(e * e))
-    d3 = 2.0 * e / m                       # dL/dr_i
+    d3 = 2.0 * e / m * OUT_SCALE           # dL/d(b3 + w3 . h2) at point i
     g = np.zeros(N_PARAMS)
     g[P_W3:P_B3] = h2.T @ d3
     g[P_B3] = d3.sum()

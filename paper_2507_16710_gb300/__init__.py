@@ -11,7 +11,7 @@ from ._lib import (  # noqa: F401
     AK_PATH_LEARNED, AK_PATH_RADIX, AK_TILE_CONFIGS, AK_U16, AK_U32, AK_U64, EXPORTED, LIB_PATH,
     AK_DEBUG_SKIP_FIRST_TILE, AK_MAX_PASSES,
     AkError, Info, Options, ak_autotune, ak_autotune_clear, ak_autotune_load, ak_autotune_save,
-    ak_last_info, ak_learned_knot_counts, ak_learned_loss_grad, ak_sort, ak_sort_pairs,
+    ak_last_info, ak_learned_knots, ak_learned_loss_grad, ak_sort, ak_sort_pairs,
     ak_sort_segmented, ak_sort_static_scratch, ak_sort_temp_bytes, ak_sortperm, ak_status_check, ak_status_string,
     ak_version, dtype_code, load, order_code, temp_bytes, workspace,
 )

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "AK_OK", 1: "AK_ERR_INVALID_ARG", 2: "AK_ERR_UNSUPPORTED",
 
 EXPORTED = (
     "ak_sort_temp_bytes", "ak_sort", "ak_sortperm", "ak_sort_pairs", "ak_sort_segmented",
-    "ak_status_check", "ak_last_info", "ak_status_string", "ak_learned_knot_counts",
+    "ak_status_check", "ak_last_info", "ak_status_string", "ak_learned_knots",
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
     "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
 )
@@ -84,7 +84,7 @@ def load() -> ctypes.CDLL:
                 "ak_status_check": ([p, p], i32),
                 "ak_last_info": ([p, p, ctypes.POINTER(Info)], i32),
                 "ak_status_string": ([i32], ctypes.c_char_p),
-                "ak_learned_knot_counts": ([p, i64, p, p], i32),
+                "ak_learned_knots": ([p, i64, p, p], i32),
                 "ak_learned_loss_grad": ([p, p, i64, p, p, p, p, p, sz, p], i32),
                 "ak_learned_grad_temp_bytes": ([i64], sz),
                 "ak_autotune": ([i32, i64, i32, i32, i32, p, p, p, p, sz, p, opt], i32),
@@ -275,12 +275,12 @@ def ak_version() -> str:
     return load().ak_version().decode()
 
 
-def ak_learned_knot_counts(xs_sorted: torch.Tensor, stream=None) -> torch.Tensor:
+def ak_learned_knots(xs_sorted: torch.Tensor, stream=None) -> torch.Tensor:
     _contig_cuda(xs_sorted, "xs")
-    counts = torch.empty(64, dtype=torch.int32, device=xs_sorted.device)
-    _check(load().ak_learned_knot_counts(xs_sorted.data_ptr(), xs_sorted.numel(), counts.data_ptr(),
-                                         _stream_ptr(stream)), "ak_learned_knot_counts")
-    return counts
+    knots = torch.empty(64, dtype=torch.float32, device=xs_sorted.device)
+    _check(load().ak_learned_knots(xs_sorted.data_ptr(), xs_sorted.numel(), knots.data_ptr(),
+                                   _stream_ptr(stream)), "ak_learned_knots")
+    return knots
 
 
 def ak_learned_loss_grad(x: torch.Tensor, y: torch.Tensor, c: torch.Tensor, params: torch.Tensor,

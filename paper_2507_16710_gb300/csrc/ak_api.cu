@@ -5,6 +5,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "learned.cuh"
 #include "onesweep.cuh"
 
 namespace ak {
@@ -159,6 +160,7 @@ __global__ void iota_u32_kernel(uint32_t *p, int64_t n) {
 // Which path serves a sort/sortperm/pairs call.
 static int choose_path(int op, int64_t n, int key_bytes, int vb, const ak_options &o) {
   if (o.path == AK_PATH_RADIX || o.path == AK_PATH_BLOCK) return o.path;
+  if (o.path == AK_PATH_LEARNED) return n < (int64_t(1) << 32) ? AK_PATH_LEARNED : AK_PATH_RADIX;
   (void)op;
   return n <= seg_cap(key_bytes, vb) ? AK_PATH_BLOCK : AK_PATH_RADIX;
 }
@@ -167,10 +169,15 @@ static int value_bytes(int op, int val_bytes) {
   return (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
 }
 
+struct LearnedLayout;
+static size_t learned_total(int op, int64_t n, int key_bytes, int val_bytes, const ak_options &o);
+
 static size_t temp_for(int op, int64_t n, int key_bytes, int val_bytes, int64_t nseg, const ak_options &o) {
   const int vb = value_bytes(op, val_bytes);
   if (op == AK_OP_SORT_SEGMENTED) return seg_layout(op, n, nseg, key_bytes, 0).total;
-  if (choose_path(op, n, key_bytes, vb, o) == AK_PATH_BLOCK) return seg_layout(op, n, 1, key_bytes, vb).total;
+  const int path = choose_path(op, n, key_bytes, vb, o);
+  if (path == AK_PATH_BLOCK) return seg_layout(op, n, 1, key_bytes, vb).total;
+  if (path == AK_PATH_LEARNED) return learned_total(op, n, key_bytes, val_bytes, o);
   return radix_layout(op, n, key_bytes, val_bytes, min_tile_keys(key_bytes, vb)).total;
 }
 
@@ -208,6 +215,177 @@ static ak_status run_seg(int op, void *keys, const int64_t *off, int64_t nseg, i
   c.path_tag = AK_PATH_BLOCK;
   c.stream = stream;
   return seg_dispatch(ki.bytes, c) == cudaSuccess ? AK_OK : AK_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ learned path
+struct LearnedLayout {
+  RadixLayout rad;  // the pairs/keys radix layout (fallback + bucket passes)
+  size_t model, sample_r, xs, xs_alt, s_hdr, s_counts, s_plan, s_status0, s_status1, partials, bcounts, seg_off,
+      seg_order, seg_counters, kcopy, total;
+  uint32_t m, bbits;
+};
+
+static int ceil_log2(uint64_t v) {
+  int b = 0;
+  while ((uint64_t(1) << b) < v) ++b;
+  return b;
+}
+
+static LearnedLayout learned_layout(int op, int64_t n, int key_bytes, int val_bytes, const ak_options &o) {
+  LearnedLayout L{};
+  // sortperm runs as a key-value sort of a key copy with the index as value
+  const int lop = (op == AK_OP_SORTPERM) ? AK_OP_SORT_PAIRS : op;
+  const int lvb = (op == AK_OP_SORTPERM) ? 4 : val_bytes;
+  const int vb = value_bytes(lop, lvb);
+  L.rad = radix_layout(lop, n, key_bytes, lvb, min_tile_keys(key_bytes, vb));
+  size_t off = L.rad.total;
+  // a 1% sample (at least 4096 keys, at most 2^20)
+  int64_t m = n / 100;
+  m = m < 4096 ? 4096 : m;
+  m = m > LM_MAX_SAMPLE ? LM_MAX_SAMPLE : m;
+  m = m > n ? n : m;
+  L.m = uint32_t(m);
+  // buckets: about 1024 keys each, 2^8 .. 2^16
+  int bb = (o.bucket_bits >= 8 && o.bucket_bits <= 16) ? o.bucket_bits : ceil_log2(uint64_t(n > 1024 ? n / 1024 : 1));
+  bb = bb < 8 ? 8 : (bb > 16 ? 16 : bb);
+  L.bbits = uint32_t(bb);
+  const size_t nb = size_t(1) << bb;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += align256(bytes);
+    return at;
+  };
+  L.model = take(sizeof(LearnedModel));
+  L.sample_r = take(size_t(m) * 8);
+  L.xs = take(size_t(m) * 4);
+  L.xs_alt = take(size_t(m) * 4);
+  L.s_hdr = take(sizeof(DevHeader));
+  L.s_counts = take(sizeof(unsigned long long) * MAX_PASSES * RADIX);
+  L.s_plan = take(sizeof(RadixPlan));
+  const int64_t stiles = (m + min_tile_keys(4, 0) - 1) / min_tile_keys(4, 0);
+  L.s_status0 = take(size_t(stiles) * RADIX * 4);
+  L.s_status1 = take(size_t(stiles) * RADIX * 4);
+  L.partials = take(learned_partials_bytes());
+  L.bcounts = take(nb * 4);
+  L.seg_off = take((nb + 1) * 8);
+  L.seg_order = take(nb * 4);
+  L.seg_counters = take(256);
+  if (op == AK_OP_SORTPERM) L.kcopy = take(size_t(n) * key_bytes);
+  L.total = off;
+  return L;
+}
+
+static size_t learned_total(int op, int64_t n, int key_bytes, int val_bytes, const ak_options &o) {
+  return learned_layout(op, n, key_bytes, val_bytes, o).total;
+}
+
+static cudaError_t learned_dispatch(int key_bytes, int kind, const RadixCall &c, const LearnedCall &lc) {
+  switch (key_bytes) {
+    case 2: return kind == KIND_SINT ? learned_launch_u16_sint(c, lc) : learned_launch_u16_uint(c, lc);
+    case 4:
+      return kind == KIND_FLOAT  ? learned_launch_u32_float(c, lc)
+             : kind == KIND_SINT ? learned_launch_u32_sint(c, lc)
+                                 : learned_launch_u32_uint(c, lc);
+    default:
+      return kind == KIND_FLOAT  ? learned_launch_u64_float(c, lc)
+             : kind == KIND_SINT ? learned_launch_u64_sint(c, lc)
+                                 : learned_launch_u64_uint(c, lc);
+  }
+}
+
+static ak_status run_learned(int op, void *keys, const void *k_in, void *vals, int val_bytes, int64_t n,
+                             const KeyInfo &ki, int order, void *d_temp, size_t temp_bytes, cudaStream_t stream,
+                             const ak_options &o) {
+  const LearnedLayout L = learned_layout(op, n, ki.bytes, val_bytes, o);
+  if (d_temp == nullptr || temp_bytes < L.total) return AK_ERR_WORKSPACE_TOO_SMALL;
+  uint8_t *t = static_cast<uint8_t *>(d_temp);
+  const size_t nb = size_t(1) << L.bbits;
+  if (cudaMemsetAsync(t, 0, L.rad.plan, stream) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaMemsetAsync(t + L.model, 0, sizeof(LearnedModel), stream) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaMemsetAsync(t + L.s_hdr, 0, L.s_plan - L.s_hdr, stream) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaMemsetAsync(t + L.bcounts, 0, nb * 4, stream) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaMemsetAsync(t + L.seg_counters, 0, 256, stream) != cudaSuccess) return AK_ERR_CUDA;
+  void *kf = keys;
+  int vb = val_bytes;
+  if (op == AK_OP_SORTPERM) {  // key-value sort of a copy of the keys, values = 0..n-1
+    kf = t + L.kcopy;
+    if (cudaMemcpyAsync(kf, k_in, size_t(n) * ki.bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+      return AK_ERR_CUDA;
+    const int g = int((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    iota_u32_kernel<<<g, 256, 0, stream>>>(static_cast<uint32_t *>(vals), n);
+    vb = 4;
+  }
+  if (op == AK_OP_SORT) vb = 0;
+  LearnedModel *md = reinterpret_cast<LearnedModel *>(t + L.model);
+  RadixCall c{};
+  c.mode = MODE_INPLACE;
+  c.k_in = kf;
+  c.k_final = kf;
+  c.k_alt0 = t + L.rad.k_alt0;
+  c.v_in = vals;
+  c.v_final = vals;
+  c.v_alt = L.rad.v_alt ? t + L.rad.v_alt : nullptr;
+  c.val_bytes = vb;
+  c.n = n;
+  c.kind = ki.kind;
+  c.descending = order == AK_DESCENDING;
+  c.tile_config = 0;
+  c.hdr = reinterpret_cast<DevHeader *>(t + L.rad.hdr);
+  c.counts = reinterpret_cast<unsigned long long *>(t + L.rad.counts);
+  c.plan = reinterpret_cast<RadixPlan *>(t + L.rad.plan);
+  c.status[0] = t + L.rad.status0;
+  c.status[1] = t + L.rad.status1;
+  c.status_wide = L.rad.status_wide;
+  c.timeout_ns = o.timeout_ns;
+  c.path_tag = 0;
+  c.stream = stream;
+  LearnedCall lc{};
+  lc.model = md;
+  lc.m = L.m;
+  lc.seed = o.seed ? o.seed : 0x2507u;
+  lc.sample_r = reinterpret_cast<unsigned long long *>(t + L.sample_r);
+  lc.xs = reinterpret_cast<uint32_t *>(t + L.xs);
+  RadixCall &sc = lc.sample_sort;
+  sc.mode = MODE_INPLACE;
+  sc.k_in = lc.xs;
+  sc.k_final = lc.xs;
+  sc.k_alt0 = t + L.xs_alt;
+  sc.n = L.m;
+  sc.kind = KIND_UINT;
+  sc.hdr = reinterpret_cast<DevHeader *>(t + L.s_hdr);
+  sc.counts = reinterpret_cast<unsigned long long *>(t + L.s_counts);
+  sc.plan = reinterpret_cast<RadixPlan *>(t + L.s_plan);
+  sc.status[0] = t + L.s_status0;
+  sc.status[1] = t + L.s_status1;
+  sc.timeout_ns = o.timeout_ns;
+  sc.stream = stream;
+  lc.partials = reinterpret_cast<float *>(t + L.partials);
+  lc.train_steps = o.train_steps < 0 ? 0 : (o.train_steps > 0 ? o.train_steps : 64);
+  lc.lr = 1e-2f;
+  lc.nbuckets = uint32_t(nb);
+  lc.bucket_bits = L.bbits;
+  lc.bucket_counts = reinterpret_cast<uint32_t *>(t + L.bcounts);
+  lc.seg_off = reinterpret_cast<int64_t *>(t + L.seg_off);
+  lc.seg_capacity = seg_cap(ki.bytes, vb);
+  SegCall &f = lc.finish;
+  f.keys = kf;
+  f.vals = vals;
+  f.alt_k = t + L.rad.k_alt0;
+  f.alt_v = L.rad.v_alt ? t + L.rad.v_alt : nullptr;
+  f.val_bytes = vb;
+  f.off = lc.seg_off;
+  f.nseg = int64_t(nb);
+  f.n = n;
+  f.kind = ki.kind;
+  f.descending = order == AK_DESCENDING;
+  f.order = reinterpret_cast<uint32_t *>(t + L.seg_order);
+  f.counters = reinterpret_cast<uint32_t *>(t + L.seg_counters);
+  f.hdr = c.hdr;
+  f.path_tag = 0;
+  f.gate = &md->use_plain;
+  f.gate_want = 0;
+  f.stream = stream;
+  return learned_dispatch(ki.bytes, ki.kind, c, lc) == cudaSuccess ? AK_OK : AK_ERR_CUDA;
 }
 
 static bool valid_order(int order) { return order == AK_ASCENDING || order == AK_DESCENDING; }
@@ -296,8 +474,11 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
   const ak_options o = resolve_options(opt);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (choose_path(AK_OP_SORT, n, ki.bytes, 0, o) == AK_PATH_BLOCK)
+  const int path = choose_path(AK_OP_SORT, n, ki.bytes, 0, o);
+  if (path == AK_PATH_BLOCK)
     return run_seg(AK_OP_SORT, d_keys, nullptr, 1, n, nullptr, nullptr, 0, ki, order, d_temp, temp_bytes, st);
+  if (path == AK_PATH_LEARNED)
+    return run_learned(AK_OP_SORT, d_keys, d_keys, nullptr, 0, n, ki, order, d_temp, temp_bytes, st, o);
   return run_radix(AK_OP_SORT, d_keys, d_keys, nullptr, nullptr, 0, n, ki, order, d_temp, temp_bytes, st, o);
 }
 
@@ -311,8 +492,11 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
   const ak_options o = resolve_options(opt);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (choose_path(AK_OP_SORTPERM, n, ki.bytes, 4, o) == AK_PATH_BLOCK)
+  const int path = choose_path(AK_OP_SORTPERM, n, ki.bytes, 4, o);
+  if (path == AK_PATH_BLOCK)
     return run_seg(AK_OP_SORTPERM, nullptr, nullptr, 1, n, d_keys, d_perm, 4, ki, order, d_temp, temp_bytes, st);
+  if (path == AK_PATH_LEARNED)
+    return run_learned(AK_OP_SORTPERM, nullptr, d_keys, d_perm, 4, n, ki, order, d_temp, temp_bytes, st, o);
   return run_radix(AK_OP_SORTPERM, d_keys, nullptr, nullptr, d_perm, 4, n, ki, order, d_temp, temp_bytes, st, o);
 }
 
@@ -326,9 +510,13 @@ ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
   const ak_options o = resolve_options(opt);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (choose_path(AK_OP_SORT_PAIRS, n, ki.bytes, val_bytes, o) == AK_PATH_BLOCK)
+  const int path = choose_path(AK_OP_SORT_PAIRS, n, ki.bytes, val_bytes, o);
+  if (path == AK_PATH_BLOCK)
     return run_seg(AK_OP_SORT_PAIRS, d_keys, nullptr, 1, n, nullptr, d_vals, val_bytes, ki, order, d_temp,
                    temp_bytes, st);
+  if (path == AK_PATH_LEARNED)
+    return run_learned(AK_OP_SORT_PAIRS, d_keys, d_keys, d_vals, val_bytes, n, ki, order, d_temp, temp_bytes, st,
+                       o);
   return run_radix(AK_OP_SORT_PAIRS, d_keys, d_keys, d_vals, d_vals, val_bytes, n, ki, order, d_temp, temp_bytes,
                    st, o);
 }

@@ -11,6 +11,7 @@ namespace ak {
 
 struct DevHeader;
 struct RadixPlan;
+struct LearnedModel;
 
 // One radix sort (keys, keys+values, or keys -> permutation) on device buffers.
 struct RadixCall {
@@ -35,6 +36,8 @@ struct RadixCall {
   int path_tag;            // written to ak_info.path (0 = leave)
   int debug_flags;
   void **pass_events;      // optional profiling events (2 per pass)
+  const uint32_t *gate;    // if set, every kernel runs only when *gate == gate_want
+  uint32_t gate_want;
   cudaStream_t stream;
 };
 
@@ -83,8 +86,37 @@ struct SegCall {
   uint32_t *counters;      // 2 zeroed counters (workspace)
   DevHeader *hdr;          // zeroed header (work counter)
   int path_tag;            // written to ak_info.path
+  const uint32_t *gate;    // if set, run only when *gate == gate_want
+  uint32_t gate_want;
   cudaStream_t stream;
 };
+
+// Learned-CDF path: model, sample and finish regions of the workspace.
+struct LearnedCall {
+  LearnedModel *model;         // zeroed
+  uint32_t m, seed;            // sample size, sample/initialisation seed
+  unsigned long long *sample_r;
+  uint32_t *xs;                // m x-hat values (fp32 bits), sorted in place
+  RadixCall sample_sort;       // radix sort of xs (u32 keys)
+  float *partials;             // training partial sums
+  int train_steps;             // 0: piecewise-linear CDF only
+  float lr;
+  uint32_t nbuckets, bucket_bits;
+  uint32_t *bucket_counts;     // nbuckets, zeroed
+  int64_t *seg_off;            // nbuckets + 1 bucket offsets
+  int64_t seg_capacity;        // shared-memory capacity of the finish
+  SegCall finish;              // segmented sort over the buckets
+};
+cudaError_t learned_launch_u16_uint(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u16_sint(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u32_uint(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u32_sint(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u32_float(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u64_uint(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u64_sint(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u64_float(const RadixCall &c, const LearnedCall &lc);
+size_t learned_model_bytes();
+size_t learned_partials_bytes();
 // Shared-memory capacity (elements) of one segment buffer: about 24 KB of
 // keys+values, a multiple of 32 elements.
 constexpr int seg_cap(int key_bytes, int val_bytes) { return (24576 / (key_bytes + val_bytes)) / 32 * 32; }

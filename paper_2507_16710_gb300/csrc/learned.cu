@@ -1,0 +1,374 @@
+// learned.cu -- model kernels of the learned-CDF path (fit, train, tabulate)
+// and the C-ABI entry points that expose them for checking.
+#include "internal.h"
+#include "learned.cuh"
+#include "onesweep.cuh"
+
+namespace ak {
+
+__global__ void lm_xhat_kernel(const unsigned long long *sample_r, uint32_t m, LearnedModel *md, uint32_t *xs,
+                               const uint32_t *gate) {
+  if (gate && *gate) return;
+  const unsigned long long lo = ~md->neg_lo, hi = md->hi;
+  const bool any = md->hi != 0 || md->neg_lo != 0;
+  const unsigned long long l = (any && lo <= hi) ? lo : 0ull, h = (any && lo <= hi) ? hi : 0ull;
+  const float inv = (h > l) ? 1.0f / __ull2float_rn(h - l) : 0.0f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    md->neg_lo = ~l;
+    md->hi = h;
+    md->inv = inv;
+    md->m = m;
+  }
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
+    xs[j] = __float_as_uint(lm_xhat(sample_r[j], l, h, inv));
+}
+
+__global__ void lm_knots_kernel(const float *xs, int64_t m, float *knots, LearnedModel *md, const uint32_t *gate) {
+  if (gate && *gate) return;
+  const int j = threadIdx.x;
+  if (j >= LM_KNOTS) return;
+  const int64_t idx = m > 0 ? (int64_t(j) * (m - 1) + (LM_KNOTS - 1) / 2) / (LM_KNOTS - 1) : 0;
+  const float xi = m > 0 ? xs[idx] : 0.f;
+  if (knots) knots[j] = xi;
+  if (md) md->c[j] = xi;
+}
+
+// Forward + backward of one point (valid == false contributes nothing); `scale`
+// is dL/dF per unit error (2 / m for the mean squared error).
+__device__ __forceinline__ void lm_point(const float *p, const float *c, float x, float y, bool valid, float scale,
+                                         GradSmem &g, int t) {
+  float a1[LM_HID], h1[LM_HID], a2[LM_HID], h2[LM_HID];
+  const float r = LM_OUT_SCALE * lm_mlp(p, x, a1, h1, a2, h2);
+  const float e = valid ? (lm_pl(c, x) + r - y) : 0.f;
+  const float d3 = scale * e * LM_OUT_SCALE;  // dL / d(b3 + w3 . h2)
+  g.x[t] = x;
+  g.d3[t] = d3;
+  g.e2[t] = e * e;
+  float d2[LM_HID];
+#pragma unroll
+  for (int j = 0; j < LM_HID; ++j) {
+    d2[j] = a2[j] > 0.f ? d3 * p[LM_P_W3 + j] : 0.f;
+    g.d2[t][j] = d2[j];
+    g.h2[t][j] = h2[j];
+  }
+#pragma unroll
+  for (int k = 0; k < LM_HID; ++k) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < LM_HID; ++j) s = fmaf(d2[j], p[LM_P_W2 + j * LM_HID + k], s);
+    g.d1[t][k] = a1[k] > 0.f ? s : 0.f;
+    g.h1[t][k] = h1[k];
+  }
+}
+
+// Gradient of parameter q summed over the CTA's points in order.
+__device__ __forceinline__ float lm_param_grad(const GradSmem &g, int q) {
+  float s = 0.f;
+  if (q < LM_P_B1) {
+    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s = fmaf(g.d1[t][q], g.x[t], s);
+  } else if (q < LM_P_W2) {
+    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.d1[t][q - LM_P_B1];
+  } else if (q < LM_P_B2) {
+    const int j = (q - LM_P_W2) / LM_HID, k = (q - LM_P_W2) % LM_HID;
+    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s = fmaf(g.d2[t][j], g.h1[t][k], s);
+  } else if (q < LM_P_W3) {
+    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.d2[t][q - LM_P_B2];
+  } else if (q < LM_P_B3) {
+    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s = fmaf(g.d3[t], g.h2[t][q - LM_P_W3], s);
+  } else if (q == LM_P_B3) {
+    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.d3[t];
+  } else {  // q == LM_PARAMS: the loss numerator
+    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.e2[t];
+  }
+  return s;
+}
+
+constexpr int LM_SLOTS = LM_PARAMS + 1;  // gradients + loss numerator
+
+// Uniform in [-1, 1) from (seed, index): initialisation stream.
+__device__ __forceinline__ float lm_unif(uint32_t seed, int i) {
+  return float(int64_t(lm_mix(((unsigned long long)seed << 32) ^ (unsigned long long)(i + 1)) >> 11)) *
+             (2.0f / 9007199254740992.0f) -
+         1.0f;
+}
+
+// Hinge-basis start: unit k of layer 1 bends at x = (k + 0.5) / 16; the
+// output layer starts at zero, so F = PL at step 0.
+__device__ __forceinline__ float lm_init_param(uint32_t seed, int q) {
+  if (q < LM_P_B1) return 4.0f + 0.5f * lm_unif(seed, q);
+  if (q < LM_P_W2) {
+    const int k = q - LM_P_B1;
+    return -(4.0f + 0.5f * lm_unif(seed, k)) * (float(k) + 0.5f) / float(LM_HID);
+  }
+  if (q < LM_P_B2) return 0.25f * lm_unif(seed, q);
+  if (q < LM_P_W3) return 0.05f * lm_unif(seed, q);
+  return 0.0f;
+}
+
+__global__ void __launch_bounds__(LM_TRAIN_BLOCK) lm_train_kernel(const float *xs, uint32_t m, LearnedModel *md,
+                                                                  float *partials, int steps, float lr,
+                                                                  uint32_t init_seed, DevHeader *hdr,
+                                                                  uint64_t timeout_ns, const uint32_t *gate) {
+  if (gate && *gate) return;
+  extern __shared__ __align__(16) uint8_t lm_smem[];
+  GradSmem &g = *reinterpret_cast<GradSmem *>(lm_smem);
+  __shared__ float p[LM_PARAMS], am[LM_PARAMS], av[LM_PARAMS], c[LM_KNOTS];
+  __shared__ float s_loss;
+  __shared__ int s_abort;
+  const int t = threadIdx.x;
+  const int G = gridDim.x;
+  for (int q = t; q < LM_PARAMS; q += LM_TRAIN_BLOCK) {
+    p[q] = lm_init_param(init_seed, q);
+    am[q] = 0.f;
+    av[q] = 0.f;
+  }
+  if (t < LM_KNOTS) c[t] = md->c[t];
+  if (t == 0) s_abort = 0;
+  // training points: T_eff evenly spaced order statistics of the sorted sample
+  const int64_t teff = m < LM_TRAIN ? int64_t(m) : int64_t(LM_TRAIN);
+  const int64_t gi = int64_t(blockIdx.x) * LM_TRAIN_BLOCK + t;
+  const bool valid = gi < teff;
+  float x = 0.f, y = 0.f;
+  if (valid) {
+    const int64_t idx = int64_t((double(gi) + 0.5) * double(m) / double(teff));
+    x = xs[idx];
+    y = (float(idx) + 0.5f) / float(m);
+  }
+  const float scale = teff > 0 ? 2.0f / float(teff) : 0.f;
+  __syncthreads();
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  float b1t = 1.f, b2t = 1.f;
+  for (int s = 0; s <= steps; ++s) {
+    lm_point(p, c, x, y, valid, scale, g, t);
+    __syncthreads();
+    float *mine = partials + (size_t(s & 1) * G + blockIdx.x) * LM_SLOTS;
+    for (int q = t; q < LM_SLOTS; q += LM_TRAIN_BLOCK) mine[q] = lm_param_grad(g, q);
+    // grid barrier s (bounded)
+    __threadfence();
+    __syncthreads();
+    if (t == 0) {
+      atomicAdd(&md->barrier, 1u);
+      const uint32_t want = uint32_t(s + 1) * uint32_t(G);
+      const uint64_t t0 = globaltimer_ns();
+      while (ld_relaxed(&md->barrier) < want) {
+        __nanosleep(32);
+        if (globaltimer_ns() - t0 > timeout_ns) {
+          set_error(hdr, AK_ERR_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const float *all = partials + size_t(s & 1) * G * LM_SLOTS;
+    b1t *= b1;
+    b2t *= b2;
+    for (int q = t; q < LM_SLOTS; q += LM_TRAIN_BLOCK) {
+      float tot = 0.f;  // fixed order over CTAs; L2 loads (other SMs wrote them)
+      for (int k = 0; k < G; ++k) tot += __ldcg(all + size_t(k) * LM_SLOTS + q);
+      if (q == LM_PARAMS) {
+        s_loss = teff > 0 ? tot / float(teff) : 0.f;
+      } else if (s < steps) {  // Adam (Kingma & Ba), bias-corrected
+        am[q] = b1 * am[q] + (1.f - b1) * tot;
+        av[q] = b2 * av[q] + (1.f - b2) * tot * tot;
+        const float mh = am[q] / (1.f - b1t), vh = av[q] / (1.f - b2t);
+        p[q] -= lr * mh / (sqrtf(vh) + eps);
+      }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && t == 0) {
+      if (s == 0) md->loss_before = s_loss;
+      if (s == steps) md->loss_after = s_loss;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int q = t; q < LM_PARAMS; q += LM_TRAIN_BLOCK) md->params[q] = p[q];
+}
+
+__global__ void __launch_bounds__(LM_TRAIN_BLOCK) lm_grad_partial_kernel(const float *x, const float *y, int64_t m,
+                                                                         const float *c, const float *params,
+                                                                         float *partials) {
+  extern __shared__ __align__(16) uint8_t lm_smem[];
+  GradSmem &g = *reinterpret_cast<GradSmem *>(lm_smem);
+  __shared__ float p[LM_PARAMS], cc[LM_KNOTS];
+  const int t = threadIdx.x;
+  for (int q = t; q < LM_PARAMS; q += LM_TRAIN_BLOCK) p[q] = params[q];
+  if (t < LM_KNOTS) cc[t] = c[t];
+  __syncthreads();
+  const int64_t i = int64_t(blockIdx.x) * LM_TRAIN_BLOCK + t;
+  const bool valid = i < m;
+  lm_point(p, cc, valid ? x[i] : 0.f, valid ? y[i] : 0.f, valid, m > 0 ? 2.0f / float(m) : 0.f, g, t);
+  __syncthreads();
+  for (int q = t; q < LM_SLOTS; q += LM_TRAIN_BLOCK) partials[size_t(blockIdx.x) * LM_SLOTS + q] = lm_param_grad(g, q);
+}
+
+__global__ void lm_grad_reduce_kernel(const float *partials, int nparts, int64_t m, float *grad, float *loss) {
+  for (int q = threadIdx.x; q < LM_SLOTS; q += blockDim.x) {
+    float tot = 0.f;
+    for (int k = 0; k < nparts; ++k) tot += partials[size_t(k) * LM_SLOTS + q];
+    if (q < LM_PARAMS) grad[q] = tot;
+    else *loss = m > 0 ? tot / float(m) : 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(1024) lm_table_kernel(LearnedModel *md, int use_mlp, uint32_t nbuckets,
+                                                        uint32_t bbits, const uint32_t *gate) {
+  if (gate && *gate) return;
+  if (threadIdx.x == 0) {
+    md->nbuckets = nbuckets;
+    md->bbits = bbits;
+  }
+  __shared__ float p[LM_PARAMS], c[LM_KNOTS];
+  __shared__ float run[1024];
+  constexpr int PER = (LM_TABLE + 1 + 1023) / 1024;  // values per thread (5)
+  const int t = threadIdx.x;
+  for (int q = t; q < LM_PARAMS; q += 1024) p[q] = md->params[q];
+  if (t < LM_KNOTS) c[t] = md->c[t];
+  __syncthreads();
+  float v[PER];
+  float mx = 0.f;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int k = t * PER + i;
+    float F = 0.f;
+    if (k <= LM_TABLE) {
+      const float u = float(k) / float(LM_TABLE);
+      F = lm_pl(c, u) + (use_mlp ? LM_OUT_SCALE * lm_mlp(p, u) : 0.f);
+      F = F > 0.f ? F : 0.f;  // NaN-safe clamp into [0, 1]
+      F = F < 1.f ? F : 1.f;
+    }
+    mx = F > mx ? F : mx;
+    v[i] = mx;  // running max inside the thread's run
+  }
+  run[t] = mx;
+  __syncthreads();
+  // exclusive running max over the thread runs (Hillis-Steele on 1024 values)
+  for (int o = 1; o < 1024; o <<= 1) {
+    const float other = t >= o ? run[t - o] : 0.f;
+    __syncthreads();
+    run[t] = run[t] > other ? run[t] : other;
+    __syncthreads();
+  }
+  const float before = t > 0 ? run[t - 1] : 0.f;
+  const uint32_t nb = nbuckets;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int k = t * PER + i;
+    if (k <= LM_TABLE) {
+      const float T = v[i] > before ? v[i] : before;
+      uint32_t K = uint32_t(__fmul_rn(T, float(nb)));
+      K = K < nb - 1 ? K : nb - 1;
+      md->tk[k] = make_float2(T, __uint_as_float(K));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) lm_plan_kernel(const uint32_t *counts, int64_t n, LearnedModel *md,
+                                                       RadixPlan *plan, DevHeader *hdr, int64_t *seg_off,
+                                                       int64_t cap) {
+  if (md->use_plain) return;
+  __shared__ unsigned long long d0[RADIX], d1[RADIX], scr[33];
+  __shared__ unsigned long long s_over, s_max;
+  __shared__ int triv[2];
+  const uint32_t nb = md->nbuckets, bb = md->bbits;
+  const int t = threadIdx.x;
+  if (t < RADIX) {
+    d0[t] = 0ull;
+    d1[t] = 0ull;
+  }
+  if (t < 2) triv[t] = 0;
+  if (t == 0) {
+    s_over = 0ull;
+    s_max = 0ull;
+  }
+  __syncthreads();
+  const uint32_t per = (nb + 1023) / 1024;
+  const uint32_t b0 = uint32_t(t) * per;
+  unsigned long long sum = 0, over = 0, mx = 0;
+  for (uint32_t b = b0; b < b0 + per && b < nb; ++b) {
+    const unsigned long long c = counts[b];
+    sum += c;
+    if (int64_t(c) > cap) over += c;
+    mx = c > mx ? c : mx;
+    if (c) {
+      atomicAdd(&d0[b & (RADIX - 1)], c);
+      if (bb > RADIX_BITS) atomicAdd(&d1[b >> RADIX_BITS], c);
+    }
+  }
+  if (over) atomicAdd(&s_over, over);
+  if (mx) atomicMax(&s_max, mx);
+  unsigned long long tot;
+  unsigned long long run = block_exclusive_scan<1024>(sum, scr, &tot);
+  for (uint32_t b = b0; b < b0 + per && b < nb; ++b) {
+    seg_off[b] = int64_t(run);
+    run += counts[b];
+  }
+  if (t == 0) seg_off[nb] = n;
+  __syncthreads();
+  const int passes = int((bb + RADIX_BITS - 1) / RADIX_BITS);
+  for (int p = 0; p < passes; ++p) {
+    const unsigned long long c = t < RADIX ? (p == 0 ? d0[t] : d1[t]) : 0ull;
+    if (t < RADIX && c == (unsigned long long)n) triv[p] = 1;
+    const unsigned long long ex = block_exclusive_scan<1024>(c, scr, &tot);
+    if (t < RADIX) plan->bin_off[p][t] = ex;
+  }
+  __syncthreads();
+  if (t == 0) {
+    uint32_t m = 0;
+    for (int p = 0; p < MAX_PASSES; ++p) plan->q[p] = (p < passes && !triv[p]) ? m++ : INACTIVE;
+    plan->m = m;
+    // fallback when more than a quarter of the keys sit in buckets above capacity
+    const uint32_t plain = (s_over * 4ull > (unsigned long long)n) ? 1u : 0u;
+    md->use_plain = plain;
+    hdr->info.path = plain ? AK_PATH_RADIX : AK_PATH_LEARNED;
+    hdr->info.radix_passes = int32_t(m);
+    hdr->info.buckets = int32_t(nb);
+    hdr->info.overfull_keys = int64_t(s_over);
+    hdr->info.max_bucket = int64_t(s_max);
+    hdr->info.loss_before = md->loss_before;
+    hdr->info.loss_after = md->loss_after;
+    hdr->info.sample_size = int64_t(md->m);
+  }
+}
+
+}  // namespace ak
+
+using namespace ak;
+
+extern "C" {
+
+ak_status ak_learned_knots(const float *d_xs, int64_t m, float *d_knots, ak_stream_t stream) {
+  if (m <= 0 || !d_xs || !d_knots) return AK_ERR_INVALID_ARG;
+  lm_knots_kernel<<<1, LM_KNOTS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_xs, m, d_knots, nullptr, nullptr);
+  return cudaGetLastError() == cudaSuccess ? AK_OK : AK_ERR_CUDA;
+}
+
+size_t ak_learned_grad_temp_bytes(int64_t m) {
+  const int64_t blocks = m > 0 ? (m + LM_TRAIN_BLOCK - 1) / LM_TRAIN_BLOCK : 1;
+  return size_t(blocks) * LM_SLOTS * sizeof(float) + 256;
+}
+
+ak_status ak_learned_loss_grad(const float *d_x, const float *d_y, int64_t m, const float *d_c,
+                               const float *d_params, float *d_grad, float *d_loss, void *d_temp, size_t temp_bytes,
+                               ak_stream_t stream) {
+  if (m < 0 || !d_c || !d_params || !d_grad || !d_loss || (m > 0 && (!d_x || !d_y))) return AK_ERR_INVALID_ARG;
+  if (!d_temp || temp_bytes < ak_learned_grad_temp_bytes(m)) return AK_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int blocks = int(m > 0 ? (m + LM_TRAIN_BLOCK - 1) / LM_TRAIN_BLOCK : 1);
+  const int smem = int(sizeof(GradSmem));
+  if (cudaFuncSetAttribute(lm_grad_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return AK_ERR_CUDA;
+  float *parts = static_cast<float *>(d_temp);
+  lm_grad_partial_kernel<<<blocks, LM_TRAIN_BLOCK, smem, st>>>(d_x, d_y, m, d_c, d_params, parts);
+  lm_grad_reduce_kernel<<<1, 352, 0, st>>>(parts, blocks, m, d_grad, d_loss);
+  return cudaGetLastError() == cudaSuccess ? AK_OK : AK_ERR_CUDA;
+}
+
+}  // extern "C"
+
+namespace ak {
+size_t learned_model_bytes() { return sizeof(LearnedModel); }
+size_t learned_partials_bytes() { return size_t(2) * LM_TRAIN_CTAS * LM_SLOTS * sizeof(float); }
+}  // namespace ak

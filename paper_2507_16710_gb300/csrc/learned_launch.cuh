@@ -1,0 +1,203 @@
+// learned_launch.cuh -- launch sequence of the learned-CDF bucketing path for one
+// key word width and key kind.
+//
+//   sample -> x-hat -> sort the sample (the library's radix path) -> knot counts
+//   -> train the residual MLP -> monotone table -> bucket histogram -> plan
+//   -> 1-2 stable onesweep passes on the bucket-id bytes -> per-bucket sort
+//   (the segmented sort, one segment per bucket)
+// The plan kernel decides on the device whether the buckets are usable; if more
+// than a quarter of the keys sit in buckets above the shared-memory capacity it
+// sets use_plain, every learned kernel after it returns at once and the plain
+// radix sequence (launched after them, gated the other way) sorts instead.  No
+// host synchronisation, so the whole call can be captured in a CUDA graph.
+#pragma once
+
+#include <algorithm>
+
+#include "internal.h"
+#include "learned.cuh"
+#include "radix_launch.cuh"
+
+namespace ak {
+
+// Full histogram of bucket ids: 16-bit shared counters (two per word); a
+// counter that reaches 0x8000 moves 0x8000 to the global count, so no counter
+// can carry into its neighbour while up to 1024 threads increment it.
+template <typename U, int KIND>
+__global__ void __launch_bounds__(1024) lm_hist_kernel(const U *__restrict__ keys, int64_t n, U flip,
+                                                       const LearnedModel *md, uint32_t *counts, uint4 *zero_buf,
+                                                       int64_t zero_vec) {
+  if (md->use_plain) return;
+  extern __shared__ uint32_t hw[];
+  const uint32_t nb = md->nbuckets;
+  for (uint32_t i = threadIdx.x; i < nb / 2; i += blockDim.x) hw[i] = 0u;
+  const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = gtid; i < zero_vec; i += stride) zero_buf[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  for (int64_t i = gtid; i < n; i += stride) {
+    const uint32_t b = lm_key_bucket<KIND>(md, keys[i], flip);
+    const uint32_t sh = (b & 1u) * 16u;
+    const uint32_t old = atomicAdd(&hw[b >> 1], 1u << sh);
+    if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
+      atomicSub(&hw[b >> 1], 0x8000u << sh);
+      atomicAdd(&counts[b], 0x8000u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
+    const uint32_t c = (hw[i >> 1] >> ((i & 1u) * 16u)) & 0xFFFFu;
+    if (c) atomicAdd(&counts[i], c);
+  }
+}
+
+// Plan of the learned passes, CSR offsets of the buckets, statistics and the
+// fallback decision.  One CTA of 1024 threads.
+__global__ void lm_plan_kernel(const uint32_t *counts, int64_t n, LearnedModel *md, RadixPlan *plan, DevHeader *hdr,
+                               int64_t *seg_off, int64_t cap);
+
+template <typename U, int KIND>
+cudaError_t radix_launch_kind(const RadixCall &c);
+template <> inline cudaError_t radix_launch_kind<uint16_t, KIND_UINT>(const RadixCall &c) { return radix_launch_u16_uint(c); }
+template <> inline cudaError_t radix_launch_kind<uint16_t, KIND_SINT>(const RadixCall &c) { return radix_launch_u16_sint(c); }
+template <> inline cudaError_t radix_launch_kind<uint32_t, KIND_UINT>(const RadixCall &c) { return radix_launch_u32_uint(c); }
+template <> inline cudaError_t radix_launch_kind<uint32_t, KIND_SINT>(const RadixCall &c) { return radix_launch_u32_sint(c); }
+template <> inline cudaError_t radix_launch_kind<uint32_t, KIND_FLOAT>(const RadixCall &c) { return radix_launch_u32_float(c); }
+template <> inline cudaError_t radix_launch_kind<uint64_t, KIND_UINT>(const RadixCall &c) { return radix_launch_u64_uint(c); }
+template <> inline cudaError_t radix_launch_kind<uint64_t, KIND_SINT>(const RadixCall &c) { return radix_launch_u64_sint(c); }
+template <> inline cudaError_t radix_launch_kind<uint64_t, KIND_FLOAT>(const RadixCall &c) { return radix_launch_u64_float(c); }
+
+template <typename U, int KIND>
+cudaError_t seg_launch_kind(const SegCall &c);
+template <> inline cudaError_t seg_launch_kind<uint16_t, KIND_UINT>(const SegCall &c) { return seg_launch_u16_uint(c); }
+template <> inline cudaError_t seg_launch_kind<uint16_t, KIND_SINT>(const SegCall &c) { return seg_launch_u16_sint(c); }
+template <> inline cudaError_t seg_launch_kind<uint32_t, KIND_UINT>(const SegCall &c) { return seg_launch_u32_uint(c); }
+template <> inline cudaError_t seg_launch_kind<uint32_t, KIND_SINT>(const SegCall &c) { return seg_launch_u32_sint(c); }
+template <> inline cudaError_t seg_launch_kind<uint32_t, KIND_FLOAT>(const SegCall &c) { return seg_launch_u32_float(c); }
+template <> inline cudaError_t seg_launch_kind<uint64_t, KIND_UINT>(const SegCall &c) { return seg_launch_u64_uint(c); }
+template <> inline cudaError_t seg_launch_kind<uint64_t, KIND_SINT>(const SegCall &c) { return seg_launch_u64_sint(c); }
+template <> inline cudaError_t seg_launch_kind<uint64_t, KIND_FLOAT>(const SegCall &c) { return seg_launch_u64_float(c); }
+
+// The learned passes (digits = bytes of the bucket id) with the radix pass kernel.
+template <typename U, typename V, bool HAS_V, int KIND, typename S>
+cudaError_t lm_passes(const RadixCall &c, const LearnedCall &lc) {
+  constexpr int CFG = 0;
+  constexpr int BLOCK = CFG_BLOCK[CFG];
+  constexpr int ITEMS = tile_items(sizeof(U), HAS_V ? sizeof(V) : 0, CFG);
+  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS, 1, DIGIT_LEARNED>;
+  auto kern = onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, 1, false, DIGIT_LEARNED>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::BYTES));
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (c.n + L::TILE - 1) / L::TILE;
+  PassArgs<U, V> a{};
+  a.k_in = reinterpret_cast<const U *>(c.k_in);
+  a.k_final = reinterpret_cast<U *>(c.k_final);
+  a.k_alt0 = reinterpret_cast<U *>(c.k_alt0);
+  a.k_alt1 = reinterpret_cast<U *>(c.k_alt1);
+  a.v_in = reinterpret_cast<const V *>(c.v_in);
+  a.v_final = reinterpret_cast<V *>(c.v_final);
+  a.v_alt = reinterpret_cast<V *>(c.v_alt);
+  a.n = c.n;
+  a.kind = c.kind;
+  a.flip = c.descending ? U(~U(0)) : U(0);
+  a.mode = MODE_INPLACE;
+  a.plan = c.plan;
+  a.hdr = c.hdr;
+  a.timeout_ns = c.timeout_ns;
+  a.num_tiles = tiles;
+  a.model = lc.model;
+  a.gate = &lc.model->use_plain;
+  a.gate_want = 0;
+  // histogram of bucket ids (zeroes the first pass's look-back words)
+  {
+    const int64_t zero_vec = tiles * RADIX * int64_t(sizeof(S)) / 16;
+    const size_t hsm = size_t(lc.nbuckets / 2) * 4;
+    auto hk = lm_hist_kernel<U, KIND>;
+    e = cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hsm));
+    if (e != cudaSuccess) return e;
+    hk<<<device_sm_count(), 1024, hsm, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, a.flip, lc.model,
+                                                   lc.bucket_counts, reinterpret_cast<uint4 *>(c.status[0]),
+                                                   zero_vec);
+  }
+  lm_plan_kernel<<<1, 1024, 0, c.stream>>>(lc.bucket_counts, c.n, lc.model, c.plan, c.hdr, lc.seg_off, lc.seg_capacity);
+  const int passes = int((lc.bucket_bits + RADIX_BITS - 1) / RADIX_BITS);
+  for (int p = 0; p < passes; ++p) {
+    a.pass = p;
+    a.status_cur = c.status[p & 1];
+    a.status_next = (p + 1 < passes) ? c.status[(p + 1) & 1] : nullptr;
+    kern<<<unsigned(tiles), BLOCK, L::BYTES, c.stream>>>(a);
+  }
+  {
+    const int64_t want = (c.n + 1023) / 1024;
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(device_sm_count()) * 4)));
+    finish_kernel<U, V, HAS_V><<<g, 256, 0, c.stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename U, typename V, bool HAS_V, int KIND>
+cudaError_t lm_passes_s(const RadixCall &c, const LearnedCall &lc) {
+  if (c.status_wide) return lm_passes<U, V, HAS_V, KIND, unsigned long long>(c, lc);
+  return lm_passes<U, V, HAS_V, KIND, uint32_t>(c, lc);
+}
+
+template <typename U, int KIND>
+cudaError_t learned_launch(const RadixCall &c, const LearnedCall &lc) {
+  if (c.n == 0) return cudaSuccess;
+  cudaError_t e;
+  const U flip = c.descending ? U(~U(0)) : U(0);
+  const int sms = device_sm_count();
+  // 1. sample and its range
+  {
+    const int g = int(std::min<int64_t>((lc.m + 255) / 256, int64_t(sms) * 4));
+    lm_sample_kernel<U, KIND><<<g, 256, 0, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, flip, lc.m,
+                                                       lc.seed, lc.sample_r, lc.model, nullptr);
+    lm_xhat_kernel<<<g, 256, 0, c.stream>>>(lc.sample_r, lc.m, lc.model, lc.xs, nullptr);
+  }
+  // 2. sort the sample (x-hat >= 0, so its fp32 bits sort as unsigned integers)
+  if ((e = radix_launch_u32_uint(lc.sample_sort)) != cudaSuccess) return e;
+  // 3. piecewise-linear CDF, residual MLP, monotone table
+  lm_knots_kernel<<<1, LM_KNOTS, 0, c.stream>>>(reinterpret_cast<const float *>(lc.xs), lc.m, nullptr, lc.model,
+                                                  nullptr);
+  if (lc.train_steps > 0) {
+    const int smem = int(sizeof(GradSmem));
+    if ((e = cudaFuncSetAttribute(lm_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(LM_TRAIN_CTAS);
+    cfg.blockDim = dim3(LM_TRAIN_BLOCK);
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident for the grid barrier
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, lm_train_kernel, reinterpret_cast<const float *>(lc.xs), lc.m, lc.model,
+                                lc.partials, lc.train_steps, lc.lr, lc.seed ^ 0x5EEDu, c.hdr, c.timeout_ns,
+                                static_cast<const uint32_t *>(nullptr))) != cudaSuccess)
+      return e;
+  }
+  lm_table_kernel<<<1, 1024, 0, c.stream>>>(lc.model, lc.train_steps > 0 ? 1 : 0, lc.nbuckets, lc.bucket_bits,
+                                            nullptr);
+  // 4. bucket histogram, plan, learned passes (all skip themselves on fallback)
+  switch (c.val_bytes) {
+    case 0: e = lm_passes_s<U, uint32_t, false, KIND>(c, lc); break;
+    case 1: e = lm_passes_s<U, uint8_t, true, KIND>(c, lc); break;
+    case 2: e = lm_passes_s<U, uint16_t, true, KIND>(c, lc); break;
+    case 4: e = lm_passes_s<U, uint32_t, true, KIND>(c, lc); break;
+    case 8: e = lm_passes_s<U, unsigned long long, true, KIND>(c, lc); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  // 5. sort inside every bucket
+  if ((e = seg_launch_kind<U, KIND>(lc.finish)) != cudaSuccess) return e;
+  // 6. fallback: the plain radix sequence, run only when use_plain was set
+  RadixCall plain = c;
+  plain.gate = &lc.model->use_plain;
+  plain.gate_want = 1;
+  plain.path_tag = 0;
+  return radix_launch_kind<U, KIND>(plain);
+}
+
+}  // namespace ak

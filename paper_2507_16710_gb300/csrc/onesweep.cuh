@@ -22,6 +22,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "learned.cuh"
 
 namespace ak {
 
@@ -68,13 +69,26 @@ struct PassArgs {
   DevHeader *hdr;
   uint64_t timeout_ns;
   int debug_skip;     // AK_DEBUG_SKIP_FIRST_TILE: tile ids start at 1
+  const LearnedModel *model;  // learned digits: bucket id of the key
+  const uint32_t *gate;       // if set, run only when *gate == gate_want
+  uint32_t gate_want;
 };
+
+// Digit of a key in a pass: a radix digit, or a byte of the learned bucket id.
+enum DigitSource : int { DIGIT_RADIX = 0, DIGIT_LEARNED = 1 };
+template <int DIGIT, int KIND, typename U, typename V>
+__device__ __forceinline__ uint32_t pass_digit(const PassArgs<U, V> &a, U k, int shift) {
+  if constexpr (DIGIT == DIGIT_LEARNED) return (lm_key_bucket<KIND>(a.model, k, a.flip) >> shift) & (RADIX - 1);
+  else return digit_of(radix_key_t<KIND>(k, a.flip), shift);
+}
 
 // ------------------------------------------------------------------ histogram
 template <typename U, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) hist_kernel(const U *__restrict__ keys, int64_t n, int kind,
                                                      U flip, unsigned long long *counts,
-                                                     uint4 *zero_buf, int64_t zero_vec) {
+                                                     uint4 *zero_buf, int64_t zero_vec,
+                                                     const uint32_t *gate, uint32_t gate_want) {
+  if (gate && *gate != gate_want) return;
   constexpr int PASSES = sizeof(U);
   __shared__ uint32_t sh[2][PASSES * RADIX];
   for (int i = threadIdx.x; i < 2 * PASSES * RADIX; i += BLOCK) (&sh[0][0])[i] = 0;
@@ -113,7 +127,8 @@ __global__ void __launch_bounds__(BLOCK) hist_kernel(const U *__restrict__ keys,
 // One CTA of RADIX threads.
 static __global__ void __launch_bounds__(RADIX) plan_kernel(const unsigned long long *counts, int64_t n,
                                                      int passes, RadixPlan *plan, DevHeader *hdr,
-                                                     int path_tag) {
+                                                     int path_tag, const uint32_t *gate, uint32_t gate_want) {
+  if (gate && *gate != gate_want) return;
   __shared__ unsigned long long scratch[RADIX / 32 + 1];
   __shared__ int triv[MAX_PASSES];
   if (threadIdx.x < MAX_PASSES) triv[threadIdx.x] = 0;
@@ -142,7 +157,7 @@ static __global__ void __launch_bounds__(RADIX) plan_kernel(const unsigned long 
 // write-out of the current one.  Forward progress of the look-back: every CTA
 // processes the tiles it holds in increasing order, so the holder of the
 // smallest unfinished tile only waits on finished tiles.
-template <typename U, typename V, bool HAS_V, int BLOCK, int ITEMS, int STAGES>
+template <typename U, typename V, bool HAS_V, int BLOCK, int ITEMS, int STAGES, int DIGIT = DIGIT_RADIX>
 struct PassSmem {
   static constexpr int TILE = BLOCK * ITEMS;
   static constexpr int NW = BLOCK / 32;
@@ -159,7 +174,8 @@ struct PassSmem {
   static constexpr size_t OFF_BAR = (OFF_SCR + (NW + 1) * 4 + 15) / 16 * 16;             // u64[STAGES]
   static constexpr size_t OFF_TILE = OFF_BAR + 8 * STAGES;                                // u32[STAGES]
   static constexpr size_t OFF_FLAG = OFF_TILE + 4 * STAGES;                               // u32
-  static constexpr size_t BYTES = OFF_FLAG + 16;
+  static constexpr size_t OFF_DIG = OFF_FLAG + 16;  // u8[TILE]: digits in tile order (learned digits)
+  static constexpr size_t BYTES = OFF_DIG + (DIGIT == DIGIT_LEARNED ? size_t(TILE) : 0);
   static_assert(TILE < 65536, "warp bases are u16");
   static_assert(KEYS % 16 == 0 && STAGE % 128 == 0 && OFF_MASK % 16 == 0 && OFF_KPTR % 8 == 0 &&
                     OFF_BAR % 8 == 0,
@@ -196,9 +212,9 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d, bool nine_bits) {
 }
 
 template <typename U, typename V, bool HAS_V, int KIND, typename S, int BLOCK, int ITEMS, int STAGES,
-          bool PERSIST>
+          bool PERSIST, int DIGIT = DIGIT_RADIX>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U, V> a) {
-  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS, STAGES>;
+  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS, STAGES, DIGIT>;
   constexpr int TILE = L::TILE;
   constexpr int NW = L::NW;
   constexpr int HROW = L::HROW;
@@ -216,6 +232,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
   uint32_t *s_tile = reinterpret_cast<uint32_t *>(smem + L::OFF_TILE);
   uint32_t *s_flag = reinterpret_cast<uint32_t *>(smem + L::OFF_FLAG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t *s_dig = smem + L::OFF_DIG;
+  if (a.gate && *a.gate != a.gate_want) return;
 
   // Clear the next pass's look-back rows (the grid covers rows blockIdx.x + k*gridDim.x).
   if (a.status_next) {
@@ -320,7 +338,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       const int idx = wbase + i * 32 + lane;
-      dr[i] = (idx < tile_n) ? digit_of(radix_key_t<KIND>(sk[idx], a.flip), shift) : uint32_t(RADIX);
+      dr[i] = (idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -382,6 +400,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
         const uint32_t pos = uint32_t(wh[d]) + (dr[i] >> 9);
         ok[pos] = sk[idx];
         if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
+        if (DIGIT == DIGIT_LEARNED) s_dig[pos] = uint8_t(d);
       }
     }
 
@@ -437,14 +456,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
       for (int r = 0; r < ITEMS; ++r) {
         const int i = r * BLOCK + tid;
         const U k = ok[i];
-        const uint32_t d = digit_of(radix_key_t<KIND>(k, a.flip), shift);
+        const uint32_t d = DIGIT == DIGIT_LEARNED ? uint32_t(s_dig[i]) : digit_of(radix_key_t<KIND>(k, a.flip), shift);
         if (write_keys) reinterpret_cast<U *>(s_kptr[d])[i] = k;
         if (HAS_V) reinterpret_cast<V *>(s_vptr[d])[i] = ov[i];
       }
     } else {
       for (int i = tid; i < tile_n; i += BLOCK) {
         const U k = ok[i];
-        const uint32_t d = digit_of(radix_key_t<KIND>(k, a.flip), shift);
+        const uint32_t d = DIGIT == DIGIT_LEARNED ? uint32_t(s_dig[i]) : digit_of(radix_key_t<KIND>(k, a.flip), shift);
         if (write_keys) reinterpret_cast<U *>(s_kptr[d])[i] = k;
         if (HAS_V) reinterpret_cast<V *>(s_vptr[d])[i] = ov[i];
       }
@@ -481,6 +500,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
 // --------------------------------------------------------------------- finish
 template <typename U, typename V, bool HAS_V>
 __global__ void finish_kernel(PassArgs<U, V> a) {
+  if (a.gate && *a.gate != a.gate_want) return;
   const uint32_t m = a.plan->m;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;

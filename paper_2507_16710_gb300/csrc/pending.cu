@@ -3,12 +3,6 @@
 #include "internal.h"
 
 extern "C" {
-ak_status ak_learned_knot_counts(const float *, int64_t, int32_t *, ak_stream_t) { return AK_ERR_UNSUPPORTED; }
-ak_status ak_learned_loss_grad(const float *, const float *, int64_t, const float *, const float *, float *,
-                               float *, void *, size_t, ak_stream_t) {
-  return AK_ERR_UNSUPPORTED;
-}
-size_t ak_learned_grad_temp_bytes(int64_t) { return 0; }
 ak_status ak_autotune(int, int64_t, ak_dtype, int, ak_order, void *, void *, uint32_t *, void *, size_t,
                       ak_stream_t, ak_options *) {
   return AK_ERR_UNSUPPORTED;

@@ -45,9 +45,10 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 8)));
     const int64_t zero_vec = tiles * RADIX * int64_t(sizeof(S)) / 16;
     hist_kernel<U, HB><<<grid, HB, 0, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, c.kind, a.flip,
-                                                   c.counts, reinterpret_cast<uint4 *>(c.status[0]), zero_vec);
+                                                   c.counts, reinterpret_cast<uint4 *>(c.status[0]), zero_vec,
+                                                   c.gate, c.gate_want);
   }
-  plan_kernel<<<1, RADIX, 0, c.stream>>>(c.counts, c.n, PASSES, c.plan, c.hdr, c.path_tag);
+  plan_kernel<<<1, RADIX, 0, c.stream>>>(c.counts, c.n, PASSES, c.plan, c.hdr, c.path_tag, c.gate, c.gate_want);
   const int64_t resident = PERSIST ? int64_t(resident_ctas(kern, BLOCK, L::BYTES)) * sms : tiles;
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, resident)));
   for (int p = 0; p < PASSES; ++p) {
@@ -84,6 +85,8 @@ cudaError_t run_status(const RadixCall &c) {
   a.hdr = c.hdr;
   a.timeout_ns = c.timeout_ns;
   a.debug_skip = (c.debug_flags & AK_DEBUG_SKIP_FIRST_TILE) ? 1 : 0;
+  a.gate = c.gate;
+  a.gate_want = c.gate_want;
   if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, 0>(c, a);
   switch (c.tile_config) {
     case 1: return run_passes<U, V, HAS_V, KIND, uint32_t, 1>(c, a);

@@ -30,6 +30,8 @@ cudaError_t seg_run(const SegCall &c) {
   a.order = c.off ? c.order : nullptr;
   a.hdr = c.hdr;
   a.path_tag = c.path_tag;
+  a.gate = c.gate;
+  a.gate_want = c.gate_want;
   a.keys = reinterpret_cast<U *>(c.keys);
   a.vals = reinterpret_cast<V *>(c.vals);
   a.alt_k = reinterpret_cast<U *>(c.alt_k);
@@ -38,7 +40,8 @@ cudaError_t seg_run(const SegCall &c) {
   a.seg_base = 0;
   if (c.off && c.nseg > 0) {
     const int64_t g = (c.nseg + 255) / 256;
-    classify_kernel<<<unsigned(g), 256, 0, c.stream>>>(c.off, c.nseg, c.n, CAP, c.order, c.counters);
+    classify_kernel<<<unsigned(g), 256, 0, c.stream>>>(c.off, c.nseg, c.n, CAP, c.order, c.counters, c.gate,
+                                                       c.gate_want);
   }
   const int64_t resident = int64_t(resident_ctas(kern, SEG_BLOCK, Lay::BYTES)) * device_sm_count();
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(a.nseg, resident)));

@@ -27,6 +27,8 @@ struct SegArgsBase {
   const uint32_t *order;  // work order (segment ids), nseg entries (NULL with off == NULL)
   DevHeader *hdr;
   int path_tag;           // written to ak_info.path by block 0
+  const uint32_t *gate;   // if set, run only when *gate == gate_want
+  uint32_t gate_want;
 };
 
 template <typename U, typename V>
@@ -42,7 +44,8 @@ struct SegArgs : SegArgsBase {
 // ------------------------------------------------------------- classification
 // Work order: segments longer than `cap` from the front, the others from the back.
 static __global__ void classify_kernel(const int64_t *off, int64_t nseg, int64_t n, int64_t cap, uint32_t *order,
-                                       uint32_t *counters) {
+                                       uint32_t *counters, const uint32_t *gate, uint32_t gate_want) {
+  if (gate && *gate != gate_want) return;
   const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
   int64_t lo = off[s], hi = off[s + 1];
@@ -367,6 +370,7 @@ struct SegCta {
 template <typename U, typename V, bool HAS_V, int KIND, int BLOCK, int ITEMS, int CAP>
 __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
   using C = SegCta<U, V, HAS_V, KIND, BLOCK, ITEMS, CAP>;
+  if (a.gate && *a.gate != a.gate_want) return;
   extern __shared__ __align__(128) uint8_t smem[];
   C c;
   c.init(smem, a.flip);
