@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--n", type=int, default=FULL_N, help="keys per array (default: the full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
+                    help="c2 (default): the headline line; the others print their own lines")
     return ap.parse_args()
 
 
@@ -383,12 +385,172 @@ def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n):
             "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3), "steps": steps}
 
 
+# ------------------------------------------------------------ other workloads
+def _timed(torch, stream, flush, restore, call, warmup, steps):
+    """Median device time (ms) of call(); restore() and an L2 flush run before
+    every call, outside the events."""
+    for _ in range(warmup):
+        restore()
+        call()
+    ms = []
+    for _ in range(steps):
+        restore()
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def _line(args, workload, value, extra):
+    line = {"metric": METRIC, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic (seeded splitmix64)",
+            "config": {"workload": workload}, "value": round(value, 3)}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_workload(args):
+    import torch
+
+    import paper_2507_16710_gb300 as ak
+    import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, _ = load_peaks()
+    W, K = args.warmup, args.steps
+
+    def sort_gbs(host, kd, opts, op="sort", vals=None, order="ascending"):
+        """Key GB/s of one operation on `host` keys (device-timed)."""
+        unsigned = host.dtype.kind == "u"
+        view = {1: np.int8, 2: np.int16, 4: np.int32, 8: np.int64}[host.itemsize] if unsigned else host.dtype
+        pristine = torch.from_numpy(host.view(view)).to(dev)
+        work = torch.empty_like(pristine)
+        o = ak.Options()
+        for k, v in (opts or {}).items():
+            setattr(o, k, v)
+        if op == "pairs":
+            vp = torch.from_numpy(vals.view(np.int32)).to(dev)
+            vw = torch.empty_like(vp)
+            tb = ak.temp_bytes(ak.AK_OP_SORT_PAIRS, host.size, kd, 4, options=o)
+        else:
+            vp = vw = None
+            tb = ak.temp_bytes(ak.AK_OP_SORT, host.size, kd, options=o)
+        temp = ak.workspace(tb, dev)
+        lib = ak.load()
+        od = ak.order_code(order)
+
+        def restore():
+            work.copy_(pristine)
+            if vw is not None:
+                vw.copy_(vp)
+
+        def call():
+            if op == "pairs":
+                rc = lib.ak_sort_pairs(work.data_ptr(), vw.data_ptr(), 4, host.size, kd, od, temp.data_ptr(),
+                                       temp.numel(), stream.cuda_stream, ctypes.byref(o))
+            else:
+                rc = lib.ak_sort(work.data_ptr(), host.size, kd, od, temp.data_ptr(), temp.numel(),
+                                 stream.cuda_stream, ctypes.byref(o))
+            if rc:
+                raise ak.AkError(rc, op)
+
+        ms = _timed(torch, stream, flush, restore, call, W, K)
+        info = ak.ak_last_info(temp)
+        del pristine, work, temp, vp, vw
+        torch.cuda.empty_cache()
+        return host.nbytes / (ms / 1e3) / 1e9, ms, info
+
+    if args.workload == "c1":
+        keys = synth.uniform_u32(1 << 20, seed=1)
+        res = {}
+        for name, opts in (("auto", None), ("radix", {"path": ak.AK_PATH_RADIX}), ("block", {"path": ak.AK_PATH_BLOCK})):
+            gbs, ms, info = sort_gbs(keys, ak.AK_U32, opts)
+            res[name] = {"GBps": round(gbs, 2), "ms": round(ms, 4), "path": info["path"]}
+        best = max(v["GBps"] for v in res.values())
+        _line(args, "1,048,576 u32 uniform, ak_sort ascending (L2-resident)", best,
+              {"dtype": "u32", "results": res})
+    elif args.workload == "c3":
+        n = args.n if args.n != FULL_N else 100_000_000
+        res, tot_b, tot_l, tot_p = {}, 0, 0.0, 0.0
+        for i, dist in enumerate(synth.F64_DISTS):
+            keys = synth.dist_f64(n, dist, seed=10 + i)
+            gp, mp, _ = sort_gbs(keys, ak.AK_F64, {"path": ak.AK_PATH_RADIX})
+            gl, ml, info = sort_gbs(keys, ak.AK_F64, {"path": ak.AK_PATH_LEARNED})
+            res[dist] = {"plain_GBps": round(gp, 2), "learned_GBps": round(gl, 2), "plain_ms": round(mp, 3),
+                         "learned_ms": round(ml, 3), "learned_path_taken": info["path"] == ak.AK_PATH_LEARNED,
+                         "overfull_frac": round(info["overfull_keys"] / n, 4),
+                         "loss_before": info["loss_before"], "loss_after": info["loss_after"]}
+            tot_b += keys.nbytes
+            tot_l += ml
+            tot_p += mp
+        big = {}
+        for i, dist in enumerate(("uniform", "normal")):
+            keys = synth.dist_f64(FULL_N, dist, seed=10 + synth.F64_DISTS.index(dist))
+            gp, mp, _ = sort_gbs(keys, ak.AK_F64, {"path": ak.AK_PATH_RADIX})
+            gl, ml, info = sort_gbs(keys, ak.AK_F64, {"path": ak.AK_PATH_LEARNED})
+            big[dist] = {"plain_GBps": round(gp, 2), "learned_GBps": round(gl, 2),
+                         "learned_path_taken": info["path"] == ak.AK_PATH_LEARNED}
+            del keys
+        value = tot_b / (tot_l / 1e3) / 1e9
+        _line(args, f"{n:,} float64 x 6 distributions, ak_sort ascending: learned-CDF bucketing vs plain radix",
+              value, {"dtype": "u64 radix keys (float64)", "learned_GBps_all": round(value, 3),
+                      "plain_GBps_all": round(tot_b / (tot_p / 1e3) / 1e9, 3), "results": res,
+                      "smooth_268M": big, "literal_2x_key_bytes_frac_of_8TBs": round(2 * value / NOMINAL_HBM_GBS, 4)})
+    elif args.workload == "c4":
+        off = synth.lognormal_segments(65536, seed=20)
+        n = int(off[-1])
+        keys = synth.uniform_u32(n, seed=21)
+        pristine = torch.from_numpy(keys.view(np.int32)).to(dev)
+        work = torch.empty_like(pristine)
+        o = torch.from_numpy(off).to(dev)
+        temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT_SEGMENTED, n, ak.AK_U32, nseg=off.size - 1), dev)
+        s = torch.cuda.Stream()
+        work.copy_(pristine)
+        ak.ak_sort_segmented(work, o, temp=temp, stream=s, unsigned=True)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ak.ak_sort_segmented(work, o, temp=temp, stream=s, unsigned=True)
+
+        def restore():
+            work.copy_(pristine)
+
+        def call():
+            g.replay()
+
+        ms = _timed(torch, torch.cuda.current_stream(dev), flush, restore, call, W, K)
+        gbs = keys.nbytes / (ms / 1e3) / 1e9
+        _line(args, f"65,536 segments, lognormal lengths (median 2,048), {n:,} u32 keys, one persistent launch "
+              "replayed from a CUDA graph", gbs,
+              {"dtype": "u32", "ms": round(ms, 4), "keys": n, "roofline_2x_bytes_frac_of_measured": round(2 * gbs / peak, 4)})
+    elif args.workload == "c5":
+        n = args.n if args.n != FULL_N else 1 << 30
+        keys = synth.zipf_mix_u32(n, seed=30)
+        vals = np.arange(n, dtype=np.uint32)
+        gp, mp, _ = sort_gbs(keys, ak.AK_U32, {"path": ak.AK_PATH_RADIX}, op="pairs", vals=vals, order="descending")
+        gl, ml, info = sort_gbs(keys, ak.AK_U32, {"path": ak.AK_PATH_LEARNED}, op="pairs", vals=vals,
+                                order="descending")
+        _line(args, f"{n:,} u32 keys (Zipf s=1.1 over 2^24 + uniform, 50/50) with u32 values, descending pairs: "
+              "learned vs plain", max(gp, gl),
+              {"dtype": "u32", "plain_GBps": round(gp, 3), "learned_GBps": round(gl, 3), "plain_ms": round(mp, 3),
+               "learned_ms": round(ml, 3), "learned_path_taken": info["path"] == ak.AK_PATH_LEARNED,
+               "overfull_frac": round(info["overfull_keys"] / n, 4),
+               "keys_plus_values_GBps_plain": round(2 * gp, 3), "keys_plus_values_GBps_learned": round(2 * gl, 3)})
+
+
 def main():
     args = parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "c2":
+        run_workload(args)
     else:
         run_ours(args)
 

@@ -94,6 +94,8 @@ typedef struct ak_options {
  * that reaches it waits until timeout_ns and the call ends with AK_ERR_TIMEOUT
  * (the keys are then unspecified).  Exercises the bounded-wait error path. */
 #define AK_DEBUG_SKIP_FIRST_TILE 1
+/* Tuning hook: no L2 prefetch of upcoming tiles in the digit passes. */
+#define AK_DEBUG_NO_PREFETCH 2
 
 #define AK_TILE_CONFIGS 3
 
@@ -103,7 +105,7 @@ typedef struct ak_info {
     int32_t path;            /* ak_path actually executed (learned may fall back to radix) */
     int32_t radix_passes;    /* digit passes that moved data (trivial passes skipped) */
     int32_t buckets;         /* learned: bucket count used */
-    int64_t overfull_keys;   /* learned: keys in buckets above the shared-memory capacity */
+    int64_t overfull_keys;   /* learned: keys in buckets above 16x the shared-memory capacity */
     int64_t max_bucket;      /* learned: largest bucket */
     float loss_before;       /* learned: training loss of the piecewise-linear CDF alone */
     float loss_after;        /* learned: training loss after the MLP residual is trained */

@@ -152,6 +152,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
       : "memory");
 }
 
+// Hint: pull `bytes` (multiple of 16, 16-byte aligned) of global memory into L2.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src_gmem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
+}
+
 // Bounded wait on an mbarrier phase.  On timeout the error is recorded and the
 // caller must not touch the destination buffer until a second bounded wait
 // confirms the copy landed (see wait_copy_or_fail).

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(1024) lm_plan_kernel(const uint32_t *counts, i
   for (uint32_t b = b0; b < b0 + per && b < nb; ++b) {
     const unsigned long long c = counts[b];
     sum += c;
-    if (int64_t(c) > cap) over += c;
+    if (int64_t(c) > 16 * cap) over += c;  // far above capacity: more than one split away
     mx = c > mx ? c : mx;
     if (c) {
       atomicAdd(&d0[b & (RADIX - 1)], c);

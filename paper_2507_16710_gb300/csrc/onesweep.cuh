@@ -72,6 +72,7 @@ struct PassArgs {
   const LearnedModel *model;  // learned digits: bucket id of the key
   const uint32_t *gate;       // if set, run only when *gate == gate_want
   uint32_t gate_want;
+  int64_t prefetch_ahead;     // one-tile CTAs: L2-prefetch the tile this many ids ahead (0: off)
 };
 
 // Digit of a key in a pass: a radix digit, or a byte of the learned bucket id.
@@ -294,6 +295,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
       const int64_t t = next_tile();
       s_tile[s] = uint32_t(t < a.num_tiles ? t : a.num_tiles);
       issue(s, t);
+      // one-tile CTAs: pull the tile about one residency wave ahead into L2 so
+      // HBM stays busy while CTAs rank, look back and write
+      if (!PERSIST && a.prefetch_ahead > 0) {
+        const int64_t tp = t + a.prefetch_ahead;
+        if (tp < full_tiles && aligned) {
+          bulk_prefetch_l2(ksrc + tp * TILE, uint32_t(L::KEYS));
+          if (load_v) bulk_prefetch_l2(vsrc + tp * TILE, uint32_t(L::VALS));
+        }
+      }
     }
     *s_flag = 0;
     // the first stage must be resident before the loop starts

@@ -49,8 +49,10 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
                                                    c.gate, c.gate_want);
   }
   plan_kernel<<<1, RADIX, 0, c.stream>>>(c.counts, c.n, PASSES, c.plan, c.hdr, c.path_tag, c.gate, c.gate_want);
-  const int64_t resident = PERSIST ? int64_t(resident_ctas(kern, BLOCK, L::BYTES)) * sms : tiles;
+  const int64_t wave = int64_t(resident_ctas(kern, BLOCK, L::BYTES)) * sms;
+  const int64_t resident = PERSIST ? wave : tiles;
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, resident)));
+  a.prefetch_ahead = (c.debug_flags & AK_DEBUG_NO_PREFETCH) ? 0 : wave;
   for (int p = 0; p < PASSES; ++p) {
     a.pass = p;
     a.status_cur = c.status[p & 1];

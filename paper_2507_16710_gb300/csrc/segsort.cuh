@@ -8,10 +8,11 @@
 //     vary inside it are found (OR of r ^ r0); LSD passes over only those bits
 //     run between two shared buffers, chunk by chunk with stable warp ranks and
 //     running digit offsets; the result is written back once.
-//   * L > CAP: one stable MSD pass through global memory on the top 8 varying
-//     bits (workspace copy of the segment), then each of the 256 buckets is
-//     sorted in shared memory like a small segment -- or, if a bucket is still
-//     above CAP, by chunked LSD passes through global memory.
+//   * L > CAP: one stable MSD pass through global memory on the top varying
+//     bits (just enough that buckets average CAP/2 keys; workspace copy of the
+//     segment), then each bucket is sorted in shared memory like a small
+//     segment -- or, if a bucket is still above CAP, by chunked LSD passes
+//     through global memory.
 // Every pass is stable, so every segment ends in the stable order of the key
 // transform of common.cuh.  Raw key bits (and values) are moved.
 #pragma once
@@ -332,13 +333,19 @@ struct SegCta {
     }
   }
 
-  // Segment above CAP: MSD split on the top 8 varying bits, then each bucket.
+  // Segment above CAP: one stable MSD split on the top varying bits -- just
+  // enough of them that buckets average about CAP/2 keys -- then every bucket
+  // is sorted in shared memory (or, if still above CAP, by chunked passes
+  // through global memory).
   __device__ void sort_large(U *gk, V *gv, U *ak, V *av, int64_t len) {
     const unsigned long long vary = vary_bits(gk, len);
     if (vary == 0) return;
     const int lo = __ffsll((long long)vary) - 1;
     const int hi = 63 - __clzll((long long)vary);
-    const int top = (hi - RADIX_BITS + 1) > lo ? (hi - RADIX_BITS + 1) : lo;
+    int bits = 1;
+    while (bits < RADIX_BITS && (int64_t(CAP / 2) << bits) < len) ++bits;
+    const int top = (hi - bits + 1) > lo ? (hi - bits + 1) : lo;
+    // digit = (r >> top) & 255: bits above hi are constant, so only 2^(hi-top+1) buckets occur
     pass_global(gk, gv, ak, av, len, top, true);  // keys now in ak in top-digit order
     if (top == lo) {  // that pass covered every varying bit
       copy(gk, gv, ak, av, len);

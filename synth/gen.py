@@ -121,13 +121,42 @@ def normal_f32_special(n: int, seed: int = 3, frac: float = 0.001) -> np.ndarray
 F64_DISTS = ("uniform", "normal", "lognormal", "zipf", "presorted", "reversed")
 
 
-def _zipf_ranks(count: int, s: float, nranks: int, seed: int) -> np.ndarray:
-    """Zipf(s) ranks in [1, nranks] by inverse transform of a uniform draw."""
+def _zipf_cdf(s: float, nranks: int):
     w = np.arange(1, nranks + 1, dtype=np.float64) ** (-s)
     cdf = np.cumsum(w)
-    cdf /= cdf[-1]
-    u = u01_f64(seed, count)
-    return np.minimum(np.searchsorted(cdf, u, side="right"), nranks - 1) + 1
+    total = cdf[-1]
+    cdf /= total
+    return cdf, total
+
+
+def _zipf_invert(u: np.ndarray, cdf: np.ndarray, total: float, s: float) -> np.ndarray:
+    """Exact inverse transform: for each u the index r = #{cdf <= u} (capped at
+    nranks-1), i.e. numpy.searchsorted(cdf, u, 'right').  A continuous
+    approximation of the harmonic sum (H(k) ~ zeta(s) - k^(1-s)/(s-1)) gives a
+    starting index that a few exact neighbour comparisons correct."""
+    nranks = cdf.size
+    zeta = total + nranks ** (1.0 - s) / (s - 1.0)  # H(K) plus the tail integral
+    tail = np.maximum(zeta - u * total, 1e-300) * (s - 1.0)
+    r = np.clip(np.floor(tail ** (1.0 / (1.0 - s))).astype(np.int64) - 1, 0, nranks - 1)
+    for _ in range(1 << 12):
+        up = (r < nranks - 1) & (cdf[r] <= u)
+        down = (r > 0) & (cdf[np.maximum(r - 1, 0)] > u)
+        if not (up.any() or down.any()):
+            break
+        r += up.astype(np.int64) - down.astype(np.int64)
+    else:  # never expected; keep the definition exact regardless
+        r = np.minimum(np.searchsorted(cdf, u, side="right"), nranks - 1)
+    return r
+
+
+def _zipf_ranks(count: int, s: float, nranks: int, seed: int) -> np.ndarray:
+    """Zipf(s) ranks in [1, nranks] by inverse transform of a uniform draw."""
+    cdf, total = _zipf_cdf(s, nranks)
+    out = np.empty(count, dtype=np.int64)
+    for lo in range(0, count, _CHUNK):
+        hi = min(count, lo + _CHUNK)
+        out[lo:hi] = _zipf_invert(u01_f64(seed, hi - lo, lo), cdf, total, s) + 1
+    return out
 
 
 def dist_f64(n: int, dist: str, seed: int) -> np.ndarray:
@@ -176,15 +205,13 @@ def zipf_mix_u32(n: int, seed: int = 30, s: float = 1.1, nranks: int = 1 << 24) 
     """Per key a fair coin picks Zipf(s) over ``nranks`` ranks (rank k maps to
     fmix32(k-1)) or a uniform u32."""
     out = np.empty(n, dtype=np.uint32)
-    w = np.arange(1, nranks + 1, dtype=np.float64) ** (-s)
-    cdf = np.cumsum(w)
-    cdf /= cdf[-1]
+    cdf, total = _zipf_cdf(s, nranks)
     for lo in range(0, n, _CHUNK):
         hi = min(n, lo + _CHUNK)
         z = splitmix64(seed, hi - lo, lo)
         coin = (z >> np.uint64(63)).astype(bool)
         u = (z & np.uint64((1 << 53) - 1)).astype(np.float64) * (2.0 ** -53)
-        ranks = np.minimum(np.searchsorted(cdf, u, side="right"), nranks - 1)
+        ranks = _zipf_invert(u, cdf, total, s)
         zipf_keys = fmix32(ranks.astype(np.uint32))
         uni = ((z >> np.uint64(16)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
         out[lo:hi] = np.where(coin, zipf_keys, uni)
