@@ -5,7 +5,7 @@ Workload (one "step"): 268,435,456 int64 keys uniform over all 2^64 bit patterns
 and 268,435,456 float32 keys ~ N(0,1) with 0.1% NaN (random sign and payload)
 and 0.1% -0.0; each array goes through a stable ak_sortperm (UInt32 indices) and
 an in-place ak_sort, ascending -- the rank-local sort of the paper's sample sort
-(Sec. III-A) on its int64/float32 dtypes.  value = key bytes sorted per step (4
+(Sec. IV-A) on its int64/float32 dtypes.  value = key bytes sorted per step (4
 calls) / device time, in GB/s (1e9 B/s), summed over ranks.
 
 Timing: 3+ warm-up steps; each call is bracketed by CUDA events on its stream;

@@ -3,7 +3,7 @@
  *
  * The library sorts large arrays of primitive numeric keys on one GPU: the
  * rank-local sorting step that every accelerator runs inside the sample sort of
- * the paper's distributed benchmark (Sec. III-A, "MPISort Algorithm"), with the
+ * the paper's distributed benchmark (Sec. IV-A, "MPISort Algorithm"), with the
  * operations of the paper's sorting building blocks (Sec. II-B: merge_sort,
  * merge_sort_by_key, sortperm) and Julia Base ordering (Sec. II).
  *
@@ -42,7 +42,7 @@ extern "C" {
 
 typedef struct CUstream_st *ak_stream_t; /* same handle as cudaStream_t */
 
-/* Key element types: the paper's FFI list (Sec. III: int16, int32, int64,
+/* Key element types: the paper's FFI list (Sec. IV: int16, int32, int64,
  * float, double) with unsigned variants; __int128 is not supported. */
 typedef enum ak_dtype {
     AK_U16 = 0, AK_I16 = 1, AK_U32 = 2, AK_I32 = 3,
@@ -129,7 +129,7 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
 
 /*
  * In-place stable sort of d_keys[0..n) (Sec. II-B "merge_sort"; the local sort of
- * Sec. III-A).  n = 0 is a no-op.
+ * Sec. IV-A).  n = 0 is a no-op.
  */
 ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order,
                   void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt);
@@ -200,7 +200,7 @@ const char *ak_status_string(ak_status s);
 
 /* ------------------------------------------------------------------------- */
 /* Learned-CDF model kernels, exposed for checking against a CPU restatement. */
-/* The sample-sort splitter step (Sec. III-A) draws the sample these act on.  */
+/* The sample-sort splitter step (Sec. IV-A) draws the sample these act on.  */
 
 #define AK_LEARNED_KNOTS 64
 #define AK_LEARNED_PARAMS 321
@@ -209,7 +209,7 @@ const char *ak_status_string(ak_status s);
  * Knots of the piecewise-linear CDF: d_knots[j] = d_xs[round(j (m-1) / 63)],
  * j < 64, for an ascending float32 sample d_xs[0..m) of x-hat values in [0, 1]:
  * the sample order statistics that the sample sort's splitter step picks
- * (Sec. III-A), through which PL interpolates (xi_j, j/63).  m >= 1.
+ * (Sec. IV-A), through which PL interpolates (xi_j, j/63).  m >= 1.
  */
 ak_status ak_learned_knots(const float *d_xs, int64_t m, float *d_knots, ak_stream_t stream);
 
@@ -231,20 +231,26 @@ ak_status ak_learned_loss_grad(const float *d_x, const float *d_y, int64_t m, co
 size_t ak_learned_grad_temp_bytes(int64_t m);
 
 /* ------------------------------------------------------------------------- */
-/* Autotuner: times the onesweep tile variants and learned/radix paths on the
- * caller's buffers (their contents are overwritten) and caches the fastest
- * per (op, dtype, log2 n, order, value bytes).  AK_PATH_AUTO consults the cache. */
+/* Autotuner: times the onesweep tile configurations and the learned and block
+ * paths on the caller's buffers and caches the fastest per (op, dtype,
+ * ceil(log2 n), value bytes).  AK_PATH_AUTO calls with tile_config 0 (and
+ * ak_sort_temp_bytes for them) take the cached choice; the environment variable
+ * AK_TUNE_CACHE names a cache file loaded on first use. */
 
 /*
- * Tunes one call shape.  d_keys/d_vals/d_perm are scratch of the call's sizes
- * (d_vals only for pairs, d_perm only for sortperm); d_temp must hold the
- * largest variant (ak_sort_temp_bytes with path AK_PATH_LEARNED).  Synchronises
- * `stream`.  best (optional) receives the chosen options.
+ * Tunes one call shape (op = AK_OP_SORT, AK_OP_SORTPERM or AK_OP_SORT_PAIRS).
+ * d_keys (and d_vals for pairs, d_perm for sortperm) are the call's buffers: they
+ * are restored from a copy before every timed call and hold the original inputs
+ * again on return.  d_temp must hold the largest candidate's workspace
+ * (ak_sort_temp_bytes with path AK_PATH_LEARNED or AK_PATH_RADIX, whichever is
+ * larger, rounded up to 256 bytes) plus n * (key bytes + value bytes) for the
+ * copy.  Synchronises `stream`.  `best` (optional) receives the chosen options.
  */
 ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order order,
                       void *d_keys, void *d_vals, uint32_t *d_perm, void *d_temp,
                       size_t temp_bytes, ak_stream_t stream, ak_options *best);
-/* JSON persistence of the tuning cache (one object per line). */
+/* The cache as JSON lines {"op", "dtype", "log2n", "val_bytes", "path",
+ * "tile_config", "ms"}: save, load (merging; malformed lines are skipped), clear. */
 ak_status ak_autotune_save(const char *path);
 ak_status ak_autotune_load(const char *path);
 void ak_autotune_clear(void);

@@ -6,7 +6,7 @@ never calls it.
 
 ``ak_oracle.c`` is a plain top-down stable merge sort under Julia ``isless`` (the
 sort, sortperm and by-key sort of Sec. II-B, used as the rank-local sort of the
-sample sort in Sec. III-A).  ``learned.py`` restates the learned-CDF model in
+sample sort in Sec. IV-A).  ``learned.py`` restates the learned-CDF model in
 float64 numpy.  This module compiles the C file with gcc on first use and wraps
 it with ctypes over numpy arrays.
 """

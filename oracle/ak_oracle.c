@@ -11,7 +11,7 @@
  *   nor lt(k[p[j]], k[p[i]]) holds and p[i] < p[j].
  *   lt is Julia's isless for ascending order and lt(a,b) = isless(b,a) for
  *   descending order (Julia's rev=true, which keeps equal keys in input order).
- *   sort        -> k o p            (the local sort of Sec. III-A)
+ *   sort        -> k o p            (the local sort of Sec. IV-A)
  *   sortperm    -> p                (Sec. II-B, "sortperm")
  *   sort_pairs  -> (k o p, v o p)   (Sec. II-B, "merge_sort_by_key")
  *   segmented   -> the same definition applied to every CSR segment alone.

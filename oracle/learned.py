@@ -1,6 +1,6 @@
 """Float64 restatement of the learned-CDF bucketing model -- TEST INFRASTRUCTURE ONLY.
 
-The paper's distributed sort (Sec. III-A, SIHSort) draws a key sample, builds
+The paper's distributed sort (Sec. IV-A, SIHSort) draws a key sample, builds
 "interpolated histograms" of it and turns them into splitters.  The learned path
 replaces the splitters by a tiny model of the key CDF trained on that sample:
 

@@ -1,6 +1,6 @@
 """GB300-native single-device sort (sm_103a) behind a C ABI.
 
-The rank-local sort of the paper's distributed sample sort (Sec. III-A), with
+The rank-local sort of the paper's distributed sample sort (Sec. IV-A), with
 the sort / sortperm / by-key operations of its building blocks (Sec. II-B), in
 Julia isless order.  Python here only marshals arguments: the compiled library
 ``lib/libak_sort.so`` (built by ``_build.build()``) does all the work.
@@ -10,7 +10,7 @@ from ._lib import (  # noqa: F401
     AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED, AK_OP_SORTPERM, AK_PATH_AUTO, AK_PATH_BLOCK,
     AK_PATH_LEARNED, AK_PATH_RADIX, AK_TILE_CONFIGS, AK_U16, AK_U32, AK_U64, EXPORTED, LIB_PATH,
     AK_DEBUG_SKIP_FIRST_TILE, AK_MAX_PASSES,
-    AkError, Info, Options, ak_autotune, ak_autotune_clear, ak_autotune_load, ak_autotune_save,
+    AkError, Info, Options, ak_autotune, autotune_temp_bytes, ak_autotune_clear, ak_autotune_load, ak_autotune_save,
     ak_last_info, ak_learned_knots, ak_learned_loss_grad, ak_sort, ak_sort_pairs,
     ak_sort_segmented, ak_sort_static_scratch, ak_sort_temp_bytes, ak_sortperm, ak_status_check, ak_status_string,
     ak_version, dtype_code, load, order_code, temp_bytes, workspace,

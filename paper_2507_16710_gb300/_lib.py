@@ -297,14 +297,22 @@ def ak_learned_loss_grad(x: torch.Tensor, y: torch.Tensor, c: torch.Tensor, para
     return loss, grad
 
 
+def autotune_temp_bytes(op: int, n: int, kd: int, val_bytes: int = 0) -> int:
+    """Workspace ak_autotune needs: the largest candidate plus a copy of the inputs."""
+    need = max(temp_bytes(op, n, kd, val_bytes, 0, {"path": p}) for p in (AK_PATH_RADIX, AK_PATH_LEARNED))
+    need = (need + 255) // 256 * 256
+    kb = {AK_U16: 2, AK_I16: 2, AK_U32: 4, AK_I32: 4, AK_F32: 4}.get(kd, 8)
+    return need + n * (kb + (val_bytes if op == AK_OP_SORT_PAIRS else 0))
+
+
 def ak_autotune(op: int, keys: torch.Tensor, order="ascending", vals=None, perm=None, temp=None,
                 stream=None, unsigned: bool = False) -> Options:
+    """Time the candidates for this call shape and cache the fastest; returns it."""
     kd = dtype_code(keys, unsigned)
     n = keys.numel()
     vb = vals.element_size() if vals is not None else 0
-    need = temp_bytes(op, n, kd, vb, 0, {"path": AK_PATH_LEARNED})
     if temp is None:
-        temp = workspace(need, keys.device)
+        temp = workspace(autotune_temp_bytes(op, n, kd, vb), keys.device)
     best = Options()
     _check(load().ak_autotune(op, n, kd, vb, order_code(order), keys.data_ptr(),
                               vals.data_ptr() if vals is not None else None,

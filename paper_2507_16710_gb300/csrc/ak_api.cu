@@ -97,6 +97,16 @@ static ak_options resolve_options(const ak_options *opt) {
   return o;
 }
 
+// AK_PATH_AUTO with no explicit tile configuration takes the autotuned choice.
+static void apply_tuning(int op, int kd, int64_t n, int val_bytes, ak_options &o) {
+  if (o.path != AK_PATH_AUTO || o.tile_config != 0) return;
+  int path = 0, tc = 0;
+  if (tune_lookup(op, kd, n, op == AK_OP_SORT_PAIRS ? val_bytes : 0, &path, &tc)) {
+    o.path = path;
+    o.tile_config = tc;
+  }
+}
+
 static cudaError_t radix_dispatch(int key_bytes, const RadixCall &c) {
   switch (key_bytes) {
     case 2: return c.kind == KIND_SINT ? radix_launch_u16_sint(c) : radix_launch_u16_uint(c);
@@ -460,7 +470,8 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
   if (op == AK_OP_SORT_PAIRS && val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8)
     return AK_ERR_INVALID_ARG;
   if (op == AK_OP_SORT_SEGMENTED && nseg < 0) return AK_ERR_INVALID_ARG;
-  const ak_options o = resolve_options(opt);
+  ak_options o = resolve_options(opt);
+  if (op != AK_OP_SORT_SEGMENTED) apply_tuning(op, kd, n, val_bytes, o);
   *bytes = temp_for(op, n, ki.bytes, val_bytes, nseg, o);
   return AK_OK;
 }
@@ -472,7 +483,8 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_
   if (n == 0) return AK_OK;
   if (!d_keys || !aligned(d_keys, ki.bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  const ak_options o = resolve_options(opt);
+  ak_options o = resolve_options(opt);
+  apply_tuning(AK_OP_SORT, kd, n, 0, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORT, n, ki.bytes, 0, o);
   if (path == AK_PATH_BLOCK)
@@ -490,7 +502,8 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
   if (n > int64_t(0xFFFFFFFFll)) return AK_ERR_INDEX_OVERFLOW;
   if (!d_keys || !d_perm || !aligned(d_keys, ki.bytes) || !aligned(d_perm, 4)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  const ak_options o = resolve_options(opt);
+  ak_options o = resolve_options(opt);
+  apply_tuning(AK_OP_SORTPERM, kd, n, 4, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORTPERM, n, ki.bytes, 4, o);
   if (path == AK_PATH_BLOCK)
@@ -508,7 +521,8 @@ ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak
   if (n == 0) return AK_OK;
   if (!d_keys || !d_vals || !aligned(d_keys, ki.bytes) || !aligned(d_vals, val_bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  const ak_options o = resolve_options(opt);
+  ak_options o = resolve_options(opt);
+  apply_tuning(AK_OP_SORT_PAIRS, kd, n, val_bytes, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORT_PAIRS, n, ki.bytes, val_bytes, o);
   if (path == AK_PATH_BLOCK)

@@ -1,0 +1,204 @@
+// autotune.cu -- timed choice of path and tile configuration per call shape.
+//
+// ak_autotune runs every candidate (radix with each tile configuration, the
+// learned path, and the one-launch block path when n fits it) on the caller's
+// buffers, restoring the inputs from a copy in the workspace before each timed
+// call, times it with CUDA events on the caller's stream and records the
+// fastest under (op, dtype, ceil(log2 n), value bytes).  AK_PATH_AUTO
+// calls consult this cache (ak_sort_temp_bytes too, so sizes agree).  The cache
+// is kept in host memory behind a mutex and persists as JSON lines.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace ak {
+namespace {
+
+struct TuneEntry {
+  int path, tile_config;
+  float ms;
+};
+using TuneKey = std::tuple<int, int, int, int>;  // op, dtype, log2 n, value bytes
+
+std::mutex g_mu;
+std::map<TuneKey, TuneEntry> g_cache;
+bool g_env_loaded = false;
+
+int log2_class(int64_t n) {
+  int b = 0;
+  while ((int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+ak_status load_file(const char *path) {
+  FILE *f = fopen(path, "r");
+  if (!f) return AK_ERR_INVALID_ARG;
+  char line[512];
+  while (fgets(line, sizeof line, f)) {
+    int op, dt, lg, vb, pth, tc;
+    float ms;
+    if (sscanf(line,
+               " {\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
+               "\"tile_config\": %d, \"ms\": %f}",
+               &op, &dt, &lg, &vb, &pth, &tc, &ms) == 7 &&
+        pth >= AK_PATH_RADIX && pth <= AK_PATH_BLOCK && tc >= 0 && tc <= AK_TILE_CONFIGS)
+      g_cache[TuneKey(op, dt, lg, vb)] = TuneEntry{pth, tc, ms};
+  }
+  fclose(f);
+  return AK_OK;
+}
+
+void load_env_once() {  // caller holds g_mu
+  if (g_env_loaded) return;
+  g_env_loaded = true;
+  const char *p = getenv("AK_TUNE_CACHE");
+  if (p && *p) load_file(p);
+}
+
+}  // namespace
+
+bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  load_env_once();
+  auto it = g_cache.find(TuneKey(op, dtype, log2_class(n), val_bytes));
+  if (it == g_cache.end()) return false;
+  *path = it->second.path;
+  *tile_config = it->second.tile_config;
+  return true;
+}
+
+}  // namespace ak
+
+using namespace ak;
+
+extern "C" {
+
+ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order order, void *d_keys, void *d_vals,
+                      uint32_t *d_perm, void *d_temp, size_t temp_bytes, ak_stream_t stream, ak_options *best) {
+  if (op != AK_OP_SORT && op != AK_OP_SORTPERM && op != AK_OP_SORT_PAIRS) return AK_ERR_INVALID_ARG;
+  if (n <= 0 || !d_keys || !d_temp || (op == AK_OP_SORT_PAIRS && !d_vals) || (op == AK_OP_SORTPERM && !d_perm))
+    return AK_ERR_INVALID_ARG;
+  const int kb = (kd <= AK_I16) ? 2 : (kd <= AK_I32 || kd == AK_F32) ? 4 : 8;
+  const int vb = (op == AK_OP_SORT_PAIRS) ? val_bytes : 0;
+  if (op == AK_OP_SORT_PAIRS && vb != 1 && vb != 2 && vb != 4 && vb != 8) return AK_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // candidates
+  std::vector<ak_options> cands;
+  for (int tc = 1; tc <= AK_TILE_CONFIGS; ++tc) {
+    ak_options o{};
+    o.path = AK_PATH_RADIX;
+    o.tile_config = tc;
+    cands.push_back(o);
+  }
+  if (n >= (int64_t(1) << 16) && n < (int64_t(1) << 32)) {
+    ak_options o{};
+    o.path = AK_PATH_LEARNED;
+    cands.push_back(o);
+  }
+  if (n <= seg_cap(kb, op == AK_OP_SORTPERM ? 4 : vb)) {
+    ak_options o{};
+    o.path = AK_PATH_BLOCK;
+    cands.push_back(o);
+  }
+  // the workspace holds the largest candidate's temporaries, then a copy of the inputs
+  size_t need = 0;
+  for (const ak_options &o : cands) {
+    size_t b = 0;
+    if (ak_sort_temp_bytes(op, n, kd, val_bytes, 0, &o, &b) == AK_OK && b > need) need = b;
+  }
+  need = (need + 255) & ~size_t(255);
+  const size_t kbytes = size_t(n) * kb, vbytes = size_t(n) * vb;
+  if (temp_bytes < need + kbytes + vbytes) return AK_ERR_WORKSPACE_TOO_SMALL;
+  uint8_t *copy_k = static_cast<uint8_t *>(d_temp) + need;
+  uint8_t *copy_v = copy_k + kbytes;
+  if (cudaMemcpyAsync(copy_k, d_keys, kbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return AK_ERR_CUDA;
+  if (vbytes && cudaMemcpyAsync(copy_v, d_vals, vbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return AK_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return AK_ERR_CUDA;
+  }
+  ak_status result = AK_OK;
+  float best_ms = INFINITY;
+  ak_options best_o{};
+  for (const ak_options &o : cands) {
+    float tot = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {  // one warm-up, three timed
+      cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st);
+      if (vbytes) cudaMemcpyAsync(d_vals, copy_v, vbytes, cudaMemcpyDeviceToDevice, st);
+      cudaEventRecord(e0, st);
+      ak_status s = AK_OK;
+      if (op == AK_OP_SORT) s = ak_sort(d_keys, n, kd, order, d_temp, need, stream, &o);
+      else if (op == AK_OP_SORTPERM) s = ak_sortperm(d_keys, d_perm, n, kd, order, d_temp, need, stream, &o);
+      else s = ak_sort_pairs(d_keys, d_vals, val_bytes, n, kd, order, d_temp, need, stream, &o);
+      cudaEventRecord(e1, st);
+      if (s != AK_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      if (ak_status_check(d_temp, stream) != AK_OK) ok = false;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;
+    }
+    if (ok && tot / 3.f < best_ms) {
+      best_ms = tot / 3.f;
+      best_o = o;
+    }
+  }
+  // leave the inputs as they were
+  cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st);
+  if (vbytes) cudaMemcpyAsync(d_vals, copy_v, vbytes, cudaMemcpyDeviceToDevice, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) result = AK_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!isfinite(best_ms)) return result == AK_OK ? AK_ERR_CUDA : result;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_cache[TuneKey(op, int(kd), log2_class(n), vb)] = TuneEntry{best_o.path, best_o.tile_config, best_ms};
+  }
+  if (best) *best = best_o;
+  return result;
+}
+
+ak_status ak_autotune_save(const char *path) {
+  if (!path) return AK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  FILE *f = fopen(path, "w");
+  if (!f) return AK_ERR_INVALID_ARG;
+  for (const auto &kv : g_cache) {
+    int op, dt, lg, vb;
+    std::tie(op, dt, lg, vb) = kv.first;
+    fprintf(f,
+            "{\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
+            "\"tile_config\": %d, \"ms\": %.6f}\n",
+            op, dt, lg, vb, kv.second.path, kv.second.tile_config, kv.second.ms);
+  }
+  fclose(f);
+  return AK_OK;
+}
+
+ak_status ak_autotune_load(const char *path) {
+  if (!path) return AK_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  return load_file(path);
+}
+
+void ak_autotune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_cache.clear();
+  g_env_loaded = true;  // an explicit clear also drops the environment's cache
+}
+
+}  // extern "C"

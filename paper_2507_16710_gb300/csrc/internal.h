@@ -131,4 +131,7 @@ cudaError_t seg_launch_u64_float(const SegCall &c);
 
 int device_sm_count();
 
+// Autotune cache: the tuned path and tile configuration of a call shape.
+bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config);
+
 }  // namespace ak

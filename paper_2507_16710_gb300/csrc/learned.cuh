@@ -1,6 +1,6 @@
 // learned.cuh -- learned-CDF bucketing: the model and its kernels.
 //
-// The splitter step of the paper's sample sort (Sec. III-A) draws a key sample
+// The splitter step of the paper's sample sort (Sec. IV-A) draws a key sample
 // and turns interpolated histograms of it into splitters.  Here the sample trains
 // a small monotone model of the key CDF, F = PL + r:
 //   x-hat = min-max normalised radix key (the order-preserving integer image of

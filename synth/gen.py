@@ -6,8 +6,8 @@ stream ``seed`` is ``mix64(seed * PHI + (i + 1) * GOLDEN)``.  Because a draw dep
 only on (seed, i), any slice of a workload can be regenerated alone, and the
 values are identical on every machine and numpy version.
 
-Workloads (the single-device step of the distributed sample sort of Sec. III-A,
-with the dtypes of Sec. III and the sizes of Sec. III-C):
+Workloads (the single-device step of the distributed sample sort of Sec. IV-A,
+with the dtypes of Sec. IV and the sizes of Sec. IV-C):
 
 * ``uniform_u32``         1,048,576 u32 uniform on [0, 2^32)
 * ``uniform_i64``         all 2^64 bit patterns, viewed as int64

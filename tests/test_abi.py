@@ -58,3 +58,31 @@ def test_host_side_argument_checks(lib):
     assert lib.ak_sortperm(ctypes.c_void_p(4096), ctypes.c_void_p(8192), 1 << 32, ak.AK_U32, 0, None, 0,
                            None, None) == 6
     assert lib.ak_status_string(5) == b"device-side wait timed out"
+
+
+def test_autotune_cache_roundtrip_and_auto_sizing(lib, tmp_path):
+    """The tuning cache persists as JSON lines, skips malformed lines, and an
+    AK_PATH_AUTO workspace query follows a cached choice (no GPU needed)."""
+    import json
+
+    import paper_2507_16710_gb300 as ak
+    lib.ak_autotune_clear()
+    n = 1 << 22
+    base = ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64)
+    learned = ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64, options={"path": ak.AK_PATH_LEARNED})
+    assert learned != base
+    src = tmp_path / "in.jsonl"
+    src.write_text(
+        json.dumps({"op": 0, "dtype": ak.AK_F64, "log2n": 22, "val_bytes": 0, "path": ak.AK_PATH_LEARNED,
+                    "tile_config": 0, "ms": 1.5}) + "\n" + "not json\n" +
+        json.dumps({"op": 1, "dtype": ak.AK_U32, "log2n": 20, "val_bytes": 0, "path": 9,
+                    "tile_config": 0, "ms": 1.0}) + "\n")
+    ak.ak_autotune_load(str(src))
+    assert ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64) == learned     # AUTO follows the cache
+    assert ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64, options={"path": ak.AK_PATH_RADIX}) == base
+    out = tmp_path / "out.jsonl"
+    ak.ak_autotune_save(str(out))
+    rows = [json.loads(x) for x in out.read_text().splitlines()]
+    assert len(rows) == 1 and rows[0]["path"] == ak.AK_PATH_LEARNED and rows[0]["log2n"] == 22
+    lib.ak_autotune_clear()
+    assert ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64) == base
