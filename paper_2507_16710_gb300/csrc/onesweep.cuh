@@ -24,6 +24,11 @@
 #include "common.cuh"
 #include "learned.cuh"
 
+// Warp matcher used by the digit passes (see warp_peers below).
+#ifndef AK_WARP_MATCH
+#define AK_WARP_MATCH 2
+#endif
+
 namespace ak {
 
 constexpr uint32_t INACTIVE = 0xFFFFFFFFu;
@@ -168,8 +173,12 @@ struct PassSmem {
   static constexpr size_t STAGE = (KEYS + VALS + 127) / 128 * 128;
   static constexpr size_t OFF_OUT = STAGE * STAGES;  // the tile in digit order
   static constexpr size_t OFF_HIST = OFF_OUT + STAGE;
-  static constexpr size_t OFF_MASK = (OFF_HIST + size_t(NW) * HROW * 2 + 15) / 16 * 16;    // u32[NW][HROW]
-  static constexpr size_t OFF_KPTR = OFF_MASK + size_t(NW) * HROW * 4;                      // u64[RADIX]
+  // OFF_HIST: u16 counters, digit-major: row d holds the NW warps' counters of
+  // digit d in NW/2 words plus one pad word, so rows start in distinct banks
+  static constexpr int HSTRIDE = NW / 2 + 1;  // 32-bit words per digit row (odd)
+  static constexpr size_t OFF_MASK = (OFF_HIST + size_t(HROW) * HSTRIDE * 4 + 15) / 16 * 16;  // u32[NW][HROW]
+  static constexpr size_t MASK_BYTES = AK_WARP_MATCH == 3 ? 8 : 4;                          // per digit and warp
+  static constexpr size_t OFF_KPTR = OFF_MASK + size_t(NW) * HROW * MASK_BYTES;             // u64[RADIX]
   static constexpr size_t OFF_VPTR = OFF_KPTR + RADIX * 8;                                  // u64[RADIX]
   static constexpr size_t OFF_SCR = OFF_VPTR + (HAS_V ? RADIX * 8 : 0);                     // u32[NW+1]
   static constexpr size_t OFF_BAR = (OFF_SCR + (NW + 1) * 4 + 15) / 16 * 16;             // u64[STAGES]
@@ -178,6 +187,7 @@ struct PassSmem {
   static constexpr size_t OFF_DIG = OFF_FLAG + 16;  // u8[TILE]: digits in tile order (learned digits)
   static constexpr size_t BYTES = OFF_DIG + (DIGIT == DIGIT_LEARNED ? size_t(TILE) : 0);
   static_assert(TILE < 65536, "warp bases are u16");
+  static_assert(NW % 2 == 0, "two 16-bit counters per word");
   static_assert(KEYS % 16 == 0 && STAGE % 128 == 0 && OFF_MASK % 16 == 0 && OFF_KPTR % 8 == 0 &&
                     OFF_BAR % 8 == 0,
                 "shared-memory arrays aligned to their element size (bulk copies: 16 bytes)");
@@ -187,12 +197,11 @@ constexpr int LOOKBACK_WINDOW = 8;  // predecessor words probed per round trip
 
 // Lanes of the warp holding the same digit.  AK_WARP_MATCH selects match.any
 // (0), a bit-sliced match from ballots (1: the peers of a lane are the lanes
-// agreeing on every bit; 9 bits when the padding digit RADIX can occur), or a
+// agreeing on every bit; 9 bits when the padding digit RADIX can occur), a
 // shared-memory mask per digit that every lane ORs its bit into (2, default:
-// fixed cost, no per-bit work).
-#ifndef AK_WARP_MATCH
-#define AK_WARP_MATCH 2
-#endif
+// fixed cost), or the same with two items per step in 64-bit masks (3: half the
+// dependent round trips but twice the mask memory; measured slower on GB300).
+// (AK_WARP_MATCH is defined at the top of this file.)
 __device__ __forceinline__ uint32_t warp_peers(uint32_t d, bool nine_bits) {
 #if AK_WARP_MATCH == 0
   (void)nine_bits;
@@ -224,6 +233,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
   extern __shared__ __align__(128) uint8_t smem[];
   uint16_t *whist = reinterpret_cast<uint16_t *>(smem + L::OFF_HIST);
   uint32_t *wmask = reinterpret_cast<uint32_t *>(smem + L::OFF_MASK);
+  unsigned long long *wmask2 = reinterpret_cast<unsigned long long *>(smem + L::OFF_MASK);
   // per digit: address of the destination of tile position 0 (base + delta,
   // kept as an integer; base + delta + i is inside the buffer for every key)
   unsigned long long *s_kptr = reinterpret_cast<unsigned long long *>(smem + L::OFF_KPTR);
@@ -287,7 +297,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
     }
   };
 
-  for (int i = tid; i < NW * HROW; i += BLOCK) wmask[i] = 0u;
+  for (int i = tid; i < NW * HROW * int(L::MASK_BYTES / 4); i += BLOCK) wmask[i] = 0u;
+  for (int i = tid; i < HROW * L::HSTRIDE; i += BLOCK) reinterpret_cast<uint32_t *>(whist)[i] = 0u;
   uint32_t phase_bits = 0;  // thread 0: parity to wait for, per stage
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
@@ -321,8 +332,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
   const int shift = a.pass * RADIX_BITS;
   const uint32_t lt_mask = lanemask_lt();
   const uint32_t gt_mask = ~(lt_mask | (1u << lane));
-  uint16_t *wh = whist + warp * HROW;
   uint32_t *wm = wmask + warp * HROW;
+  unsigned long long *wm2 = wmask2 + warp * HROW;
   S *st = reinterpret_cast<S *>(a.status_cur);
 
   for (int it = 0;; ++it) {
@@ -341,8 +352,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
     }
 
     // ---- warp multisplit ranking (item i of lane l sits at wbase + 32 i + l)
-    for (int i = lane; i < HROW / 2; i += 32) reinterpret_cast<uint32_t *>(wh)[i] = 0u;
-    __syncwarp();
     const int wbase = warp * 32 * ITEMS;
     uint32_t dr[ITEMS];  // rank << 9 | digit (digit RADIX marks a padding slot)
 #pragma unroll
@@ -350,52 +359,105 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
       const int idx = wbase + i * 32 + lane;
       dr[i] = (idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
     }
+#if AK_WARP_MATCH == 3
+    // two items per step: lane l sets bit l (item A) and bit 32 + l (item B) of
+    // the 64-bit mask of its digit; one read gives both peer sets and how many
+    // lanes of item A (all earlier than item B) share item B's digit.  Each
+    // digit's counter is advanced by exactly one leader: A's group leader, or
+    // B's when no lane of A has that digit.
+#pragma unroll
+    for (int i = 0; i + 1 < ITEMS; i += 2) {
+      const uint32_t dA = dr[i], dB = dr[i + 1];
+      uint16_t *cA = whist + dA * (2 * L::HSTRIDE) + warp;
+      uint16_t *cB = whist + dB * (2 * L::HSTRIDE) + warp;
+      atomicOr(&wm2[dA], 1ull << lane);
+      atomicOr(&wm2[dB], 1ull << (32 + lane));
+      __syncwarp();
+      const unsigned long long MA = wm2[dA], MB = wm2[dB];
+      const uint32_t nA = *cA, nB = *cB;
+      __syncwarp();
+      const uint32_t peersA = uint32_t(MA), peersB = uint32_t(MB >> 32), aInB = uint32_t(MB);
+      if ((peersA & gt_mask) == 0) {
+        *cA = uint16_t(nA + __popcll(MA));
+        wm2[dA] = 0ull;
+      }
+      if (aInB == 0u && (peersB & gt_mask) == 0) {
+        *cB = uint16_t(nB + __popc(peersB));
+        wm2[dB] = 0ull;
+      }
+      __syncwarp();
+      dr[i] = ((nA + __popc(peersA & lt_mask)) << 9) | dA;
+      dr[i + 1] = ((nB + __popc(aInB) + __popc(peersB & lt_mask)) << 9) | dB;
+    }
+    if (ITEMS & 1) {  // odd item count: the last item alone
+      const uint32_t d = dr[ITEMS - 1];
+      uint16_t *wc = whist + d * (2 * L::HSTRIDE) + warp;
+      atomicOr(&wm2[d], 1ull << lane);
+      __syncwarp();
+      const uint32_t peers = uint32_t(wm2[d]);
+      const uint32_t cnt = *wc;
+      __syncwarp();
+      if ((peers & gt_mask) == 0) {
+        *wc = uint16_t(cnt + __popc(peers));
+        wm2[d] = 0ull;
+      }
+      __syncwarp();
+      dr[ITEMS - 1] = ((cnt + __popc(peers & lt_mask)) << 9) | d;
+    }
+#else
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       const uint32_t d = dr[i];
 #if AK_WARP_MATCH == 2
+      uint16_t *wc = whist + d * (2 * L::HSTRIDE) + warp;  // this warp's running count of digit d
       atomicOr(&wm[d], 1u << lane);
       __syncwarp();
       const uint32_t peers = wm[d];
-      const uint32_t cnt = wh[d];  // running count of this digit in the warp
+      const uint32_t cnt = *wc;
       __syncwarp();
       if ((peers & gt_mask) == 0) {  // highest lane of the group updates and resets
-        wh[d] = uint16_t(cnt + __popc(peers));
+        *wc = uint16_t(cnt + __popc(peers));
         wm[d] = 0u;
       }
       __syncwarp();
 #else
+      uint16_t *wc = whist + d * (2 * L::HSTRIDE) + warp;
       const uint32_t peers = warp_peers(d, tile_n != TILE);
       const bool leader = (peers & gt_mask) == 0;  // highest lane of the group
       uint32_t cnt = 0;
-      if (leader) cnt = wh[d];
-      if (leader) wh[d] = uint16_t(cnt + __popc(peers));
+      if (leader) cnt = *wc;
+      if (leader) *wc = uint16_t(cnt + __popc(peers));
       cnt = __shfl_sync(0xffffffffu, cnt, 31 - __clz(peers));
       __syncwarp();
 #endif
       dr[i] = ((cnt + __popc(peers & lt_mask)) << 9) | d;
     }
+#endif
     __syncthreads();  // A: every warp row complete
 
     // ---- per-digit tile counts, publish, warp bases = tile digit start + earlier warps
     uint32_t my_cnt = 0;
+    uint32_t *hrow = reinterpret_cast<uint32_t *>(whist) + tid * L::HSTRIDE;
     if (tid < RADIX) {
-      uint32_t run = 0;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const uint32_t c = whist[w * HROW + tid];
-        whist[w * HROW + tid] = uint16_t(run);
-        run += c;
+      for (int v = 0; v < NW / 2; ++v) {
+        const uint32_t q = hrow[v];
+        my_cnt += (q & 0xFFFFu) + (q >> 16);
       }
-      my_cnt = run;
       const S word = (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt);
       st_relaxed(&st[tile * RADIX + tid], word);
     }
     uint32_t total;
     const uint32_t start = block_exclusive_scan<BLOCK>(tid < RADIX ? my_cnt : 0u, s_scr, &total);
-    if (tid < RADIX) {
+    if (tid < RADIX) {  // each warp's base = tile digit start + counts of earlier warps
+      uint32_t run = start;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) whist[w * HROW + tid] = uint16_t(whist[w * HROW + tid] + start);
+      for (int v = 0; v < NW / 2; ++v) {
+        const uint32_t q = hrow[v];
+        const uint32_t lo = run, hi = run + (q & 0xFFFFu);
+        run = hi + (q >> 16);
+        hrow[v] = (lo & 0xFFFFu) | (hi << 16);
+      }
     }
     __syncthreads();  // B
 
@@ -407,7 +469,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
       const uint32_t d = dr[i] & 511u;
       if (d < RADIX) {
         const int idx = wbase + i * 32 + lane;
-        const uint32_t pos = uint32_t(wh[d]) + (dr[i] >> 9);
+        const uint32_t pos = uint32_t(whist[d * (2 * L::HSTRIDE) + warp]) + (dr[i] >> 9);
         ok[pos] = sk[idx];
         if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
         if (DIGIT == DIGIT_LEARNED) s_dig[pos] = uint8_t(d);
@@ -459,6 +521,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
         s_vptr[tid] = reinterpret_cast<unsigned long long>(vdst) + (unsigned long long)(delta * (long long)sizeof(V));
     }
     __syncthreads();  // C
+    if (PERSIST)  // counters of the next tile (barrier D follows before its ranking)
+      for (int i = tid; i < HROW * L::HSTRIDE; i += BLOCK) reinterpret_cast<uint32_t *>(whist)[i] = 0u;
 
     // ---- write the tile out: consecutive threads store consecutive keys of a digit run
     if (tile_n == TILE) {
