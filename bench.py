@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
                     help="c2 (default): the headline line; the others print their own lines")
+    ap.add_argument("--segments", type=int, default=65536, help="c4: number of segments")
     return ap.parse_args()
 
 
@@ -502,7 +503,7 @@ def run_workload(args):
                       "plain_GBps_all": round(tot_b / (tot_p / 1e3) / 1e9, 3), "results": res,
                       "smooth_268M": big, "literal_2x_key_bytes_frac_of_8TBs": round(2 * value / NOMINAL_HBM_GBS, 4)})
     elif args.workload == "c4":
-        off = synth.lognormal_segments(65536, seed=20)
+        off = synth.lognormal_segments(args.segments, seed=20)
         n = int(off[-1])
         keys = synth.uniform_u32(n, seed=21)
         pristine = torch.from_numpy(keys.view(np.int32)).to(dev)
@@ -525,12 +526,12 @@ def run_workload(args):
 
         ms = _timed(torch, torch.cuda.current_stream(dev), flush, restore, call, W, K)
         gbs = keys.nbytes / (ms / 1e3) / 1e9
-        _line(args, f"65,536 segments, lognormal lengths (median 2,048), {n:,} u32 keys, one persistent launch "
+        _line(args, f"{args.segments:,} segments, lognormal lengths (median 2,048), {n:,} u32 keys, one persistent launch "
               "replayed from a CUDA graph", gbs,
               {"dtype": "u32", "ms": round(ms, 4), "keys": n, "roofline_2x_bytes_frac_of_measured": round(2 * gbs / peak, 4)})
     elif args.workload == "c5":
         n = args.n if args.n != FULL_N else 1 << 30
-        keys = synth.zipf_mix_u32(n, seed=30)
+        keys = synth.zipf_mix_u32(n, seed=30, workers=os.cpu_count() or 1)
         vals = np.arange(n, dtype=np.uint32)
         gp, mp, _ = sort_gbs(keys, ak.AK_U32, {"path": ak.AK_PATH_RADIX}, op="pairs", vals=vals, order="descending")
         gl, ml, info = sort_gbs(keys, ak.AK_U32, {"path": ak.AK_PATH_LEARNED}, op="pairs", vals=vals,

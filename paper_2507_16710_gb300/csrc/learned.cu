@@ -61,26 +61,32 @@ __device__ __forceinline__ void lm_point(const float *p, const float *c, float x
   }
 }
 
-// Gradient of parameter q summed over the CTA's points in order.
-__device__ __forceinline__ float lm_param_grad(const GradSmem &g, int q) {
-  float s = 0.f;
-  if (q < LM_P_B1) {
-    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s = fmaf(g.d1[t][q], g.x[t], s);
-  } else if (q < LM_P_W2) {
-    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.d1[t][q - LM_P_B1];
-  } else if (q < LM_P_B2) {
-    const int j = (q - LM_P_W2) / LM_HID, k = (q - LM_P_W2) % LM_HID;
-    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s = fmaf(g.d2[t][j], g.h1[t][k], s);
-  } else if (q < LM_P_W3) {
-    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.d2[t][q - LM_P_B2];
-  } else if (q < LM_P_B3) {
-    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s = fmaf(g.d3[t], g.h2[t][q - LM_P_W3], s);
-  } else if (q == LM_P_B3) {
-    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.d3[t];
-  } else {  // q == LM_PARAMS: the loss numerator
-    for (int t = 0; t < LM_TRAIN_BLOCK; ++t) s += g.e2[t];
+// Gradient of parameter q summed over the CTA's points: four interleaved
+// accumulators (point t goes to accumulator t % 4), combined in a fixed order,
+// so the result is deterministic and the dependent chain is a quarter as long.
+template <typename F>
+__device__ __forceinline__ float lm_sum4(F term) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  for (int t = 0; t < LM_TRAIN_BLOCK; t += 4) {
+    s0 += term(t);
+    s1 += term(t + 1);
+    s2 += term(t + 2);
+    s3 += term(t + 3);
   }
-  return s;
+  return (s0 + s1) + (s2 + s3);
+}
+
+__device__ __forceinline__ float lm_param_grad(const GradSmem &g, int q) {
+  if (q < LM_P_B1) return lm_sum4([&](int t) { return g.d1[t][q] * g.x[t]; });
+  if (q < LM_P_W2) return lm_sum4([&](int t) { return g.d1[t][q - LM_P_B1]; });
+  if (q < LM_P_B2) {
+    const int j = (q - LM_P_W2) / LM_HID, k = (q - LM_P_W2) % LM_HID;
+    return lm_sum4([&](int t) { return g.d2[t][j] * g.h1[t][k]; });
+  }
+  if (q < LM_P_W3) return lm_sum4([&](int t) { return g.d2[t][q - LM_P_B2]; });
+  if (q < LM_P_B3) return lm_sum4([&](int t) { return g.d3[t] * g.h2[t][q - LM_P_W3]; });
+  if (q == LM_P_B3) return lm_sum4([&](int t) { return g.d3[t]; });
+  return lm_sum4([&](int t) { return g.e2[t]; });  // q == LM_PARAMS: the loss numerator
 }
 
 constexpr int LM_SLOTS = LM_PARAMS + 1;  // gradients + loss numerator

@@ -23,6 +23,8 @@ with the dtypes of Sec. IV and the sizes of Sec. IV-C):
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 __all__ = [
@@ -121,6 +123,7 @@ def normal_f32_special(n: int, seed: int = 3, frac: float = 0.001) -> np.ndarray
 F64_DISTS = ("uniform", "normal", "lognormal", "zipf", "presorted", "reversed")
 
 
+@functools.lru_cache(maxsize=4)
 def _zipf_cdf(s: float, nranks: int):
     w = np.arange(1, nranks + 1, dtype=np.float64) ** (-s)
     cdf = np.cumsum(w)
@@ -201,20 +204,34 @@ def fmix32(x: np.ndarray) -> np.ndarray:
     return x
 
 
-def zipf_mix_u32(n: int, seed: int = 30, s: float = 1.1, nranks: int = 1 << 24) -> np.ndarray:
-    """Per key a fair coin picks Zipf(s) over ``nranks`` ranks (rank k maps to
-    fmix32(k-1)) or a uniform u32."""
-    out = np.empty(n, dtype=np.uint32)
+def _zipf_mix_chunk(args):
+    lo, hi, seed, s, nranks = args
     cdf, total = _zipf_cdf(s, nranks)
-    for lo in range(0, n, _CHUNK):
-        hi = min(n, lo + _CHUNK)
-        z = splitmix64(seed, hi - lo, lo)
-        coin = (z >> np.uint64(63)).astype(bool)
-        u = (z & np.uint64((1 << 53) - 1)).astype(np.float64) * (2.0 ** -53)
-        ranks = _zipf_invert(u, cdf, total, s)
-        zipf_keys = fmix32(ranks.astype(np.uint32))
-        uni = ((z >> np.uint64(16)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
-        out[lo:hi] = np.where(coin, zipf_keys, uni)
+    z = splitmix64(seed, hi - lo, lo)
+    coin = (z >> np.uint64(63)).astype(bool)
+    u = (z & np.uint64((1 << 53) - 1)).astype(np.float64) * (2.0 ** -53)
+    ranks = _zipf_invert(u, cdf, total, s)
+    zipf_keys = fmix32(ranks.astype(np.uint32))
+    uni = ((z >> np.uint64(16)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    return np.where(coin, zipf_keys, uni)
+
+
+def zipf_mix_u32(n: int, seed: int = 30, s: float = 1.1, nranks: int = 1 << 24, workers: int = 1) -> np.ndarray:
+    """Per key a fair coin picks Zipf(s) over ``nranks`` ranks (rank k maps to
+    fmix32(k-1)) or a uniform u32.  ``workers`` > 1 generates chunks in a spawned
+    process pool (same values: every chunk depends only on its counter range)."""
+    out = np.empty(n, dtype=np.uint32)
+    chunk = 1 << 24
+    jobs = [(lo, min(n, lo + chunk), seed, s, nranks) for lo in range(0, n, chunk)]
+    if workers > 1 and len(jobs) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            for (lo, hi, *_), part in zip(jobs, ex.map(_zipf_mix_chunk, jobs)):
+                out[lo:hi] = part
+    else:
+        for job in jobs:
+            out[job[0]:job[1]] = _zipf_mix_chunk(job)
     return out
 
 
