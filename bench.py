@@ -37,9 +37,11 @@ sys.path.insert(0, ROOT)
 FULL_N = 268_435_456
 METRIC = "keys GB/s sorted (device-timed, 1 GB300) and % of 2×bytes/8TB/s roofline; learned vs plain"
 NOMINAL_HBM_GBS = 8000.0
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of onesweep_pass per key and
-# pass, from the capture summarised in profiles/ (None until captured for the
-# current kernel).
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of onesweep_pass, averaged
+# over the 24 digit-pass launches of one step at 33,554,432 keys per array
+# (profiles/onesweep_pass_traffic_33M.md): (keys per array, bytes per launch).
+# Traffic grows in proportion to the keys, so it is scaled to the run's n.  Set
+# to None whenever the digit-pass kernel changes until it is captured again.
 NCU_TRAFFIC = None
 
 
@@ -312,7 +314,7 @@ def run_ours(args):
     achieved = sum(pass_bytes) / (sum(pass_ms) / 1e3) / 1e9
     traffic = None
     if NCU_TRAFFIC is not None:
-        traffic = NCU_TRAFFIC
+        traffic = int(NCU_TRAFFIC[1] * n / NCU_TRAFFIC[0])
     roofline = {"bound": "hbm", "kernel": "onesweep_pass", "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": f"{peak_kind} (copy, burst)", "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "launches": len(pass_ms),

@@ -54,18 +54,17 @@ cudaError_t radix_launch_u64_sint(const RadixCall &c);
 cudaError_t radix_launch_u64_float(const RadixCall &c);
 
 // Tile shapes of the digit-pass kernel.  Configuration c has CFG_BLOCK[c]
-// threads and stages CFG_STAGES[c] tile buffers of about CFG_BYTES[c] bytes of
-// keys+values each; keys per thread are clamped to [2, 16].  Persistent
-// configurations launch one wave of CTAs that loop over tiles with bulk copies
-// in flight ahead of use; the others launch one CTA per tile.
-constexpr int CFG_BLOCK[3] = {512, 256, 512};
+// threads and a tile of about CFG_BYTES[c] bytes of keys+values (keys per
+// thread clamped to [2, 12]).  Persistent configurations launch one wave of
+// CTAs that loop over tiles, each copying its next tile in while it finishes
+// the current one; the other launches one CTA per tile.
+constexpr int CFG_BLOCK[3] = {512, 512, 512};
 constexpr int CFG_BYTES[3] = {32768, 16384, 32768};
-constexpr int CFG_STAGES[3] = {1, 1, 2};
-constexpr bool CFG_PERSIST[3] = {false, false, true};
+constexpr bool CFG_PERSIST[3] = {true, true, false};
 
 constexpr int tile_items(int key_bytes, int val_bytes, int cfg) {
-  return (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) < 2   ? 2
-         : (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) > 16 ? 16
+  return (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) < 2    ? 2
+         : (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) > 12 ? 12
                                                                                : CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes));
 }
 constexpr int tile_keys(int key_bytes, int val_bytes, int cfg) {

@@ -5,14 +5,14 @@
 //   plan_kernel      exclusive scan of each pass's 256 counts; marks "trivial"
 //                    passes (one digit holds all n keys: a stable no-op) so they
 //                    move no data
-//   onesweep_pass    per active pass: each CTA takes the next tile id, stages
-//                    the tile in shared memory with one bulk copy, ranks keys by
-//                    digit with a warp multisplit (match.any), publishes its
-//                    per-digit counts, finds its global offsets by decoupled
-//                    look-back over predecessor tiles (the "opportunistic
-//                    look-back" scan the paper's accumulate uses, Sec. II-B), and
-//                    writes the tile out in digit order from shared memory so
-//                    each warp stores contiguous runs
+//   onesweep_pass    per active pass: CTAs take tile ids in increasing order,
+//                    stage each tile in shared memory with a bulk copy issued
+//                    ahead of use, rank keys by digit with a warp multisplit,
+//                    publish per-digit counts, find their global offsets by
+//                    decoupled look-back over predecessor tiles (the
+//                    "opportunistic look-back" scan the paper's accumulate
+//                    uses, Sec. II-B), and write the tile out in digit order
+//                    from shared memory so each warp stores contiguous runs
 //   finish_kernel    copy-back when an odd number of passes moved data, or the
 //                    identity permutation when none did
 //
@@ -23,11 +23,6 @@
 
 #include "common.cuh"
 #include "learned.cuh"
-
-// Warp matcher used by the digit passes (see warp_peers below).
-#ifndef AK_WARP_MATCH
-#define AK_WARP_MATCH 2
-#endif
 
 namespace ak {
 
@@ -82,11 +77,6 @@ struct PassArgs {
 
 // Digit of a key in a pass: a radix digit, or a byte of the learned bucket id.
 enum DigitSource : int { DIGIT_RADIX = 0, DIGIT_LEARNED = 1 };
-template <int DIGIT, int KIND, typename U, typename V>
-__device__ __forceinline__ uint32_t pass_digit(const PassArgs<U, V> &a, U k, int shift) {
-  if constexpr (DIGIT == DIGIT_LEARNED) return (lm_key_bucket<KIND>(a.model, k, a.flip) >> shift) & (RADIX - 1);
-  else return digit_of(radix_key_t<KIND>(k, a.flip), shift);
-}
 
 // ------------------------------------------------------------------ histogram
 template <typename U, int BLOCK>
@@ -157,93 +147,111 @@ static __global__ void __launch_bounds__(RADIX) plan_kernel(const unsigned long 
 }
 
 // ---------------------------------------------------------------- digit pass
-// Persistent CTAs walk tiles in increasing id order (ids from an atomic counter).
-// A ring of STAGES shared-memory tile buffers is filled by the bulk-copy engine
-// ahead of use, so loads of later tiles overlap the ranking, look-back and
-// write-out of the current one.  Forward progress of the look-back: every CTA
-// processes the tiles it holds in increasing order, so the holder of the
-// smallest unfinished tile only waits on finished tiles.
-template <typename U, typename V, bool HAS_V, int BLOCK, int ITEMS, int STAGES, int DIGIT = DIGIT_RADIX>
+// Digit of a key in a radix pass.  A 64-bit key's digit lies in one 32-bit
+// half (the same half for every key of a pass), so only that half is
+// transformed; the result equals digit_of(radix_key_t(k)).
+template <int KIND, typename U>
+__device__ __forceinline__ uint32_t radix_digit(U k, U flip, int shift) {
+  if constexpr (sizeof(U) == 8) {
+    const uint32_t lo = uint32_t(k), hi = uint32_t(uint64_t(k) >> 32);
+    const bool upper = shift >= 32;
+    uint32_t w = upper ? hi : lo;
+    const uint32_t f = upper ? uint32_t(uint64_t(flip) >> 32) : uint32_t(flip);
+    if constexpr (KIND == KIND_SINT) {
+      if (upper) w ^= 0x80000000u;
+    } else if constexpr (KIND == KIND_FLOAT) {
+      const uint32_t neg = uint32_t(int32_t(hi) >> 31);  // negative: every bit flips
+      w ^= neg | (upper ? 0x80000000u : 0u);             // otherwise only the sign bit
+      const uint32_t mh = hi & 0x7FFFFFFFu;
+      if (mh > 0x7FF00000u || (mh == 0x7FF00000u && lo != 0u)) w = 0xFFFFFFFFu;  // NaN: all ones
+    }
+    return ((w ^ f) >> (shift & 31)) & uint32_t(RADIX - 1);
+  } else {
+    return digit_of(radix_key_t<KIND>(k, flip), shift);
+  }
+}
+
+template <int DIGIT, int KIND, typename U, typename V>
+__device__ __forceinline__ uint32_t pass_digit(const PassArgs<U, V> &a, U k, int shift) {
+  if constexpr (DIGIT == DIGIT_LEARNED) return (lm_key_bucket<KIND>(a.model, k, a.flip) >> shift) & (RADIX - 1);
+  else return radix_digit<KIND>(k, a.flip, shift);
+}
+
+// Shared memory of the digit pass: the staged tile (keys then values, filled
+// by the bulk-copy engine), the same tile in digit order, and the ranking
+// state.
+template <typename U, typename V, bool HAS_V, int BLOCK, int ITEMS>
 struct PassSmem {
   static constexpr int TILE = BLOCK * ITEMS;
   static constexpr int NW = BLOCK / 32;
-  static constexpr int HROW = RADIX + 2;  // u16 per warp row: digits + the invalid-key slot
+  static constexpr int HROW = RADIX + 1;  // digit rows + the padding digit of a ragged tile
   static constexpr size_t KEYS = size_t(TILE) * sizeof(U);
   static constexpr size_t VALS = HAS_V ? size_t(TILE) * sizeof(V) : 0;
   static constexpr size_t STAGE = (KEYS + VALS + 127) / 128 * 128;
-  static constexpr size_t OFF_OUT = STAGE * STAGES;  // the tile in digit order
-  static constexpr size_t OFF_HIST = OFF_OUT + STAGE;
-  // OFF_HIST: u16 counters, digit-major: row d holds the NW warps' counters of
-  // digit d in NW/2 words plus one pad word, so rows start in distinct banks
+  static constexpr size_t OFF_OUT = STAGE;  // the tile in digit order
+  // u16 warp counters, digit-major: row d holds the NW warps' counters of
+  // digit d in NW/2 words plus one pad word, so consecutive rows start in
+  // different banks
   static constexpr int HSTRIDE = NW / 2 + 1;  // 32-bit words per digit row (odd)
+  static constexpr size_t OFF_HIST = OFF_OUT + STAGE;
   static constexpr size_t OFF_MASK = (OFF_HIST + size_t(HROW) * HSTRIDE * 4 + 15) / 16 * 16;  // u32[NW][HROW]
-  static constexpr size_t MASK_BYTES = AK_WARP_MATCH == 3 ? 8 : 4;                          // per digit and warp
-  static constexpr size_t OFF_KPTR = OFF_MASK + size_t(NW) * HROW * MASK_BYTES;             // u64[RADIX]
-  static constexpr size_t OFF_VPTR = OFF_KPTR + RADIX * 8;                                  // u64[RADIX]
-  static constexpr size_t OFF_SCR = OFF_VPTR + (HAS_V ? RADIX * 8 : 0);                     // u32[NW+1]
-  static constexpr size_t OFF_BAR = (OFF_SCR + (NW + 1) * 4 + 15) / 16 * 16;             // u64[STAGES]
-  static constexpr size_t OFF_TILE = OFF_BAR + 8 * STAGES;                                // u32[STAGES]
-  static constexpr size_t OFF_FLAG = OFF_TILE + 4 * STAGES;                               // u32
-  static constexpr size_t OFF_DIG = OFF_FLAG + 16;  // u8[TILE]: digits in tile order (learned digits)
-  static constexpr size_t BYTES = OFF_DIG + (DIGIT == DIGIT_LEARNED ? size_t(TILE) : 0);
+  static constexpr size_t OFF_DELTA = (OFF_MASK + size_t(NW) * HROW * 4 + 15) / 16 * 16;      // i32 or i64 [RADIX]
+  static constexpr size_t OFF_SCR = OFF_DELTA + size_t(RADIX) * 8;                           // u32[RADIX/32]
+  static constexpr size_t OFF_BAR = (OFF_SCR + (RADIX / 32) * 4 + 15) / 16 * 16;               // u64
+  static constexpr size_t OFF_TILE = OFF_BAR + 8;                                            // i64: next tile
+  static constexpr size_t OFF_FLAG = OFF_TILE + 8;                                           // u32
+  static constexpr size_t OFF_DIG = (OFF_FLAG + 4 + 15) / 16 * 16;  // u8[TILE]: digit of each output slot
+  static constexpr size_t BYTES = OFF_DIG + size_t(TILE);
   static_assert(TILE < 65536, "warp bases are u16");
   static_assert(NW % 2 == 0, "two 16-bit counters per word");
-  static_assert(KEYS % 16 == 0 && STAGE % 128 == 0 && OFF_MASK % 16 == 0 && OFF_KPTR % 8 == 0 &&
-                    OFF_BAR % 8 == 0,
+  static_assert(KEYS % 16 == 0 && STAGE % 128 == 0 && OFF_DELTA % 8 == 0 && OFF_BAR % 8 == 0 && OFF_TILE % 8 == 0,
                 "shared-memory arrays aligned to their element size (bulk copies: 16 bytes)");
 };
 
 constexpr int LOOKBACK_WINDOW = 8;  // predecessor words probed per round trip
 
-// Lanes of the warp holding the same digit.  AK_WARP_MATCH selects match.any
-// (0), a bit-sliced match from ballots (1: the peers of a lane are the lanes
-// agreeing on every bit; 9 bits when the padding digit RADIX can occur), a
-// shared-memory mask per digit that every lane ORs its bit into (2, default:
-// fixed cost), or the same with two items per step in 64-bit masks (3: half the
-// dependent round trips but twice the mask memory; measured slower on GB300).
-// (AK_WARP_MATCH is defined at the top of this file.)
-__device__ __forceinline__ uint32_t warp_peers(uint32_t d, bool nine_bits) {
-#if AK_WARP_MATCH == 0
-  (void)nine_bits;
-  return __match_any_sync(0xffffffffu, d);
-#else
-  uint32_t peers = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-    peers &= ((d >> b) & 1u) ? bal : ~bal;
-  }
-  if (nine_bits) {
-    const uint32_t bal = __ballot_sync(0xffffffffu, (d >> 8) & 1u);
-    peers &= ((d >> 8) & 1u) ? bal : ~bal;
-  }
-  return peers;
-#endif
-}
-
-template <typename U, typename V, bool HAS_V, int KIND, typename S, int BLOCK, int ITEMS, int STAGES,
-          bool PERSIST, int DIGIT = DIGIT_RADIX>
+// One digit pass.  Tile ids come from an atomic counter, so every predecessor
+// of a tile is held by a CTA that already runs (forward progress of the
+// look-back).  PERSIST: a wave of CTAs loops over tiles; a CTA claims its next
+// tile as soon as the current tile's counts are published (a tile claimed
+// earlier would hold up every later tile's look-back), pulls it into L2, and
+// starts its bulk copy into the stage buffer once the current tile has left
+// it, so the copy overlaps the look-back and the write-out.  Otherwise one CTA
+// per tile, which also pulls the tile one residency wave ahead into L2.
+//
+// Per tile: (1) digit of every key, warp multisplit rank: peers of a digit
+// found by OR-ing lane bits into a per-warp shared mask word, per-warp 16-bit
+// counters, stable rank = running count + popc(peers below this lane);
+// (2) per-digit tile counts published (flag AGG), a CTA scan of the 256 counts
+// gives digit starts and warp bases; (3) scatter into the output buffer in
+// digit order; (4) decoupled look-back, inclusive counts published (flag INC);
+// (5) write-out: consecutive threads store consecutive slots of a digit run.
+template <typename U, typename V, bool HAS_V, int KIND, typename S, int BLOCK, int ITEMS, bool PERSIST,
+          int DIGIT = DIGIT_RADIX>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U, V> a) {
-  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS, STAGES, DIGIT>;
+  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
   constexpr int TILE = L::TILE;
   constexpr int NW = L::NW;
   constexpr int HROW = L::HROW;
-  static_assert(BLOCK >= RADIX, "one digit per thread in the look-back");
-  static_assert(PERSIST ? STAGES >= 2 : STAGES == 1, "stage ring");
+  constexpr int H2 = 2 * L::HSTRIDE;  // u16 slots per digit row
+  static_assert(BLOCK >= RADIX, "one digit per thread in the scan and look-back");
   extern __shared__ __align__(128) uint8_t smem[];
+  U *sk = reinterpret_cast<U *>(smem);
+  V *sv = reinterpret_cast<V *>(smem + L::KEYS);
+  U *ok = reinterpret_cast<U *>(smem + L::OFF_OUT);
+  V *ov = reinterpret_cast<V *>(smem + L::OFF_OUT + L::KEYS);
   uint16_t *whist = reinterpret_cast<uint16_t *>(smem + L::OFF_HIST);
+  uint32_t *whist32 = reinterpret_cast<uint32_t *>(smem + L::OFF_HIST);
   uint32_t *wmask = reinterpret_cast<uint32_t *>(smem + L::OFF_MASK);
-  unsigned long long *wmask2 = reinterpret_cast<unsigned long long *>(smem + L::OFF_MASK);
-  // per digit: address of the destination of tile position 0 (base + delta,
-  // kept as an integer; base + delta + i is inside the buffer for every key)
-  unsigned long long *s_kptr = reinterpret_cast<unsigned long long *>(smem + L::OFF_KPTR);
-  unsigned long long *s_vptr = reinterpret_cast<unsigned long long *>(smem + L::OFF_VPTR);
+  // per digit: destination index of output slot 0 (32-bit when every index fits)
+  using Delta = typename std::conditional<sizeof(S) == 4, int32_t, long long>::type;
+  Delta *s_delta = reinterpret_cast<Delta *>(smem + L::OFF_DELTA);
   uint32_t *s_scr = reinterpret_cast<uint32_t *>(smem + L::OFF_SCR);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::OFF_BAR);
-  uint32_t *s_tile = reinterpret_cast<uint32_t *>(smem + L::OFF_TILE);
+  long long *s_next = reinterpret_cast<long long *>(smem + L::OFF_TILE);
   uint32_t *s_flag = reinterpret_cast<uint32_t *>(smem + L::OFF_FLAG);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *s_dig = smem + L::OFF_DIG;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (a.gate && *a.gate != a.gate_want) return;
 
   // Clear the next pass's look-back rows (the grid covers rows blockIdx.x + k*gridDim.x).
@@ -283,49 +291,40 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
                        (!load_v || ((reinterpret_cast<uintptr_t>(vsrc) & 15) == 0));
   const int64_t full_tiles = a.n / TILE;  // tiles that need no bounds checks
   auto is_bulk = [&](int64_t t) { return aligned && t < full_tiles; };
-  const uint32_t tx_bytes = uint32_t(L::KEYS + (load_v ? L::VALS : 0));
-  auto stage_keys = [&](int s) { return reinterpret_cast<U *>(smem + size_t(s) * L::STAGE); };
-  auto stage_vals = [&](int s) { return reinterpret_cast<V *>(smem + size_t(s) * L::STAGE + L::KEYS); };
-  auto next_tile = [&]() -> int64_t {
-    return int64_t(atomicAdd(&a.hdr->tile_counter[a.pass], 1u)) + (a.debug_skip ? 1 : 0);
+  uint32_t phase = 0;     // thread 0: parity of the next completion of bar
+  bool pending = false;   // thread 0: a bulk copy is in flight
+  auto claim = [&]() -> int64_t {
+    const int64_t t = int64_t(atomicAdd(&a.hdr->tile_counter[a.pass], 1u)) + (a.debug_skip ? 1 : 0);
+    return t < a.num_tiles ? t : a.num_tiles;
   };
-  auto issue = [&](int s, int64_t t) {  // thread 0 only
+  constexpr int CLAIMER = BLOCK - 1;  // claims the next tile; not a look-back thread when BLOCK > RADIX
+  auto issue = [&](int64_t t) {  // thread 0 only; the stage buffer must be free
     if (t < a.num_tiles && is_bulk(t)) {
-      mbar_expect_tx(&bar[s], tx_bytes);
-      bulk_g2s(stage_keys(s), ksrc + t * TILE, uint32_t(L::KEYS), &bar[s]);
-      if (load_v) bulk_g2s(stage_vals(s), vsrc + t * TILE, uint32_t(L::VALS), &bar[s]);
+      mbar_expect_tx(bar, uint32_t(L::KEYS + (load_v ? L::VALS : 0)));
+      bulk_g2s(sk, ksrc + t * TILE, uint32_t(L::KEYS), bar);
+      if (load_v) bulk_g2s(sv, vsrc + t * TILE, uint32_t(L::VALS), bar);
+      pending = true;
+    }
+  };
+  auto prefetch_l2 = [&](int64_t t) {  // thread 0 only
+    if (t < full_tiles && aligned) {
+      bulk_prefetch_l2(ksrc + t * TILE, uint32_t(L::KEYS));
+      if (load_v) bulk_prefetch_l2(vsrc + t * TILE, uint32_t(L::VALS));
     }
   };
 
-  for (int i = tid; i < NW * HROW * int(L::MASK_BYTES / 4); i += BLOCK) wmask[i] = 0u;
-  for (int i = tid; i < HROW * L::HSTRIDE; i += BLOCK) reinterpret_cast<uint32_t *>(whist)[i] = 0u;
-  uint32_t phase_bits = 0;  // thread 0: parity to wait for, per stage
+  for (int i = tid; i < NW * HROW; i += BLOCK) wmask[i] = 0u;
+  for (int i = tid; i < HROW * L::HSTRIDE; i += BLOCK) whist32[i] = 0u;
+  int64_t next_tile = 0;  // CLAIMER: the tile claimed for the next iteration
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
-    for (int s = 0; s < STAGES; ++s) {
-      const int64_t t = next_tile();
-      s_tile[s] = uint32_t(t < a.num_tiles ? t : a.num_tiles);
-      issue(s, t);
-      // one-tile CTAs: pull the tile about one residency wave ahead into L2 so
-      // HBM stays busy while CTAs rank, look back and write
-      if (!PERSIST && a.prefetch_ahead > 0) {
-        const int64_t tp = t + a.prefetch_ahead;
-        if (tp < full_tiles && aligned) {
-          bulk_prefetch_l2(ksrc + tp * TILE, uint32_t(L::KEYS));
-          if (load_v) bulk_prefetch_l2(vsrc + tp * TILE, uint32_t(L::VALS));
-        }
-      }
-    }
+    mbar_init(bar, 1);
+    const int64_t t = claim();
+    *s_next = (long long)t;
+    issue(t);
+    // one-tile CTAs: pull the tile about one residency wave ahead into L2 so
+    // HBM stays busy while CTAs rank, look back and write
+    if (!PERSIST && a.prefetch_ahead > 0) prefetch_l2(t + a.prefetch_ahead);
     *s_flag = 0;
-    // the first stage must be resident before the loop starts
-    const int64_t t0 = s_tile[0];
-    if (t0 < a.num_tiles && is_bulk(t0)) {
-      if (!mbar_wait_bounded(&bar[0], 0, a.timeout_ns)) {
-        set_error(a.hdr, AK_ERR_TIMEOUT);
-        *s_flag = 1;
-      }
-      phase_bits ^= 1u;
-    }
   }
   __syncthreads();
 
@@ -333,17 +332,25 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
   const uint32_t lt_mask = lanemask_lt();
   const uint32_t gt_mask = ~(lt_mask | (1u << lane));
   uint32_t *wm = wmask + warp * HROW;
-  unsigned long long *wm2 = wmask2 + warp * HROW;
   S *st = reinterpret_cast<S *>(a.status_cur);
 
-  for (int it = 0;; ++it) {
-    const int s = it % STAGES;
-    const int64_t tile = s_tile[s];
-    if (tile >= a.num_tiles || *s_flag) break;  // uniform: read after a barrier
+  for (;;) {
+    const int64_t tile = *s_next;  // written by thread 0 before barriers B and C of the previous tile
+    if (tile >= a.num_tiles) break;
+    if (tid == 0 && pending) {
+      if (mbar_wait_bounded(bar, phase, a.timeout_ns)) {
+        pending = false;
+        phase ^= 1u;
+      } else {  // the copy is still owed: the exit path waits for it again
+        set_error(a.hdr, AK_ERR_TIMEOUT);
+        *s_flag = 1;
+      }
+    }
+    __syncthreads();  // S: the tile is resident; the previous tile is fully written out
+    if (*s_flag) break;
+
     const int64_t base = tile * TILE;
     const int tile_n = int((a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE));
-    U *sk = stage_keys(s);
-    V *sv = stage_vals(s);
     if (!is_bulk(tile)) {  // ragged last tile or unaligned source: plain loads
       for (int i = tid; i < tile_n; i += BLOCK) sk[i] = ksrc[base + i];
       if (load_v)
@@ -351,224 +358,175 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
       __syncthreads();
     }
 
-    // ---- warp multisplit ranking (item i of lane l sits at wbase + 32 i + l)
-    const int wbase = warp * 32 * ITEMS;
-    uint32_t dr[ITEMS];  // rank << 9 | digit (digit RADIX marks a padding slot)
+    auto body = [&](auto full_tag) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      // ---- warp multisplit ranking (item i of lane l sits at wbase + 32 i + l)
+      const int wbase = warp * 32 * ITEMS;
+      uint32_t dr[ITEMS];  // rank << 9 | digit (digit RADIX marks a padding slot)
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const int idx = wbase + i * 32 + lane;
-      dr[i] = (idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
-    }
-#if AK_WARP_MATCH == 3
-    // two items per step: lane l sets bit l (item A) and bit 32 + l (item B) of
-    // the 64-bit mask of its digit; one read gives both peer sets and how many
-    // lanes of item A (all earlier than item B) share item B's digit.  Each
-    // digit's counter is advanced by exactly one leader: A's group leader, or
-    // B's when no lane of A has that digit.
-#pragma unroll
-    for (int i = 0; i + 1 < ITEMS; i += 2) {
-      const uint32_t dA = dr[i], dB = dr[i + 1];
-      uint16_t *cA = whist + dA * (2 * L::HSTRIDE) + warp;
-      uint16_t *cB = whist + dB * (2 * L::HSTRIDE) + warp;
-      atomicOr(&wm2[dA], 1ull << lane);
-      atomicOr(&wm2[dB], 1ull << (32 + lane));
-      __syncwarp();
-      const unsigned long long MA = wm2[dA], MB = wm2[dB];
-      const uint32_t nA = *cA, nB = *cB;
-      __syncwarp();
-      const uint32_t peersA = uint32_t(MA), peersB = uint32_t(MB >> 32), aInB = uint32_t(MB);
-      if ((peersA & gt_mask) == 0) {
-        *cA = uint16_t(nA + __popcll(MA));
-        wm2[dA] = 0ull;
-      }
-      if (aInB == 0u && (peersB & gt_mask) == 0) {
-        *cB = uint16_t(nB + __popc(peersB));
-        wm2[dB] = 0ull;
-      }
-      __syncwarp();
-      dr[i] = ((nA + __popc(peersA & lt_mask)) << 9) | dA;
-      dr[i + 1] = ((nB + __popc(aInB) + __popc(peersB & lt_mask)) << 9) | dB;
-    }
-    if (ITEMS & 1) {  // odd item count: the last item alone
-      const uint32_t d = dr[ITEMS - 1];
-      uint16_t *wc = whist + d * (2 * L::HSTRIDE) + warp;
-      atomicOr(&wm2[d], 1ull << lane);
-      __syncwarp();
-      const uint32_t peers = uint32_t(wm2[d]);
-      const uint32_t cnt = *wc;
-      __syncwarp();
-      if ((peers & gt_mask) == 0) {
-        *wc = uint16_t(cnt + __popc(peers));
-        wm2[d] = 0ull;
-      }
-      __syncwarp();
-      dr[ITEMS - 1] = ((cnt + __popc(peers & lt_mask)) << 9) | d;
-    }
-#else
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const uint32_t d = dr[i];
-#if AK_WARP_MATCH == 2
-      uint16_t *wc = whist + d * (2 * L::HSTRIDE) + warp;  // this warp's running count of digit d
-      atomicOr(&wm[d], 1u << lane);
-      __syncwarp();
-      const uint32_t peers = wm[d];
-      const uint32_t cnt = *wc;
-      __syncwarp();
-      if ((peers & gt_mask) == 0) {  // highest lane of the group updates and resets
-        *wc = uint16_t(cnt + __popc(peers));
-        wm[d] = 0u;
-      }
-      __syncwarp();
-#else
-      uint16_t *wc = whist + d * (2 * L::HSTRIDE) + warp;
-      const uint32_t peers = warp_peers(d, tile_n != TILE);
-      const bool leader = (peers & gt_mask) == 0;  // highest lane of the group
-      uint32_t cnt = 0;
-      if (leader) cnt = *wc;
-      if (leader) *wc = uint16_t(cnt + __popc(peers));
-      cnt = __shfl_sync(0xffffffffu, cnt, 31 - __clz(peers));
-      __syncwarp();
-#endif
-      dr[i] = ((cnt + __popc(peers & lt_mask)) << 9) | d;
-    }
-#endif
-    __syncthreads();  // A: every warp row complete
-
-    // ---- per-digit tile counts, publish, warp bases = tile digit start + earlier warps
-    uint32_t my_cnt = 0;
-    uint32_t *hrow = reinterpret_cast<uint32_t *>(whist) + tid * L::HSTRIDE;
-    if (tid < RADIX) {
-#pragma unroll
-      for (int v = 0; v < NW / 2; ++v) {
-        const uint32_t q = hrow[v];
-        my_cnt += (q & 0xFFFFu) + (q >> 16);
-      }
-      const S word = (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt);
-      st_relaxed(&st[tile * RADIX + tid], word);
-    }
-    uint32_t total;
-    const uint32_t start = block_exclusive_scan<BLOCK>(tid < RADIX ? my_cnt : 0u, s_scr, &total);
-    if (tid < RADIX) {  // each warp's base = tile digit start + counts of earlier warps
-      uint32_t run = start;
-#pragma unroll
-      for (int v = 0; v < NW / 2; ++v) {
-        const uint32_t q = hrow[v];
-        const uint32_t lo = run, hi = run + (q & 0xFFFFu);
-        run = hi + (q >> 16);
-        hrow[v] = (lo & 0xFFFFu) | (hi << 16);
-      }
-    }
-    __syncthreads();  // B
-
-    // ---- scatter the stage into the output buffer in digit order
-    U *ok = reinterpret_cast<U *>(smem + L::OFF_OUT);
-    V *ov = reinterpret_cast<V *>(smem + L::OFF_OUT + L::KEYS);
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const uint32_t d = dr[i] & 511u;
-      if (d < RADIX) {
+      for (int i = 0; i < ITEMS; ++i) {
         const int idx = wbase + i * 32 + lane;
-        const uint32_t pos = uint32_t(whist[d * (2 * L::HSTRIDE) + warp]) + (dr[i] >> 9);
-        ok[pos] = sk[idx];
-        if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
-        if (DIGIT == DIGIT_LEARNED) s_dig[pos] = uint8_t(d);
+        dr[i] = (FULL || idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
       }
-    }
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = dr[i];
+        uint16_t *wc = whist + d * H2 + warp;  // this warp's running count of digit d
+        atomicOr(&wm[d], 1u << lane);
+        __syncwarp();
+        const uint32_t peers = wm[d];
+        const uint32_t cnt = *wc;
+        __syncwarp();
+        if ((peers & gt_mask) == 0) {  // highest lane of the group updates and resets
+          *wc = uint16_t(cnt + __popc(peers));
+          wm[d] = 0u;
+        }
+        __syncwarp();
+        dr[i] = ((cnt + __popc(peers & lt_mask)) << 9) | d;
+      }
+      __syncthreads();  // A: every warp row complete
 
-    // ---- decoupled look-back over a window of predecessors per probe
-    if (tid < RADIX) {
-      unsigned long long excl = 0;
-      if (tile > 0) {
-        int64_t j = tile - 1;
-        uint64_t t0 = 0;
-        uint32_t spins = 0;
-        bool done = false;
-        while (!done) {
-          S w4[LOOKBACK_WINDOW];
+      // ---- tile counts, publish, digit scan
+      uint32_t my_cnt = 0, inc = 0;
+      uint32_t *hrow = whist32 + tid * L::HSTRIDE;
+      if (tid < RADIX) {
 #pragma unroll
-          for (int k = 0; k < LOOKBACK_WINDOW; ++k)
-            w4[k] = (j - k >= 0) ? ld_relaxed(&st[(j - k) * RADIX + tid]) : S(0);
-          int used = 0;
+        for (int v = 0; v < NW / 2; ++v) {
+          const uint32_t w = hrow[v];
+          my_cnt += (w & 0xFFFFu) + (w >> 16);
+        }
+        st_relaxed(&st[tile * RADIX + tid], (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt));
+        inc = warp_inclusive_scan(my_cnt);
+        if (lane == 31) s_scr[warp] = inc;
+      }
+
+      __syncthreads();  // A2: warp totals of the digit scan; this tile's counts are published
+      // the next tile is claimed only now (a claimed tile whose counts are not
+      // yet published would hold up every later tile's look-back); the claim's
+      // round trip overlaps the scan and scatter
+      if (PERSIST && tid == CLAIMER) next_tile = claim();
+      uint32_t start = 0;
+      if (tid < RADIX) {
+        start = inc - my_cnt;
 #pragma unroll
-          for (int k = 0; k < LOOKBACK_WINDOW; ++k) {
-            if (done || used != k) break;
-            const uint32_t flag = uint32_t(w4[k] >> StatusWord<S>::SHIFT);
-            if (flag == 0) break;
-            excl += (unsigned long long)(w4[k] & StatusWord<S>::MASK);
-            ++used;
-            if (flag == FLAG_INC || j - k == 0) done = true;
-          }
-          j -= used;
-          if (!done && used == 0) {
-            __nanosleep(64);  // predecessor not published yet: yield issue slots
-            if ((++spins & 31u) == 0) {
-              const uint64_t now = globaltimer_ns();
-              if (t0 == 0) t0 = now;
-              else if (now - t0 > a.timeout_ns) {
-                set_error(a.hdr, AK_ERR_TIMEOUT);
-                done = true;
+        for (int w2 = 0; w2 < RADIX / 32; ++w2)
+          if (w2 < warp) start += s_scr[w2];
+        uint32_t run = start;  // warp bases: digit start + counts of earlier warps
+#pragma unroll
+        for (int v = 0; v < NW / 2; ++v) {
+          const uint32_t w = hrow[v];
+          const uint32_t lo = run, hi = run + (w & 0xFFFFu);
+          run = hi + (w >> 16);
+          hrow[v] = (lo & 0xFFFFu) | (hi << 16);
+        }
+      }
+      __syncthreads();  // B: warp bases ready
+
+      // ---- scatter into the output buffer in digit order
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = dr[i] & 511u;
+        if (FULL || d < RADIX) {
+          const int idx = wbase + i * 32 + lane;
+          const uint32_t pos = uint32_t(whist[d * H2 + warp]) + (dr[i] >> 9);
+          ok[pos] = sk[idx];
+          if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
+          s_dig[pos] = uint8_t(d);
+        }
+      }
+
+      if (PERSIST && tid == CLAIMER) {
+        *s_next = (long long)next_tile;
+        prefetch_l2(next_tile);
+      }
+
+      // ---- decoupled look-back over a window of predecessors per probe
+      if (tid < RADIX) {
+        unsigned long long excl = 0;
+        if (tile > 0) {
+          int64_t j = tile - 1;
+          uint64_t t0 = 0;
+          uint32_t spins = 0;
+          for (;;) {
+            S lb[LOOKBACK_WINDOW];  // lb[k]: status word of predecessor j - k
+#pragma unroll
+            for (int k = 0; k < LOOKBACK_WINDOW; ++k) lb[k] = (j - k >= 0) ? ld_relaxed(&st[(j - k) * RADIX + tid]) : S(0);
+            int used = 0;
+            bool done = false, stop = false;
+#pragma unroll
+            for (int k = 0; k < LOOKBACK_WINDOW; ++k) {
+              const uint32_t flag = uint32_t(lb[k] >> StatusWord<S>::SHIFT);
+              if (!stop) {
+                if (flag == 0) {
+                  stop = true;  // not published yet (tile 0 publishes INC, so j - k >= 0 here)
+                } else {
+                  excl += (unsigned long long)(lb[k] & StatusWord<S>::MASK);
+                  ++used;
+                  if (flag == FLAG_INC) done = stop = true;
+                }
+              }
+            }
+            if (done) break;
+            j -= used;
+            if (used == 0) {
+              __nanosleep(64);  // predecessor not published yet: yield issue slots
+              if ((++spins & 31u) == 0) {
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > a.timeout_ns) {
+                  // partial sums of published predecessors keep every store in bounds
+                  set_error(a.hdr, AK_ERR_TIMEOUT);
+                  break;
+                }
               }
             }
           }
+          st_relaxed(&st[tile * RADIX + tid], (S(FLAG_INC) << StatusWord<S>::SHIFT) | S(excl + my_cnt));
         }
-        const S word = (S(FLAG_INC) << StatusWord<S>::SHIFT) | S(excl + my_cnt);
-        st_relaxed(&st[tile * RADIX + tid], word);
+        s_delta[tid] = Delta((long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start);
       }
-      const long long delta = (long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start;
-      s_kptr[tid] = reinterpret_cast<unsigned long long>(kdst) + (unsigned long long)(delta * (long long)sizeof(U));
-      if (HAS_V)
-        s_vptr[tid] = reinterpret_cast<unsigned long long>(vdst) + (unsigned long long)(delta * (long long)sizeof(V));
-    }
-    __syncthreads();  // C
-    if (PERSIST)  // counters of the next tile (barrier D follows before its ranking)
-      for (int i = tid; i < HROW * L::HSTRIDE; i += BLOCK) reinterpret_cast<uint32_t *>(whist)[i] = 0u;
+      __syncthreads();  // C: output buffer and destinations ready; the stage buffer is free
+      if (PERSIST) {
+        if (tid == 0) issue(*s_next);  // lands while this tile is written out
+        // counters of the next tile (barrier S separates this from its ranking)
+        for (int i = tid; i < HROW * L::HSTRIDE; i += BLOCK) whist32[i] = 0u;
+      }
 
-    // ---- write the tile out: consecutive threads store consecutive keys of a digit run
-    if (tile_n == TILE) {
-#pragma unroll 4
-      for (int r = 0; r < ITEMS; ++r) {
-        const int i = r * BLOCK + tid;
-        const U k = ok[i];
-        const uint32_t d = DIGIT == DIGIT_LEARNED ? uint32_t(s_dig[i]) : digit_of(radix_key_t<KIND>(k, a.flip), shift);
-        if (write_keys) reinterpret_cast<U *>(s_kptr[d])[i] = k;
-        if (HAS_V) reinterpret_cast<V *>(s_vptr[d])[i] = ov[i];
+      // ---- write the tile out: consecutive threads store consecutive slots of a digit run
+      if (FULL) {
+        constexpr int WB = ITEMS % 4 == 0 ? 4 : (ITEMS % 3 == 0 ? 3 : (ITEMS % 2 == 0 ? 2 : 1));
+#pragma unroll
+        for (int r0 = 0; r0 < ITEMS; r0 += WB) {  // WB slots per thread: all loads before the stores
+          U k[WB];
+          long long dst[WB];
+#pragma unroll
+          for (int r = 0; r < WB; ++r) {
+            const int i = (r0 + r) * BLOCK + tid;
+            k[r] = ok[i];
+            dst[r] = (long long)s_delta[s_dig[i]] + i;
+          }
+#pragma unroll
+          for (int r = 0; r < WB; ++r) {
+            if (write_keys) kdst[dst[r]] = k[r];
+            if (HAS_V) vdst[dst[r]] = ov[(r0 + r) * BLOCK + tid];
+          }
+        }
+      } else {
+        for (int i = tid; i < tile_n; i += BLOCK) {
+          const U k = ok[i];
+          const long long dst = (long long)s_delta[s_dig[i]] + i;
+          if (write_keys) kdst[dst] = k;
+          if (HAS_V) vdst[dst] = ov[i];
+        }
       }
-    } else {
-      for (int i = tid; i < tile_n; i += BLOCK) {
-        const U k = ok[i];
-        const uint32_t d = DIGIT == DIGIT_LEARNED ? uint32_t(s_dig[i]) : digit_of(radix_key_t<KIND>(k, a.flip), shift);
-        if (write_keys) reinterpret_cast<U *>(s_kptr[d])[i] = k;
-        if (HAS_V) reinterpret_cast<V *>(s_vptr[d])[i] = ov[i];
-      }
-    }
+    };
+    if (tile_n == TILE) body(std::true_type{});
+    else body(std::false_type{});
 
     if (!PERSIST) break;  // one tile per CTA
-
-    // ---- make the next stage resident, then recycle this one
-    if (tid == 0) {
-      const int sn = (it + 1) % STAGES;
-      const int64_t tn = s_tile[sn];
-      if (tn < a.num_tiles && is_bulk(tn)) {
-        if (!mbar_wait_bounded(&bar[sn], (phase_bits >> sn) & 1u, a.timeout_ns)) {
-          set_error(a.hdr, AK_ERR_TIMEOUT);
-          *s_flag = 1;
-        }
-        phase_bits ^= 1u << sn;
-      }
-    }
-    __syncthreads();  // D: stage s is free, the next stage is resident
-    if (tid == 0 && !*s_flag) {
-      const int64_t t = next_tile();
-      s_tile[s] = uint32_t(t < a.num_tiles ? t : a.num_tiles);
-      issue(s, t);
-    }
-    // s_tile[s] is next read STAGES-1 iterations later, after barriers
   }
   // a copy left in flight by a timed-out wait must land before the CTA exits
-  if (tid == 0 && *s_flag) {
-    for (int s = 0; s < STAGES; ++s) mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u, a.timeout_ns);
-  }
+  if (tid == 0 && pending) mbar_wait_bounded(bar, phase, a.timeout_ns);
 }
 
 // --------------------------------------------------------------------- finish

@@ -3,36 +3,44 @@
 #pragma once
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "internal.h"
 #include "onesweep.cuh"
 
 namespace ak {
 
-// Resident CTAs per SM of a kernel (cached per device).
+// Resident CTAs per SM of a kernel launch shape (cached per kernel and device).
 template <typename K>
 int resident_ctas(K kern, int block, size_t smem) {
-  static int cache[64] = {0};
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> cache;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  const auto key = std::make_pair(reinterpret_cast<const void *>(kern), dev);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, block, smem) != cudaSuccess || nb < 1) nb = 1;
-  if (dev >= 0 && dev < 64) cache[dev] = nb;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = nb;
   return nb;
 }
 
 template <typename U, typename V, bool HAS_V, int KIND, typename S, int CFG>
 cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
   constexpr int BLOCK = CFG_BLOCK[CFG];
-  constexpr int STAGES = CFG_STAGES[CFG];
   constexpr int ITEMS = tile_items(sizeof(U), HAS_V ? sizeof(V) : 0, CFG);
-  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS, STAGES>;
+  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
   static_assert(L::TILE == tile_keys(sizeof(U), HAS_V ? sizeof(V) : 0, CFG), "tile shape");
   constexpr bool PERSIST = CFG_PERSIST[CFG];
-  static_assert(PERSIST || STAGES == 1, "one tile per CTA needs one stage");
-  auto kern = onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, STAGES, PERSIST>;
+  auto kern = onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, PERSIST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::BYTES));
   if (e != cudaSuccess) return e;
   const int64_t tiles = (c.n + L::TILE - 1) / L::TILE;
@@ -52,7 +60,7 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
   const int64_t wave = int64_t(resident_ctas(kern, BLOCK, L::BYTES)) * sms;
   const int64_t resident = PERSIST ? wave : tiles;
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, resident)));
-  a.prefetch_ahead = (c.debug_flags & AK_DEBUG_NO_PREFETCH) ? 0 : wave;
+  a.prefetch_ahead = (PERSIST || (c.debug_flags & AK_DEBUG_NO_PREFETCH)) ? 0 : wave;
   for (int p = 0; p < PASSES; ++p) {
     a.pass = p;
     a.status_cur = c.status[p & 1];
