@@ -58,8 +58,8 @@ cudaError_t radix_launch_u64_float(const RadixCall &c);
 // thread clamped to [2, 12]).  Persistent configurations launch one wave of
 // CTAs that loop over tiles, each copying its next tile in while it finishes
 // the current one; the other launches one CTA per tile.
-constexpr int CFG_BLOCK[3] = {512, 512, 512};
-constexpr int CFG_BYTES[3] = {32768, 16384, 32768};
+constexpr int CFG_BLOCK[3] = {512, 384, 512};
+constexpr int CFG_BYTES[3] = {32768, 24576, 32768};
 constexpr bool CFG_PERSIST[3] = {true, true, false};
 
 constexpr int tile_items(int key_bytes, int val_bytes, int cfg) {

@@ -208,7 +208,10 @@ struct PassSmem {
                 "shared-memory arrays aligned to their element size (bulk copies: 16 bytes)");
 };
 
-constexpr int LOOKBACK_WINDOW = 8;  // predecessor words probed per round trip
+#ifndef AK_LOOKBACK_WINDOW
+#define AK_LOOKBACK_WINDOW 8
+#endif
+constexpr int LOOKBACK_WINDOW = AK_LOOKBACK_WINDOW;  // predecessor words probed per round trip
 
 // One digit pass.  Tile ids come from an atomic counter, so every predecessor
 // of a tile is held by a CTA that already runs (forward progress of the
@@ -226,9 +229,12 @@ constexpr int LOOKBACK_WINDOW = 8;  // predecessor words probed per round trip
 // gives digit starts and warp bases; (3) scatter into the output buffer in
 // digit order; (4) decoupled look-back, inclusive counts published (flag INC);
 // (5) write-out: consecutive threads store consecutive slots of a digit run.
+// CTAs per SM the register budget is sized for (2 x 512, 3 x 384 threads).
+constexpr int pass_min_blocks(int block) { return block >= 512 ? 2 : (block >= 384 ? 3 : 4); }
+
 template <typename U, typename V, bool HAS_V, int KIND, typename S, int BLOCK, int ITEMS, bool PERSIST,
           int DIGIT = DIGIT_RADIX>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U, V> a) {
+__global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(PassArgs<U, V> a) {
   using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
   constexpr int TILE = L::TILE;
   constexpr int NW = L::NW;
@@ -435,11 +441,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
         }
       }
 
-      if (PERSIST && tid == CLAIMER) {
-        *s_next = (long long)next_tile;
-        prefetch_l2(next_tile);
-      }
-
       // ---- decoupled look-back over a window of predecessors per probe
       if (tid < RADIX) {
         unsigned long long excl = 0;
@@ -485,6 +486,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) onesweep_pass(PassArgs<U,
         }
         s_delta[tid] = Delta((long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start);
       }
+      if (PERSIST && tid == CLAIMER) {
+        *s_next = (long long)next_tile;
+        prefetch_l2(next_tile);
+      }
+
       __syncthreads();  // C: output buffer and destinations ready; the stage buffer is free
       if (PERSIST) {
         if (tid == 0) issue(*s_next);  // lands while this tile is written out

@@ -4,10 +4,15 @@
 // classify_kernel  builds the work order: segments above the shared-memory
 //                  capacity first (they take longest), then the rest
 // segsort_kernel   persistent CTAs pop segments from a device work counter.
-//   * L <= CAP: the segment is loaded into shared memory; the radix bits that
-//     vary inside it are found (OR of r ^ r0); LSD passes over only those bits
-//     run between two shared buffers, chunk by chunk with stable warp ranks and
-//     running digit offsets; the result is written back once.
+//   * L <= CAP: the segment is loaded into shared memory and its radix-key
+//     range [rmin, rmax] found.  One counting pass spreads the keys over up to
+//     2^SUB_BITS sub-ranges of equal width ((r - rmin) >> sh, monotone in r);
+//     each sub-range (a handful of keys when the keys are spread smoothly) is
+//     insertion-sorted on (radix key, input position), which keeps the sort
+//     stable; the result is gathered out once.  When a sub-range holds more
+//     than SUB_MAX keys (clustered keys), the segment instead takes LSD passes
+//     over only the radix bits that vary inside it (OR of r ^ r0), between two
+//     shared buffers, chunk by chunk with stable warp ranks.
 //   * L > CAP: one stable MSD pass through global memory on the top varying
 //     bits (just enough that buckets average CAP/2 keys; workspace copy of the
 //     segment), then each bucket is sorted in shared memory like a small
@@ -20,6 +25,9 @@
 #include "common.cuh"
 
 namespace ak {
+
+constexpr int SUB_BITS = 11;  // at most 2^SUB_BITS sub-ranges per segment
+constexpr int SUB_MAX = 48;   // largest sub-range the insertion sort takes
 
 struct SegArgsBase {
   const int64_t *off;     // nseg + 1 offsets (clamped to [0, n] on read); NULL: one segment [0, n)
@@ -92,12 +100,14 @@ struct SegSmem {
   static constexpr size_t OFF_BST = OFF_CCNT + RADIX * 4;                           // u32[RADIX] bucket starts
   static constexpr size_t OFF_BCNT = OFF_BST + RADIX * 4;                           // u32[RADIX] bucket counts
   static constexpr size_t OFF_SCR = OFF_BCNT + RADIX * 4;                           // u64[NW+1]
-  static constexpr size_t OFF_MISC = OFF_SCR + (NW + 1) * 8;                        // u32[8]
-  static constexpr size_t BYTES = OFF_MISC + 32;
+  static constexpr size_t OFF_MISC = OFF_SCR + (NW + 1) * 8;                        // u32[8 + NW]
+  static constexpr size_t BYTES = OFF_MISC + (8 + NW) * 4;
   static_assert(CH <= CAP, "a chunk fits in a segment buffer");
   static_assert(VOFF % 16 == 0 && BUF % 128 == 0 && OFF_MASK % 16 == 0 && OFF_SCR % 8 == 0,
                 "shared-memory arrays aligned to their element size");
-  static_assert(CAP < 65536, "16-bit warp bases");
+  static_assert(CAP < 65536, "16-bit warp bases and input positions");
+  static_assert(size_t(NW) * HROW * 4 >= (size_t(1) << SUB_BITS) * 4, "sub-range counters fit in the mask words");
+  static_assert(BUF >= size_t(CAP) * 2, "input positions fit in buffer B");
 };
 
 // One CTA sorts segments.  Generic pointers address shared or global buffers.
@@ -296,22 +306,149 @@ struct SegCta {
     return which;
   }
 
+  // Range of the radix keys of a shared buffer: min, max and OR of (r ^ r[0]).
+  __device__ void key_range(const U *src, int len, U &mn, U &mx, unsigned long long &vary) {
+    const U r0 = rk(src[0]);
+    U lo = r0, hi = r0;
+    unsigned long long v = 0;
+    for (int i = tid; i < len; i += BLOCK) {
+      const U r = rk(src[i]);
+      lo = r < lo ? r : lo;
+      hi = r > hi ? r : hi;
+      v |= (unsigned long long)(U(r ^ r0));
+    }
+    unsigned long long l64 = lo, h64 = hi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, l64, o);
+      const unsigned long long hi2 = __shfl_xor_sync(0xffffffffu, h64, o);
+      v |= __shfl_xor_sync(0xffffffffu, v, o);
+      l64 = lo2 < l64 ? lo2 : l64;
+      h64 = hi2 > h64 ? hi2 : h64;
+    }
+    unsigned long long *scr = reinterpret_cast<unsigned long long *>(s_cnt);  // 3 x NW words
+    if (lane == 0) {
+      scr[warp] = l64;
+      scr[NW + warp] = h64;
+      scr[2 * NW + warp] = v;
+    }
+    __syncthreads();
+    l64 = scr[0];
+    h64 = scr[NW];
+    v = scr[2 * NW];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) {
+      l64 = scr[w] < l64 ? scr[w] : l64;
+      h64 = scr[NW + w] > h64 ? scr[NW + w] : h64;
+      v |= scr[2 * NW + w];
+    }
+    __syncthreads();
+    mn = U(l64);
+    mx = U(h64);
+    vary = v;
+  }
+
+  // Exclusive scan of cnt[0, m) in place; returns the largest count.
+  __device__ uint32_t scan_counts(uint32_t *cnt, int m) {
+    const int per = (m + BLOCK - 1) / BLOCK;
+    const int b0 = tid * per, b1 = (b0 + per) < m ? (b0 + per) : m;
+    uint32_t sum = 0, big = 0;
+    for (int i = b0; i < b1; ++i) {
+      const uint32_t c = cnt[i];
+      sum += c;
+      big = c > big ? c : big;
+    }
+    unsigned long long total;
+    uint32_t run = uint32_t(block_exclusive_scan<BLOCK>((unsigned long long)sum, s_scr, &total));
+    for (int i = b0; i < b1; ++i) {
+      const uint32_t c = cnt[i];
+      cnt[i] = run;
+      run += c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t b2 = __shfl_xor_sync(0xffffffffu, big, o);
+      big = b2 > big ? b2 : big;
+    }
+    uint32_t *wbig = s_misc + 8;  // one word per warp
+    if (lane == 0) wbig[warp] = big;
+    __syncthreads();
+    big = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) big = wbig[w] > big ? wbig[w] : big;
+    __syncthreads();
+    return big;
+  }
+
   // Sort gk/gv[0, len) (global) into dk/dv (global, may alias gk/gv), len <= CAP.
   __device__ void sort_small(const U *gk, const V *gv, U *dk, V *dv, int len) {
-    copy(buf_k(0), buf_v(0), gk, gv, len);
+    U *ak = buf_k(0);
+    V *av = buf_v(0);
+    copy(ak, av, gk, gv, len);
     __syncthreads();
-    const unsigned long long vary = vary_bits(buf_k(0), len);
+    U mn, mx;
+    unsigned long long vary;
+    key_range(ak, len, mn, mx, vary);
     if (vary == 0) {  // every key equivalent: stable order is the input order
       if (dk != gk) {
-        copy(dk, dv, buf_k(0), buf_v(0), len);
+        copy(dk, dv, ak, av, len);
         __syncthreads();
       }
       return;
     }
-    const int lo = __ffsll((long long)vary) - 1;
-    const int hi = 63 - __clzll((long long)vary);
-    const int res = lsd_smem(0, len, lo, hi);
-    copy(dk, dv, buf_k(res), buf_v(res), len);
+    // sub-ranges of width 2^sh over [mn, mx]: about two keys each when spread evenly
+    const unsigned long long span = (unsigned long long)(U(mx - mn));
+    const int span_bits = 64 - __clzll((long long)span);
+    int want = (32 - __clz(uint32_t(len - 1))) - 1;
+    want = want < 1 ? 1 : (want > SUB_BITS ? SUB_BITS : want);
+    const int sh = span_bits > want ? span_bits - want : 0;
+    const int nsub = int(span >> sh) + 1;
+    uint32_t *sub = wmask;  // mask words are zero outside a ranking step
+    for (int i = tid; i < len; i += BLOCK) atomicAdd(&sub[(unsigned long long)(U(rk(ak[i]) - mn)) >> sh], 1u);
+    __syncthreads();
+    const uint32_t biggest = scan_counts(sub, nsub);
+    if (biggest > uint32_t(SUB_MAX)) {  // clustered keys: LSD over the varying bits
+      for (int i = tid; i < nsub; i += BLOCK) sub[i] = 0u;
+      __syncthreads();
+      const int lo = __ffsll((long long)vary) - 1;
+      const int hi = 63 - __clzll((long long)vary);
+      const int res = lsd_smem(0, len, lo, hi);
+      copy(dk, dv, buf_k(res), buf_v(res), len);
+      __syncthreads();
+      return;
+    }
+    // input positions by sub-range (any order inside a sub-range) ...
+    uint16_t *pos = reinterpret_cast<uint16_t *>(buf_k(1));
+    for (int i = tid; i < len; i += BLOCK) {
+      const uint32_t slot = atomicAdd(&sub[(unsigned long long)(U(rk(ak[i]) - mn)) >> sh], 1u);
+      pos[slot] = uint16_t(i);
+    }
+    __syncthreads();
+    // ... then each sub-range in (radix key, input position) order; sub[s] now
+    // holds the end of sub-range s
+    for (int s_ = tid; s_ < nsub; s_ += BLOCK) {
+      const int b = s_ ? int(sub[s_ - 1]) : 0, e = int(sub[s_]);
+      for (int p = b + 1; p < e; ++p) {
+        const uint16_t x = pos[p];
+        const U rx = rk(ak[x]);
+        int q = p - 1;
+        while (q >= b) {
+          const uint16_t y = pos[q];
+          const U ry = rk(ak[y]);
+          if (ry < rx || (ry == rx && y < x)) break;
+          pos[q + 1] = y;
+          --q;
+        }
+        pos[q + 1] = x;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < nsub; i += BLOCK) sub[i] = 0u;
+    for (int j = tid; j < len; j += BLOCK) {
+      const int x = pos[j];
+      dk[j] = ak[x];
+      if (HAS_V) dv[j] = av[x];
+    }
     __syncthreads();
   }
 
