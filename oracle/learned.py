@@ -4,8 +4,10 @@ The paper's distributed sort (Sec. IV-A, SIHSort) draws a key sample, builds
 "interpolated histograms" of it and turns them into splitters.  The learned path
 replaces the splitters by a tiny model of the key CDF trained on that sample:
 
-  x-hat   min-max normalised order-preserving integer image of a key (the
-          "radix key"; see ``radix_key``), lo/hi = sample minimum/maximum
+  x-hat   min-max normalised coordinate of a key, lo/hi = sample minimum/
+          maximum: the order-preserving integer image of an integer key (the
+          "radix key"; see ``radix_key``), the value of a float key (negated for
+          a descending sort; NaN clamps to the end)
   PL(x)   64-knot piecewise-linear CDF through (xi_j, j/63), xi_j the sorted
           sample's order statistic of rank round(j (m-1) / 63): the splitters
           of the sample sort, interpolated; 0 below xi_0, 1 from xi_63 on

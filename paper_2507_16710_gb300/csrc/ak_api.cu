@@ -230,7 +230,7 @@ static ak_status run_seg(int op, void *keys, const int64_t *off, int64_t nseg, i
 // ------------------------------------------------------------ learned path
 struct LearnedLayout {
   RadixLayout rad;  // the pairs/keys radix layout (fallback + bucket passes)
-  size_t model, sample_r, xs, xs_alt, s_hdr, s_counts, s_plan, s_status0, s_status1, partials, bcounts, seg_off,
+  size_t model, sample_r, sample_alt, xs, xs_v, s_hdr, s_counts, s_plan, s_status0, s_status1, partials, bcounts, seg_off,
       seg_order, seg_counters, kcopy, total;
   uint32_t m, bbits;
 };
@@ -267,12 +267,13 @@ static LearnedLayout learned_layout(int op, int64_t n, int key_bytes, int val_by
   };
   L.model = take(sizeof(LearnedModel));
   L.sample_r = take(size_t(m) * 8);
+  L.sample_alt = take(size_t(m) * 8);
   L.xs = take(size_t(m) * 4);
-  L.xs_alt = take(size_t(m) * 4);
+  L.xs_v = take(size_t(m) * 4);
   L.s_hdr = take(sizeof(DevHeader));
   L.s_counts = take(sizeof(unsigned long long) * MAX_PASSES * RADIX);
   L.s_plan = take(sizeof(RadixPlan));
-  const int64_t stiles = (m + min_tile_keys(4, 0) - 1) / min_tile_keys(4, 0);
+  const int64_t stiles = (m + min_tile_keys(8, 0) - 1) / min_tile_keys(8, 0);
   L.s_status0 = take(size_t(stiles) * RADIX * 4);
   L.s_status1 = take(size_t(stiles) * RADIX * 4);
   L.partials = take(learned_partials_bytes());
@@ -354,12 +355,13 @@ static ak_status run_learned(int op, void *keys, const void *k_in, void *vals, i
   lc.m = L.m;
   lc.seed = o.seed ? o.seed : 0x2507u;
   lc.sample_r = reinterpret_cast<unsigned long long *>(t + L.sample_r);
-  lc.xs = reinterpret_cast<uint32_t *>(t + L.xs);
+  lc.xs = reinterpret_cast<float *>(t + L.xs);
+  lc.xs_v = reinterpret_cast<float *>(t + L.xs_v);
   RadixCall &sc = lc.sample_sort;
   sc.mode = MODE_INPLACE;
-  sc.k_in = lc.xs;
-  sc.k_final = lc.xs;
-  sc.k_alt0 = t + L.xs_alt;
+  sc.k_in = lc.sample_r;
+  sc.k_final = lc.sample_r;
+  sc.k_alt0 = t + L.sample_alt;
   sc.n = L.m;
   sc.kind = KIND_UINT;
   sc.hdr = reinterpret_cast<DevHeader *>(t + L.s_hdr);

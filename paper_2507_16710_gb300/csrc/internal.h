@@ -95,8 +95,8 @@ struct LearnedCall {
   LearnedModel *model;         // zeroed
   uint32_t m, seed;            // sample size, sample/initialisation seed
   unsigned long long *sample_r;
-  uint32_t *xs;                // m x-hat values (fp32 bits), sorted in place
-  RadixCall sample_sort;       // radix sort of xs (u32 keys)
+  float *xs, *xs_v;            // x-hat of the sorted sample: radix / value coordinate
+  RadixCall sample_sort;       // radix sort of sample_r (u64 keys) in place
   float *partials;             // training partial sums
   int train_steps;             // 0: piecewise-linear CDF only
   float lr;

@@ -6,21 +6,76 @@
 
 namespace ak {
 
-__global__ void lm_xhat_kernel(const unsigned long long *sample_r, uint32_t m, LearnedModel *md, uint32_t *xs,
-                               const uint32_t *gate) {
+__global__ void lm_xhat_kernel(const unsigned long long *sample_r, uint32_t m, LearnedModel *md, float *xs,
+                               float *xs_v, int vbytes, unsigned long long flip, const uint32_t *gate) {
   if (gate && *gate) return;
   const unsigned long long lo = ~md->neg_lo, hi = md->hi;
   const bool any = md->hi != 0 || md->neg_lo != 0;
   const unsigned long long l = (any && lo <= hi) ? lo : 0ull, h = (any && lo <= hi) ? hi : 0ull;
   const float inv = (h > l) ? 1.0f / __ull2float_rn(h - l) : 0.0f;
+  auto value = [&](unsigned long long r) {
+    return vbytes == 8 ? lm_value_f32<uint64_t>(uint64_t(r), uint64_t(flip))
+                       : lm_value_f32<uint32_t>(uint32_t(r), uint32_t(flip));
+  };
+  // value coordinate: range of the finite sample keys
+  float lo_f = 0.f, inv_f = 0.f;
+  if (vbytes && h > l) {
+    lo_f = value(l);
+    const float span = __fsub_rn(value(h), lo_f);
+    inv_f = (span > 0.f && span <= FLT_MAX) ? __fdiv_rn(1.f, span) : 0.f;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     md->neg_lo = ~l;
     md->hi = h;
     md->inv = inv;
+    md->lo_f = lo_f;
+    md->inv_f = inv_f;
     md->m = m;
   }
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
-    xs[j] = __float_as_uint(lm_xhat(sample_r[j], l, h, inv));
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    xs[j] = lm_xhat(sample_r[j], l, h, inv);
+    if (vbytes) xs_v[j] = lm_xhat_value(value(sample_r[j]), lo_f, inv_f);
+  }
+}
+
+__global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t m, LearnedModel *md,
+                                    const uint32_t *gate) {
+  if (gate && *gate) return;
+  __shared__ float c[2][LM_KNOTS];
+  __shared__ uint32_t s_err[2];
+  if (threadIdx.x < LM_KNOTS) {
+    c[0][threadIdx.x] = md->c[threadIdx.x];
+    c[1][threadIdx.x] = md->c_v[threadIdx.x];
+  }
+  if (threadIdx.x < 2) s_err[threadIdx.x] = 0u;
+  __syncthreads();
+  // overload of a window of k consecutive sample keys: the share of keys it
+  // holds over the share of buckets the model gives it
+  const uint32_t k = m >= 2 * LM_FIT_WINDOW ? uint32_t(LM_FIT_WINDOW) : (m > 1 ? m / 2 : 1u);
+  const float share = float(k) / float(m);
+  auto overload = [&](const float *cc, const float *x, uint32_t i) {
+    const float d = lm_pl(cc, x[i + k]) - lm_pl(cc, x[i]);
+    return d > 0.f ? share / d : FLT_MAX;
+  };
+  float e0 = 0.f, e1 = 0.f;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i + k < m; i += gridDim.x * blockDim.x) {
+    e0 = fmaxf(e0, overload(c[0], xs, i));
+    if (xs_v) e1 = fmaxf(e1, overload(c[1], xs_v, i));
+  }
+  atomicMax(&s_err[0], __float_as_uint(e0));  // non-negative floats order like their bits
+  atomicMax(&s_err[1], __float_as_uint(e1));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&md->err_bits[0], s_err[0]);
+    atomicMax(&md->err_bits[1], s_err[1]);
+  }
+}
+
+__global__ void lm_choose_kernel(LearnedModel *md, int has_value, const uint32_t *gate) {
+  if (gate && *gate) return;
+  const bool value = has_value && md->err_bits[1] < md->err_bits[0];
+  if (threadIdx.x == 0) md->coord = value ? 1u : 0u;
+  if (value && threadIdx.x < LM_KNOTS) md->c[threadIdx.x] = md->c_v[threadIdx.x];
 }
 
 __global__ void lm_knots_kernel(const float *xs, int64_t m, float *knots, LearnedModel *md, const uint32_t *gate) {
@@ -111,8 +166,9 @@ __device__ __forceinline__ float lm_init_param(uint32_t seed, int q) {
   return 0.0f;
 }
 
-__global__ void __launch_bounds__(LM_TRAIN_BLOCK) lm_train_kernel(const float *xs, uint32_t m, LearnedModel *md,
-                                                                  float *partials, int steps, float lr,
+__global__ void __launch_bounds__(LM_TRAIN_BLOCK) lm_train_kernel(const float *xs, const float *xs_v, uint32_t m,
+                                                                  LearnedModel *md, float *partials, int steps,
+                                                                  float lr,
                                                                   uint32_t init_seed, DevHeader *hdr,
                                                                   uint64_t timeout_ns, const uint32_t *gate) {
   if (gate && *gate) return;
@@ -137,7 +193,7 @@ __global__ void __launch_bounds__(LM_TRAIN_BLOCK) lm_train_kernel(const float *x
   float x = 0.f, y = 0.f;
   if (valid) {
     const int64_t idx = int64_t((double(gi) + 0.5) * double(m) / double(teff));
-    x = xs[idx];
+    x = (md->coord && xs_v) ? xs_v[idx] : xs[idx];  // the coordinate chosen on the sample
     y = (float(idx) + 0.5f) / float(m);
   }
   const float scale = teff > 0 ? 2.0f / float(teff) : 0.f;

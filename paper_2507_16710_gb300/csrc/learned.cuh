@@ -3,8 +3,16 @@
 // The splitter step of the paper's sample sort (Sec. IV-A) draws a key sample
 // and turns interpolated histograms of it into splitters.  Here the sample trains
 // a small monotone model of the key CDF, F = PL + r:
-//   x-hat = min-max normalised radix key (the order-preserving integer image of
-//           the key, common.cuh), computed in fp32 from the sample's range
+//   x-hat = min-max normalised coordinate of the key over the sample's range:
+//           the radix key (the order-preserving integer image of common.cuh),
+//           or, for float keys, a float32 image of the value (negated for a
+//           descending sort; NaN after every number) -- whichever of the two
+//           overloads buckets less on the sample under the piecewise-linear fit
+//           below (largest ratio, over windows of LM_FIT_WINDOW consecutive
+//           sample keys, of the keys' share to the share of the CDF the fit
+//           gives them)
+//           (in radix-key space float keys are roughly logarithmic: heavy tails
+//           stay smooth, mass near zero does not; in value space the reverse)
 //   PL    = 64-knot piecewise-linear CDF through (xi_j, j/63), xi_j the sample
 //           order statistic of rank round(j (m-1) / 63): the sample sort's
 //           splitters, interpolated
@@ -18,6 +26,8 @@
 // the stable sort, whatever the model learned; the model only decides speed.
 #pragma once
 
+#include <float.h>
+
 #include "common.cuh"
 
 namespace ak {
@@ -30,6 +40,7 @@ constexpr int LM_TABLE = 4096;   // table cells M
 constexpr int LM_TRAIN = 8192;   // training points T
 constexpr int LM_MAX_SAMPLE = 1 << 20;
 constexpr int LM_TRAIN_BLOCK = 256;
+constexpr int LM_FIT_WINDOW = 64;  // sample keys per window of the coordinate choice
 constexpr int LM_TRAIN_CTAS = LM_TRAIN / LM_TRAIN_BLOCK;  // one point per thread
 // r = LM_OUT_SCALE * (b3 + w3 . h2): keeps the residual's steps at the scale of
 // the piecewise-linear fit's error while the optimiser takes unit-scale steps
@@ -44,7 +55,11 @@ struct LearnedModel {
   uint32_t use_plain;         // 1: fall back to the plain radix path
   uint32_t barrier;           // training grid barrier arrivals
   float loss_before, loss_after;
-  uint32_t pad[5];
+  uint32_t coord;             // 1: float keys use the value coordinate
+  uint32_t err_bits[2];       // largest PL window overload on the sample (fp32 bits): radix, value coordinate
+  float lo_f, inv_f;          // value coordinate: sample minimum, 1 / sample range
+  uint32_t pad[1];
+  float c_v[LM_KNOTS];        // knots of the value coordinate
   float c[LM_KNOTS];          // PL knots xi_j (x-hat of sample order statistics)
   float params[LM_PARAMS];
   float2 tk[LM_TABLE + 1];    // (T[k], bits of K[k])
@@ -124,10 +139,52 @@ __device__ __forceinline__ uint32_t lm_bucket(const float2 *tk, float x, uint32_
   return q < nb - 1 ? q : nb - 1;
 }
 
+// Value coordinate of a float key from its radix key r (of a sort whose flip is
+// `flip`): a float32 image of the value, negated for a descending sort, NaN
+// after every number.  A float64 value is narrowed with integer operations
+// (exponent rebiased, mantissa truncated, underflow to zero, overflow to the
+// largest float), so the image is non-decreasing in r and needs no FP64 unit.
+template <typename U>
+__device__ __forceinline__ float lm_value_f32(U r, U flip) {
+  constexpr U SIGN = U(U(1) << (8 * sizeof(U) - 1));
+  const U ra = U(r ^ flip);  // ascending radix key
+  const bool desc = flip != U(0);
+  if (ra == U(~U(0))) return desc ? -FLT_MAX : FLT_MAX;  // NaN
+  const U bits = (ra & SIGN) ? U(ra ^ SIGN) : U(~ra);     // the key's own bits
+  uint32_t f;
+  if constexpr (sizeof(U) == 8) {
+    const uint32_t sgn = uint32_t(uint64_t(bits) >> 63);
+    const int e = int((uint64_t(bits) >> 52) & 0x7FFu) - 1023 + 127;
+    uint32_t mag;
+    if (e <= 0) mag = 0u;                 // below the float range (and zero): 0
+    else if (e >= 255) mag = 0x7F7FFFFFu;  // above it (and infinity): FLT_MAX
+    else mag = (uint32_t(e) << 23) | uint32_t((uint64_t(bits) >> 29) & 0x7FFFFFu);
+    f = (sgn << 31) | mag;
+  } else {
+    f = uint32_t(bits);
+  }
+  const float v = __uint_as_float(f);
+  return desc ? -v : v;
+}
+
+// x-hat of a value coordinate: monotone non-decreasing in v.
+__device__ __forceinline__ float lm_xhat_value(float v, float lo, float inv) {
+  const float x = __fmul_rn(__fsub_rn(v, lo), inv);
+  return x > 0.f ? (x < 1.f ? x : 1.f) : 0.f;  // NaN (inf * 0) -> 0
+}
+
+// x-hat of a key from its radix key r.
+template <int KIND, typename U>
+__device__ __forceinline__ float lm_key_xhat(const LearnedModel *md, U r, U flip) {
+  if constexpr (KIND == KIND_FLOAT && sizeof(U) >= 4) {
+    if (md->coord) return lm_xhat_value(lm_value_f32(r, flip), md->lo_f, md->inv_f);
+  }
+  return lm_xhat(r, ~md->neg_lo, md->hi, md->inv);
+}
+
 template <int KIND, typename U>
 __device__ __forceinline__ uint32_t lm_key_bucket(const LearnedModel *md, U key, U flip) {
-  const U r = radix_key_t<KIND>(key, flip);
-  return lm_bucket(md->tk, lm_xhat(r, ~md->neg_lo, md->hi, md->inv), md->nbuckets);
+  return lm_bucket(md->tk, lm_key_xhat<KIND>(md, radix_key_t<KIND>(key, flip), flip), md->nbuckets);
 }
 
 // splitmix64 finaliser on a counter: the sample index stream.
@@ -163,12 +220,12 @@ __global__ void lm_sample_kernel(const U *keys, int64_t n, U flip, uint32_t m, u
     const U k = keys[int64_t(h % (unsigned long long)n)];
     const U r = radix_key_t<KIND>(k, flip);
     sample_r[j] = (unsigned long long)r;
-    bool nan = false;
+    bool nonfinite = false;  // NaN and infinities stay out of the range (x-hat clamps them)
     if (KIND == KIND_FLOAT) {
       constexpr U SIGN = U(U(1) << (8 * sizeof(U) - 1));
-      nan = U(k & U(~SIGN)) > FloatBits<U>::EXP;
+      nonfinite = U(k & U(~SIGN)) >= FloatBits<U>::EXP;
     }
-    if (!nan) {
+    if (!nonfinite) {
       lo_n = max(lo_n, ~(unsigned long long)r);
       hi = max(hi, (unsigned long long)r);
     }
@@ -196,15 +253,28 @@ __global__ void lm_sample_kernel(const U *keys, int64_t n, U flip, uint32_t m, u
   }
 }
 
-// x-hat of every sample key as fp32 bits (sortable as u32 since x-hat >= 0).
-__global__ void lm_xhat_kernel(const unsigned long long *sample_r, uint32_t m, LearnedModel *md, uint32_t *xs,
-                               const uint32_t *gate);
+// x-hat of every key of the sorted sample in the radix coordinate (xs) and,
+// for float keys of `vbytes` (4 or 8; 0: integer keys), the value coordinate
+// (xs_v); flip: the sort's flip (all ones when descending).
+__global__ void lm_xhat_kernel(const unsigned long long *sample_r, uint32_t m, LearnedModel *md, float *xs,
+                               float *xs_v, int vbytes, unsigned long long flip, const uint32_t *gate);
+
+// Largest bucket overload of the PL fit over windows of LM_FIT_WINDOW
+// consecutive keys of the sorted sample, per coordinate, max-reduced into
+// md->err_bits.
+__global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t m, LearnedModel *md,
+                                    const uint32_t *gate);
+
+// Picks the coordinate with the smaller overload (float keys) and makes its
+// knots the model's.
+__global__ void lm_choose_kernel(LearnedModel *md, int has_value, const uint32_t *gate);
 
 // Knots xi_j = xs[round(j (m-1) / 63)] of an ascending sample.
 __global__ void lm_knots_kernel(const float *xs, int64_t m, float *knots, LearnedModel *md, const uint32_t *gate);
 
 // Training: LM_TRAIN_CTAS co-resident CTAs, one training point per thread.
-__global__ void lm_train_kernel(const float *xs, uint32_t m, LearnedModel *md, float *partials, int steps,
+__global__ void lm_train_kernel(const float *xs, const float *xs_v, uint32_t m, LearnedModel *md, float *partials,
+                                int steps,
                                 float lr, uint32_t init_seed, DevHeader *hdr, uint64_t timeout_ns,
                                 const uint32_t *gate);
 

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstddef>
 
 #include "internal.h"
 #include "learned.cuh"
@@ -151,18 +152,23 @@ cudaError_t learned_launch(const RadixCall &c, const LearnedCall &lc) {
   cudaError_t e;
   const U flip = c.descending ? U(~U(0)) : U(0);
   const int sms = device_sm_count();
-  // 1. sample and its range
-  {
-    const int g = int(std::min<int64_t>((lc.m + 255) / 256, int64_t(sms) * 4));
-    lm_sample_kernel<U, KIND><<<g, 256, 0, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, flip, lc.m,
-                                                       lc.seed, lc.sample_r, lc.model, nullptr);
-    lm_xhat_kernel<<<g, 256, 0, c.stream>>>(lc.sample_r, lc.m, lc.model, lc.xs, nullptr);
+  // 1. sample (radix keys) and its range; 2. sort it by radix key
+  const int g = int(std::min<int64_t>((lc.m + 255) / 256, int64_t(sms) * 4));
+  lm_sample_kernel<U, KIND><<<g, 256, 0, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, flip, lc.m, lc.seed,
+                                                     lc.sample_r, lc.model, nullptr);
+  if ((e = radix_launch_u64_uint(lc.sample_sort)) != cudaSuccess) return e;
+  // 3. x-hat of the sorted sample in each coordinate, the knots of each, the
+  //    coordinate whose piecewise-linear fit is closer; residual MLP; table
+  constexpr int VBYTES = (KIND == KIND_FLOAT && sizeof(U) >= 4) ? int(sizeof(U)) : 0;
+  lm_xhat_kernel<<<g, 256, 0, c.stream>>>(lc.sample_r, lc.m, lc.model, lc.xs, VBYTES ? lc.xs_v : nullptr, VBYTES,
+                                          (unsigned long long)flip, nullptr);
+  lm_knots_kernel<<<1, LM_KNOTS, 0, c.stream>>>(lc.xs, lc.m, nullptr, lc.model, nullptr);
+  if (VBYTES) {
+    float *cv = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(lc.model) + offsetof(LearnedModel, c_v));
+    lm_knots_kernel<<<1, LM_KNOTS, 0, c.stream>>>(lc.xs_v, lc.m, cv, nullptr, nullptr);
+    lm_fit_error_kernel<<<g, 256, 0, c.stream>>>(lc.xs, lc.xs_v, lc.m, lc.model, nullptr);
+    lm_choose_kernel<<<1, LM_KNOTS, 0, c.stream>>>(lc.model, 1, nullptr);
   }
-  // 2. sort the sample (x-hat >= 0, so its fp32 bits sort as unsigned integers)
-  if ((e = radix_launch_u32_uint(lc.sample_sort)) != cudaSuccess) return e;
-  // 3. piecewise-linear CDF, residual MLP, monotone table
-  lm_knots_kernel<<<1, LM_KNOTS, 0, c.stream>>>(reinterpret_cast<const float *>(lc.xs), lc.m, nullptr, lc.model,
-                                                  nullptr);
   if (lc.train_steps > 0) {
     const int smem = int(sizeof(GradSmem));
     if ((e = cudaFuncSetAttribute(lm_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
@@ -177,8 +183,9 @@ cudaError_t learned_launch(const RadixCall &c, const LearnedCall &lc) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if ((e = cudaLaunchKernelEx(&cfg, lm_train_kernel, reinterpret_cast<const float *>(lc.xs), lc.m, lc.model,
-                                lc.partials, lc.train_steps, lc.lr, lc.seed ^ 0x5EEDu, c.hdr, c.timeout_ns,
+    if ((e = cudaLaunchKernelEx(&cfg, lm_train_kernel, static_cast<const float *>(lc.xs),
+                                static_cast<const float *>(VBYTES ? lc.xs_v : nullptr), lc.m, lc.model, lc.partials,
+                                lc.train_steps, lc.lr, lc.seed ^ 0x5EEDu, c.hdr, c.timeout_ns,
                                 static_cast<const uint32_t *>(nullptr))) != cudaSuccess)
       return e;
   }
