@@ -255,8 +255,9 @@ static LearnedLayout learned_layout(int op, int64_t n, int key_bytes, int val_by
   m = m > LM_MAX_SAMPLE ? LM_MAX_SAMPLE : m;
   m = m > n ? n : m;
   L.m = uint32_t(m);
-  // buckets: about 1024 keys each, 2^8 .. 2^16
-  int bb = (o.bucket_bits >= 8 && o.bucket_bits <= 16) ? o.bucket_bits : ceil_log2(uint64_t(n > 1024 ? n / 1024 : 1));
+  // buckets: about half the finish's shared-memory capacity each, 2^8 .. 2^16
+  const int64_t per = seg_cap(key_bytes, vb) / 2;
+  int bb = (o.bucket_bits >= 8 && o.bucket_bits <= 16) ? o.bucket_bits : ceil_log2(uint64_t((n + per - 1) / per));
   bb = bb < 8 ? 8 : (bb > 16 ? 16 : bb);
   L.bbits = uint32_t(bb);
   const size_t nb = size_t(1) << bb;

@@ -116,9 +116,9 @@ cudaError_t learned_launch_u64_sint(const RadixCall &c, const LearnedCall &lc);
 cudaError_t learned_launch_u64_float(const RadixCall &c, const LearnedCall &lc);
 size_t learned_model_bytes();
 size_t learned_partials_bytes();
-// Shared-memory capacity (elements) of one segment buffer: about 24 KB of
-// keys+values, a multiple of 32 elements.
-constexpr int seg_cap(int key_bytes, int val_bytes) { return (24576 / (key_bytes + val_bytes)) / 32 * 32; }
+// Keys of one segment the shared-memory sort takes (a multiple of 32): 80 KB
+// of keys, values and 16-bit positions, so two CTAs fit an SM.
+constexpr int seg_cap(int key_bytes, int val_bytes) { return (81920 / (key_bytes + val_bytes + 2)) / 32 * 32; }
 cudaError_t seg_launch_u16_uint(const SegCall &c);
 cudaError_t seg_launch_u16_sint(const SegCall &c);
 cudaError_t seg_launch_u32_uint(const SegCall &c);

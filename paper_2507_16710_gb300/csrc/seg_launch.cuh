@@ -9,7 +9,7 @@
 
 namespace ak {
 
-constexpr int SEG_BLOCK = 256;
+constexpr int SEG_BLOCK = 512;
 // keys ranked per thread and chunk: at most 8, and a chunk never exceeds CAP
 constexpr int seg_items(int key_bytes, int val_bytes) {
   return seg_cap(key_bytes, val_bytes) / SEG_BLOCK < 8 ? seg_cap(key_bytes, val_bytes) / SEG_BLOCK : 8;

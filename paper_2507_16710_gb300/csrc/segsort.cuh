@@ -9,10 +9,11 @@
 //     2^SUB_BITS sub-ranges of equal width ((r - rmin) >> sh, monotone in r);
 //     each sub-range (a handful of keys when the keys are spread smoothly) is
 //     insertion-sorted on (radix key, input position), which keeps the sort
-//     stable; the result is gathered out once.  When a sub-range holds more
-//     than SUB_MAX keys (clustered keys), the segment instead takes LSD passes
-//     over only the radix bits that vary inside it (OR of r ^ r0), between two
-//     shared buffers, chunk by chunk with stable warp ranks.
+//     stable; only 16-bit input positions move in shared memory and the result
+//     is gathered out once.  When a sub-range holds more than SUB_MAX keys
+//     (clustered keys), the segment instead takes stable LSD passes over only
+//     the radix bits that vary inside it (OR of r ^ r0), through a global
+//     workspace copy, chunk by chunk with warp ranks.
 //   * L > CAP: one stable MSD pass through global memory on the top varying
 //     bits (just enough that buckets average CAP/2 keys; workspace copy of the
 //     segment), then each bucket is sorted in shared memory like a small
@@ -26,7 +27,7 @@
 
 namespace ak {
 
-constexpr int SUB_BITS = 11;  // at most 2^SUB_BITS sub-ranges per segment
+constexpr int SUB_BITS = 12;  // at most 2^SUB_BITS sub-ranges per segment
 constexpr int SUB_MAX = 48;   // largest sub-range the insertion sort takes
 
 struct SegArgsBase {
@@ -86,12 +87,13 @@ struct SegSmem {
   static constexpr int NW = BLOCK / 32;
   static constexpr int CH = BLOCK * ITEMS;  // keys ranked per chunk
   static constexpr int HROW = RADIX + 2;
-  // a segment buffer: CAP keys, then (16-byte aligned) CAP values
+  // buffer A: CAP keys, then (16-byte aligned) CAP values; buffer B: CAP
+  // 16-bit input positions
   static constexpr size_t VOFF = (size_t(CAP) * sizeof(U) + 15) / 16 * 16;
   static constexpr size_t BUF = (VOFF + (HAS_V ? size_t(CAP) * sizeof(V) : 0) + 127) / 128 * 128;
   static constexpr size_t OFF_A = 0;
   static constexpr size_t OFF_B = BUF;
-  static constexpr size_t OFF_HIST = 2 * BUF;                                        // u16[NW][HROW]
+  static constexpr size_t OFF_HIST = BUF + (size_t(CAP) * 2 + 127) / 128 * 128;      // u16[NW][HROW]
   static constexpr size_t OFF_MASK = (OFF_HIST + size_t(NW) * HROW * 2 + 15) / 16 * 16;  // u32[NW][HROW]
   static constexpr size_t OFF_CNT = OFF_MASK + size_t(NW) * HROW * 4;               // u32[RADIX] digit hist
   static constexpr size_t OFF_RUN = OFF_CNT + RADIX * 4;                            // u32[RADIX] running offsets
@@ -107,7 +109,6 @@ struct SegSmem {
                 "shared-memory arrays aligned to their element size");
   static_assert(CAP < 65536, "16-bit warp bases and input positions");
   static_assert(size_t(NW) * HROW * 4 >= (size_t(1) << SUB_BITS) * 4, "sub-range counters fit in the mask words");
-  static_assert(BUF >= size_t(CAP) * 2, "input positions fit in buffer B");
 };
 
 // One CTA sorts segments.  Generic pointers address shared or global buffers.
@@ -231,31 +232,6 @@ struct SegCta {
     __syncthreads();
   }
 
-  // One stable LSD pass src -> dst (both shared memory), len <= CAP.
-  __device__ void pass_smem(const U *sk, const V *sv, U *dk, V *dv, int len, int shift) {
-    if (len > CH) digit_offsets(sk, len, shift);
-    for (int c0 = 0; c0 < len; c0 += CH) {
-      const int cn = (len - c0) < CH ? (len - c0) : CH;
-      uint32_t dr[ITEMS];
-      rank_chunk(sk + c0, cn, shift, dr);
-      const int wbase = warp * 32 * ITEMS;
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = dr[i] & 511u;
-        if (d < RADIX) {
-          const int idx = wbase + i * 32 + lane;
-          uint32_t pos = uint32_t(wh[d]) + (dr[i] >> 9);
-          if (len > CH) pos += s_run[d] - s_cst[d];
-          dk[pos] = sk[c0 + idx];
-          if (HAS_V) dv[pos] = sv[c0 + idx];
-        }
-      }
-      __syncthreads();
-      if (len > CH && tid < RADIX) s_run[tid] += s_ccnt[tid];
-      __syncthreads();
-    }
-  }
-
   // One stable pass src -> dst in global memory (len > CAP possible), chunks
   // staged through buffer A so that every warp stores digit runs.  If
   // `buckets`, s_bst/s_bcnt receive the digit starts/counts.
@@ -294,16 +270,6 @@ struct SegCta {
       if (tid < RADIX) s_run[tid] += s_ccnt[tid];
       __syncthreads();
     }
-  }
-
-  // Passes over the varying bits [lo, hi] of a range held in shared buffer
-  // `which`; returns the buffer holding the result.
-  __device__ int lsd_smem(int which, int len, int lo, int hi) {
-    for (int sh = lo; sh <= hi; sh += RADIX_BITS) {
-      pass_smem(buf_k(which), buf_v(which), buf_k(which ^ 1), buf_v(which ^ 1), len, sh);
-      which ^= 1;
-    }
-    return which;
   }
 
   // Range of the radix keys of a shared buffer: min, max and OR of (r ^ r[0]).
@@ -380,8 +346,9 @@ struct SegCta {
     return big;
   }
 
-  // Sort gk/gv[0, len) (global) into dk/dv (global, may alias gk/gv), len <= CAP.
-  __device__ void sort_small(const U *gk, const V *gv, U *dk, V *dv, int len) {
+  // Sort gk/gv[0, len) (global) into dk/dv (global, may alias gk/gv), len <= CAP;
+  // tk/tv: len elements of global scratch other than dk/dv (may alias gk/gv).
+  __device__ void sort_small(const U *gk, const V *gv, U *dk, V *dv, int len, U *tk, V *tv) {
     U *ak = buf_k(0);
     V *av = buf_v(0);
     copy(ak, av, gk, gv, len);
@@ -409,12 +376,11 @@ struct SegCta {
     const uint32_t biggest = scan_counts(sub, nsub);
     if (biggest > uint32_t(SUB_MAX)) {  // clustered keys: LSD over the varying bits
       for (int i = tid; i < nsub; i += BLOCK) sub[i] = 0u;
+      copy(tk, tv, ak, av, len);  // buffer A stages the chunks of the passes
       __syncthreads();
       const int lo = __ffsll((long long)vary) - 1;
       const int hi = 63 - __clzll((long long)vary);
-      const int res = lsd_smem(0, len, lo, hi);
-      copy(dk, dv, buf_k(res), buf_v(res), len);
-      __syncthreads();
+      lsd_global(tk, tv, dk, dv, len, lo, hi, dk, dv);
       return;
     }
     // input positions by sub-range (any order inside a sub-range) ...
@@ -493,7 +459,8 @@ struct SegCta {
       const int64_t bs = s_bst[b], bl = s_bcnt[b];
       if (bl == 0) continue;
       if (bl <= CAP) {
-        sort_small(ak + bs, HAS_V ? av + bs : nullptr, gk + bs, HAS_V ? gv + bs : nullptr, int(bl));
+        sort_small(ak + bs, HAS_V ? av + bs : nullptr, gk + bs, HAS_V ? gv + bs : nullptr, int(bl), ak + bs,
+                   HAS_V ? av + bs : nullptr);
       } else {
         // still too large: chunked LSD over the bits below the top digit
         const unsigned long long bv = vary_bits(ak + bs, bl);
@@ -534,7 +501,8 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
     if (len <= 1) continue;
     const int64_t g = a.seg_base + lo;
     if (len <= CAP) {
-      c.sort_small(a.keys + g, HAS_V ? a.vals + g : nullptr, a.keys + g, HAS_V ? a.vals + g : nullptr, int(len));
+      c.sort_small(a.keys + g, HAS_V ? a.vals + g : nullptr, a.keys + g, HAS_V ? a.vals + g : nullptr, int(len),
+                   a.alt_k + g, HAS_V ? a.alt_v + g : nullptr);
     } else {
       c.sort_large(a.keys + g, HAS_V ? a.vals + g : nullptr, a.alt_k + g, HAS_V ? a.alt_v + g : nullptr, len);
     }
