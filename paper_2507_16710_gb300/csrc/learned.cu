@@ -42,12 +42,15 @@ __global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t
                                     const uint32_t *gate) {
   if (gate && *gate) return;
   __shared__ float c[2][LM_KNOTS];
-  __shared__ uint32_t s_err[2];
+  __shared__ uint32_t s_err[2], s_heavy[2];
   if (threadIdx.x < LM_KNOTS) {
     c[0][threadIdx.x] = md->c[threadIdx.x];
     c[1][threadIdx.x] = md->c_v[threadIdx.x];
   }
-  if (threadIdx.x < 2) s_err[threadIdx.x] = 0u;
+  if (threadIdx.x < 2) {
+    s_err[threadIdx.x] = 0u;
+    s_heavy[threadIdx.x] = 0u;
+  }
   __syncthreads();
   // overload of a window of k consecutive sample keys: the share of keys it
   // holds over the share of buckets the model gives it
@@ -58,24 +61,49 @@ __global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t
     return d > 0.f ? share / d : FLT_MAX;
   };
   float e0 = 0.f, e1 = 0.f;
+  uint32_t h0 = 0, h1 = 0;  // sample keys whose window would overflow its buckets far beyond capacity
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i + k < m; i += gridDim.x * blockDim.x) {
-    e0 = fmaxf(e0, overload(c[0], xs, i));
-    if (xs_v) e1 = fmaxf(e1, overload(c[1], xs_v, i));
+    const float o0 = overload(c[0], xs, i);
+    e0 = fmaxf(e0, o0);
+    h0 += o0 > LM_HEAVY ? 1u : 0u;
+    if (xs_v) {
+      const float o1 = overload(c[1], xs_v, i);
+      e1 = fmaxf(e1, o1);
+      h1 += o1 > LM_HEAVY ? 1u : 0u;
+    }
   }
   atomicMax(&s_err[0], __float_as_uint(e0));  // non-negative floats order like their bits
   atomicMax(&s_err[1], __float_as_uint(e1));
+  if (h0) atomicAdd(&s_heavy[0], h0);
+  if (h1) atomicAdd(&s_heavy[1], h1);
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicMax(&md->err_bits[0], s_err[0]);
     atomicMax(&md->err_bits[1], s_err[1]);
+    atomicAdd(&md->heavy[0], s_heavy[0]);
+    atomicAdd(&md->heavy[1], s_heavy[1]);
   }
 }
 
-__global__ void lm_choose_kernel(LearnedModel *md, int has_value, const uint32_t *gate) {
+__global__ void lm_choose_kernel(LearnedModel *md, int has_value, DevHeader *hdr, int64_t n, uint32_t nbuckets,
+                                 const uint32_t *gate) {
   if (gate && *gate) return;
   const bool value = has_value && md->err_bits[1] < md->err_bits[0];
-  if (threadIdx.x == 0) md->coord = value ? 1u : 0u;
   if (value && threadIdx.x < LM_KNOTS) md->c[threadIdx.x] = md->c_v[threadIdx.x];
+  if (threadIdx.x == 0) {
+    md->coord = value ? 1u : 0u;
+    // early fallback: more than a quarter of the sample in windows that would
+    // overflow their buckets far beyond capacity (the plan's criterion, read
+    // off the sample before any pass over the keys)
+    const uint32_t heavy = md->heavy[value ? 1 : 0];
+    if (uint64_t(heavy) * 4u > uint64_t(md->m)) {
+      md->use_plain = 1u;
+      hdr->info.path = AK_PATH_RADIX;
+      hdr->info.buckets = int32_t(nbuckets);
+      hdr->info.overfull_keys = md->m ? int64_t(double(heavy) / double(md->m) * double(n)) : 0;  // estimate
+      hdr->info.sample_size = int64_t(md->m);
+    }
+  }
 }
 
 __global__ void lm_knots_kernel(const float *xs, int64_t m, float *knots, LearnedModel *md, const uint32_t *gate) {

@@ -41,6 +41,9 @@ constexpr int LM_TRAIN = 8192;   // training points T
 constexpr int LM_MAX_SAMPLE = 1 << 20;
 constexpr int LM_TRAIN_BLOCK = 256;
 constexpr int LM_FIT_WINDOW = 64;  // sample keys per window of the coordinate choice
+// A window overloaded LM_HEAVY times fills its buckets (half the finish
+// capacity each on average) to 16 times the capacity: the plan's overfull mark.
+constexpr float LM_HEAVY = 32.0f;
 constexpr int LM_TRAIN_CTAS = LM_TRAIN / LM_TRAIN_BLOCK;  // one point per thread
 // r = LM_OUT_SCALE * (b3 + w3 . h2): keeps the residual's steps at the scale of
 // the piecewise-linear fit's error while the optimiser takes unit-scale steps
@@ -57,8 +60,9 @@ struct LearnedModel {
   float loss_before, loss_after;
   uint32_t coord;             // 1: float keys use the value coordinate
   uint32_t err_bits[2];       // largest PL window overload on the sample (fp32 bits): radix, value coordinate
+  uint32_t heavy[2];          // sample keys in windows overloaded above LM_HEAVY, per coordinate
   float lo_f, inv_f;          // value coordinate: sample minimum, 1 / sample range
-  uint32_t pad[1];
+  uint32_t pad[3];
   float c_v[LM_KNOTS];        // knots of the value coordinate
   float c[LM_KNOTS];          // PL knots xi_j (x-hat of sample order statistics)
   float params[LM_PARAMS];
@@ -266,8 +270,10 @@ __global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t
                                     const uint32_t *gate);
 
 // Picks the coordinate with the smaller overload (float keys) and makes its
-// knots the model's.
-__global__ void lm_choose_kernel(LearnedModel *md, int has_value, const uint32_t *gate);
+// knots the model's; sets use_plain at once when the sample shows that the
+// plan would fall back.
+__global__ void lm_choose_kernel(LearnedModel *md, int has_value, DevHeader *hdr, int64_t n, uint32_t nbuckets,
+                                 const uint32_t *gate);
 
 // Knots xi_j = xs[round(j (m-1) / 63)] of an ascending sample.
 __global__ void lm_knots_kernel(const float *xs, int64_t m, float *knots, LearnedModel *md, const uint32_t *gate);

@@ -5,10 +5,13 @@
 //   -> train the residual MLP -> monotone table -> bucket histogram -> plan
 //   -> 1-2 stable onesweep passes on the bucket-id bytes -> per-bucket sort
 //   (the segmented sort, one segment per bucket)
-// The plan kernel decides on the device whether the buckets are usable; if more
-// than a quarter of the keys sit in buckets above the shared-memory capacity it
-// sets use_plain, every learned kernel after it returns at once and the plain
-// radix sequence (launched after them, gated the other way) sorts instead.  No
+// The device decides whether the buckets are usable: already on the sample
+// (lm_choose_kernel: more than a quarter of the sample in windows the model
+// would overload far beyond capacity) or on the full bucket histogram
+// (lm_plan_kernel: more than a quarter of the keys in buckets above 16 times
+// the shared-memory capacity).  Either sets use_plain; every learned kernel
+// after it returns at once and the plain radix sequence (launched after them,
+// gated the other way) sorts instead.  No
 // host synchronisation, so the whole call can be captured in a CUDA graph.
 #pragma once
 
@@ -166,9 +169,10 @@ cudaError_t learned_launch(const RadixCall &c, const LearnedCall &lc) {
   if (VBYTES) {
     float *cv = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(lc.model) + offsetof(LearnedModel, c_v));
     lm_knots_kernel<<<1, LM_KNOTS, 0, c.stream>>>(lc.xs_v, lc.m, cv, nullptr, nullptr);
-    lm_fit_error_kernel<<<g, 256, 0, c.stream>>>(lc.xs, lc.xs_v, lc.m, lc.model, nullptr);
-    lm_choose_kernel<<<1, LM_KNOTS, 0, c.stream>>>(lc.model, 1, nullptr);
   }
+  lm_fit_error_kernel<<<g, 256, 0, c.stream>>>(lc.xs, VBYTES ? lc.xs_v : nullptr, lc.m, lc.model, nullptr);
+  lm_choose_kernel<<<1, LM_KNOTS, 0, c.stream>>>(lc.model, VBYTES ? 1 : 0, c.hdr, c.n, lc.nbuckets, nullptr);
+  const uint32_t *fallback = &lc.model->use_plain;  // every later learned kernel skips itself once set
   if (lc.train_steps > 0) {
     const int smem = int(sizeof(GradSmem));
     if ((e = cudaFuncSetAttribute(lm_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
@@ -185,12 +189,12 @@ cudaError_t learned_launch(const RadixCall &c, const LearnedCall &lc) {
     cfg.numAttrs = 1;
     if ((e = cudaLaunchKernelEx(&cfg, lm_train_kernel, static_cast<const float *>(lc.xs),
                                 static_cast<const float *>(VBYTES ? lc.xs_v : nullptr), lc.m, lc.model, lc.partials,
-                                lc.train_steps, lc.lr, lc.seed ^ 0x5EEDu, c.hdr, c.timeout_ns,
-                                static_cast<const uint32_t *>(nullptr))) != cudaSuccess)
+                                lc.train_steps, lc.lr, lc.seed ^ 0x5EEDu, c.hdr, c.timeout_ns, fallback)) !=
+        cudaSuccess)
       return e;
   }
   lm_table_kernel<<<1, 1024, 0, c.stream>>>(lc.model, lc.train_steps > 0 ? 1 : 0, lc.nbuckets, lc.bucket_bits,
-                                            nullptr);
+                                            fallback);
   // 4. bucket histogram, plan, learned passes (all skip themselves on fallback)
   switch (c.val_bytes) {
     case 0: e = lm_passes_s<U, uint32_t, false, KIND>(c, lc); break;
