@@ -42,7 +42,7 @@ NOMINAL_HBM_GBS = 8000.0
 # (profiles/onesweep_pass_traffic_33M.md): (keys per array, bytes per launch).
 # Traffic grows in proportion to the keys, so it is scaled to the run's n.  Set
 # to None whenever the digit-pass kernel changes until it is captured again.
-NCU_TRAFFIC = None
+NCU_TRAFFIC = (33_554_432, 522_239_040)
 
 
 def parse_args():
