@@ -110,7 +110,8 @@ typedef struct ak_info {
     float loss_before;       /* learned: training loss of the piecewise-linear CDF alone */
     float loss_after;        /* learned: training loss after the MLP residual is trained */
     int64_t sample_size;     /* learned: sample keys drawn */
-    int64_t reserved[4];
+    int64_t coordinate;      /* learned: model input, 0 radix key, 1 value of a float key */
+    int64_t reserved[3];
 } ak_info;
 
 /*
@@ -257,6 +258,13 @@ void ak_autotune_clear(void);
 
 /* Library version string. */
 const char *ak_version(void);
+
+/* Keys of one segment that the segmented sort (and AK_PATH_BLOCK) sorts in
+ * shared memory, for keys of key_bytes (2, 4, 8) and values of val_bytes (0, 1,
+ * 2, 4, 8; ak_sortperm carries 4-byte indices).  Longer segments first take an
+ * MSD split through global memory (the workspace copy of the segment).  Returns
+ * 0 for unsupported widths. */
+int64_t ak_segment_capacity(int key_bytes, int val_bytes);
 
 #ifdef __cplusplus
 }

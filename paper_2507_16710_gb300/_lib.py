@@ -32,6 +32,7 @@ EXPORTED = (
     "ak_status_check", "ak_last_info", "ak_status_string", "ak_learned_knots",
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
     "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
+    "ak_segment_capacity",
 )
 
 
@@ -54,7 +55,8 @@ class Info(ctypes.Structure):
                 ("radix_passes", ctypes.c_int32), ("buckets", ctypes.c_int32),
                 ("overfull_keys", ctypes.c_int64), ("max_bucket", ctypes.c_int64),
                 ("loss_before", ctypes.c_float), ("loss_after", ctypes.c_float),
-                ("sample_size", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
+                ("sample_size", ctypes.c_int64), ("coordinate", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -93,6 +95,7 @@ def load() -> ctypes.CDLL:
                 "ak_autotune_clear": ([], None),
                 "ak_version": ([], ctypes.c_char_p),
                 "ak_sort_static_scratch": ([p, i64, i32, i32, p], i32),
+                "ak_segment_capacity": ([i32, i32], i64),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -273,6 +276,11 @@ def ak_status_string(status: int) -> str:
 
 def ak_version() -> str:
     return load().ak_version().decode()
+
+
+def ak_segment_capacity(key_bytes: int, val_bytes: int = 0) -> int:
+    """Keys of one segment sorted in shared memory (see include/ak_sort.h)."""
+    return int(load().ak_segment_capacity(key_bytes, val_bytes))
 
 
 def ak_learned_knots(xs_sorted: torch.Tensor, stream=None) -> torch.Tensor:

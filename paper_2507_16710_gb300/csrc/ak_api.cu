@@ -452,6 +452,12 @@ extern "C" {
 
 const char *ak_version(void) { return "ak_sort 0.1 (sm_103a)"; }
 
+int64_t ak_segment_capacity(int key_bytes, int val_bytes) {
+  if (key_bytes != 2 && key_bytes != 4 && key_bytes != 8) return 0;
+  if (val_bytes != 0 && val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8) return 0;
+  return seg_cap(key_bytes, val_bytes);
+}
+
 const char *ak_status_string(ak_status s) {
   switch (s) {
     case AK_OK: return "ok";

@@ -102,6 +102,7 @@ __global__ void lm_choose_kernel(LearnedModel *md, int has_value, DevHeader *hdr
       hdr->info.buckets = int32_t(nbuckets);
       hdr->info.overfull_keys = md->m ? int64_t(double(heavy) / double(md->m) * double(n)) : 0;  // estimate
       hdr->info.sample_size = int64_t(md->m);
+      hdr->info.coordinate = int64_t(md->coord);
     }
   }
 }
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(1024) lm_plan_kernel(const uint32_t *counts, i
     hdr->info.loss_before = md->loss_before;
     hdr->info.loss_after = md->loss_after;
     hdr->info.sample_size = int64_t(md->m);
+    hdr->info.coordinate = int64_t(md->coord);
   }
 }
 

@@ -37,6 +37,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(_declared()) == set(ak.EXPORTED)
 
 
+def test_segment_capacity_query(lib):
+    """Host-only query: 80 KB of keys, values and 16-bit positions per segment,
+    a multiple of 32; 0 for unsupported widths."""
+    caps = {(kb, vb): lib.ak_segment_capacity(kb, vb) for kb in (2, 4, 8) for vb in (0, 1, 2, 4, 8)}
+    for (kb, vb), c in caps.items():
+        assert c % 32 == 0 and c == (81920 // (kb + vb + 2)) // 32 * 32, (kb, vb, c)
+        assert c < 65536
+    assert caps[(8, 0)] == 8192 and caps[(4, 0)] == 13632
+    assert lib.ak_segment_capacity(3, 0) == 0 and lib.ak_segment_capacity(4, 3) == 0
+
+
 def test_host_side_argument_checks(lib):
     import paper_2507_16710_gb300 as ak
     out = ctypes.c_size_t(0)

@@ -93,6 +93,20 @@ def test_learned_every_dtype(ak, dtype):
         _check_all_ops(ak, keys, desc, _learned(ak))
 
 
+@pytest.mark.parametrize("dist,coord", [("normal", 1), ("uniform", 1), ("lognormal", 0)])
+def test_model_coordinate_follows_the_sample(ak, dist, coord):
+    """Float keys: the model reads the value where a normal sample is smooth
+    and the radix key (log-like) where a lognormal sample's tail is; either way
+    the buckets stay balanced and the output exact."""
+    n = 1 << 22
+    keys = synth.dist_f64(n, dist, seed=21)
+    info = _check_all_ops(ak, keys, False, _learned(ak))
+    assert info["path"] == ak.AK_PATH_LEARNED
+    assert info["coordinate"] == coord, info
+    avg = n / info["buckets"]
+    assert info["max_bucket"] < 8 * avg, info
+
+
 def test_adversarial_input_falls_back_exactly(ak):
     """90% of the keys share one value (one bucket far above capacity): the
     device-side check routes the call to the plain radix path."""

@@ -35,9 +35,10 @@ def _want(keys, off, desc):
     return oracle.gather(keys, oracle.sortperm_segmented(keys, off, "descending" if desc else "ascending"))
 
 
-def _mixed_offsets(seed):
-    """Empty, single-key, small, above-capacity and very large segments."""
-    lens = [0, 1, 2, 0, 31, 33, 500, 2047, 2049, 6143, 6145, 12289, 40000, 3, 0, 70001, 1]
+def _mixed_offsets(seed, cap=6144):
+    """Empty, single-key, small, at-capacity (cap - 1, cap, cap + 1),
+    above-capacity and very large segments."""
+    lens = [0, 1, 2, 0, 31, 33, 500, 2047, 2049, cap - 1, cap, cap + 1, 2 * cap + 1, 40000, 3, 0, 70001, 1]
     lens += list(np.diff(synth.lognormal_segments(300, seed=seed, median=300.0, max_len=50000)))
     off = np.zeros(len(lens) + 1, dtype=np.int64)
     np.cumsum(lens, out=off[1:])
@@ -48,7 +49,7 @@ def _mixed_offsets(seed):
 @pytest.mark.parametrize("desc", [False, True])
 @pytest.mark.parametrize("mode", ["bits", "dups"])
 def test_segmented_matches_oracle(ak, dtype, desc, mode):
-    off = _mixed_offsets(40)
+    off = _mixed_offsets(40, ak.ak_segment_capacity(np.dtype(dtype).itemsize))
     keys = synth.random_keys(int(off[-1]), dtype, seed=41, mode=mode)
     assert_bits_equal(_seg_sort(ak, keys, off, desc), _want(keys, off, desc), f"{np.dtype(dtype)}")
 
@@ -114,12 +115,15 @@ def test_segmented_degenerate_inputs(ak):
 
 
 @pytest.mark.parametrize("dtype", [np.uint32, np.float64, np.int16])
-@pytest.mark.parametrize("n", [1, 2, 100, 2048, 3000, 6143, 6144, 6145, 100003])
+@pytest.mark.parametrize("n", [1, 2, 100, 2048, 3000, "cap-1", "cap", "cap+1", 100003])
 def test_block_path_sort_perm_pairs(ak, dtype, n):
     """AK_PATH_BLOCK: one launch sorts the whole array as a single segment
-    (shared memory up to the capacity, MSD split above it)."""
+    (shared memory up to the capacity, MSD split above it).  cap: the
+    key-value (8-byte values) capacity, so sort and sortperm sit below theirs."""
+    if isinstance(n, str):
+        n = ak.ak_segment_capacity(np.dtype(dtype).itemsize, 8) + {"cap-1": -1, "cap": 0, "cap+1": 1}[n]
     opts = {"path": ak.AK_PATH_BLOCK}
-    keys = synth.random_keys(n, dtype, seed=60 + n, mode="dups")
+    keys = synth.random_keys(n, dtype, seed=60 + n, mode="dups" if n % 2 else "bits")
     for desc in (False, True):
         order = "descending" if desc else "ascending"
         p = oracle_perm(keys, desc)
