@@ -42,15 +42,12 @@ __global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t
                                     const uint32_t *gate) {
   if (gate && *gate) return;
   __shared__ float c[2][LM_KNOTS];
-  __shared__ uint32_t s_err[2], s_heavy[2];
+  __shared__ uint32_t s_cnt[2][2];  // [coordinate][moderate, heavy]
   if (threadIdx.x < LM_KNOTS) {
     c[0][threadIdx.x] = md->c[threadIdx.x];
     c[1][threadIdx.x] = md->c_v[threadIdx.x];
   }
-  if (threadIdx.x < 2) {
-    s_err[threadIdx.x] = 0u;
-    s_heavy[threadIdx.x] = 0u;
-  }
+  if (threadIdx.x < 4) s_cnt[threadIdx.x >> 1][threadIdx.x & 1] = 0u;
   __syncthreads();
   // overload of a window of k consecutive sample keys: the share of keys it
   // holds over the share of buckets the model gives it
@@ -60,35 +57,35 @@ __global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t
     const float d = lm_pl(cc, x[i + k]) - lm_pl(cc, x[i]);
     return d > 0.f ? share / d : FLT_MAX;
   };
-  float e0 = 0.f, e1 = 0.f;
-  uint32_t h0 = 0, h1 = 0;  // sample keys whose window would overflow its buckets far beyond capacity
+  uint32_t n0[2] = {0u, 0u}, n1[2] = {0u, 0u};
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i + k < m; i += gridDim.x * blockDim.x) {
     const float o0 = overload(c[0], xs, i);
-    e0 = fmaxf(e0, o0);
-    h0 += o0 > LM_HEAVY ? 1u : 0u;
+    n0[0] += o0 > LM_MODERATE ? 1u : 0u;
+    n0[1] += o0 > LM_HEAVY ? 1u : 0u;
     if (xs_v) {
       const float o1 = overload(c[1], xs_v, i);
-      e1 = fmaxf(e1, o1);
-      h1 += o1 > LM_HEAVY ? 1u : 0u;
+      n1[0] += o1 > LM_MODERATE ? 1u : 0u;
+      n1[1] += o1 > LM_HEAVY ? 1u : 0u;
     }
   }
-  atomicMax(&s_err[0], __float_as_uint(e0));  // non-negative floats order like their bits
-  atomicMax(&s_err[1], __float_as_uint(e1));
-  if (h0) atomicAdd(&s_heavy[0], h0);
-  if (h1) atomicAdd(&s_heavy[1], h1);
+  for (int q = 0; q < 2; ++q) {
+    if (n0[q]) atomicAdd(&s_cnt[0][q], n0[q]);
+    if (n1[q]) atomicAdd(&s_cnt[1][q], n1[q]);
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicMax(&md->err_bits[0], s_err[0]);
-    atomicMax(&md->err_bits[1], s_err[1]);
-    atomicAdd(&md->heavy[0], s_heavy[0]);
-    atomicAdd(&md->heavy[1], s_heavy[1]);
+  if (threadIdx.x < 2) {
+    atomicAdd(&md->moderate[threadIdx.x], s_cnt[threadIdx.x][0]);
+    atomicAdd(&md->heavy[threadIdx.x], s_cnt[threadIdx.x][1]);
   }
 }
 
 __global__ void lm_choose_kernel(LearnedModel *md, int has_value, DevHeader *hdr, int64_t n, uint32_t nbuckets,
                                  const uint32_t *gate) {
   if (gate && *gate) return;
-  const bool value = has_value && md->err_bits[1] < md->err_bits[0];
+  // fewer windows far beyond capacity, then fewer moderately overloaded ones;
+  // duplicate runs (no model splits them) weigh the same in both coordinates
+  const bool value = has_value && (md->heavy[1] < md->heavy[0] ||
+                                   (md->heavy[1] == md->heavy[0] && md->moderate[1] < md->moderate[0]));
   if (value && threadIdx.x < LM_KNOTS) md->c[threadIdx.x] = md->c_v[threadIdx.x];
   if (threadIdx.x == 0) {
     md->coord = value ? 1u : 0u;

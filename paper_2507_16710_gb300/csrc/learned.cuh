@@ -8,9 +8,10 @@
 //           or, for float keys, a float32 image of the value (negated for a
 //           descending sort; NaN after every number) -- whichever of the two
 //           overloads buckets less on the sample under the piecewise-linear fit
-//           below (largest ratio, over windows of LM_FIT_WINDOW consecutive
-//           sample keys, of the keys' share to the share of the CDF the fit
-//           gives them)
+//           below: the overload of a window of LM_FIT_WINDOW consecutive sample
+//           keys is their share of the keys over the share of the CDF the fit
+//           gives them; fewer windows above LM_HEAVY wins, then fewer above
+//           LM_MODERATE
 //           (in radix-key space float keys are roughly logarithmic: heavy tails
 //           stay smooth, mass near zero does not; in value space the reverse)
 //   PL    = 64-knot piecewise-linear CDF through (xi_j, j/63), xi_j the sample
@@ -43,7 +44,9 @@ constexpr int LM_TRAIN_BLOCK = 256;
 constexpr int LM_FIT_WINDOW = 64;  // sample keys per window of the coordinate choice
 // A window overloaded LM_HEAVY times fills its buckets (half the finish
 // capacity each on average) to 16 times the capacity: the plan's overfull mark.
+// LM_MODERATE: twice the capacity (one split in the finish).
 constexpr float LM_HEAVY = 32.0f;
+constexpr float LM_MODERATE = 4.0f;
 constexpr int LM_TRAIN_CTAS = LM_TRAIN / LM_TRAIN_BLOCK;  // one point per thread
 // r = LM_OUT_SCALE * (b3 + w3 . h2): keeps the residual's steps at the scale of
 // the piecewise-linear fit's error while the optimiser takes unit-scale steps
@@ -59,8 +62,8 @@ struct LearnedModel {
   uint32_t barrier;           // training grid barrier arrivals
   float loss_before, loss_after;
   uint32_t coord;             // 1: float keys use the value coordinate
-  uint32_t err_bits[2];       // largest PL window overload on the sample (fp32 bits): radix, value coordinate
-  uint32_t heavy[2];          // sample keys in windows overloaded above LM_HEAVY, per coordinate
+  uint32_t moderate[2];       // sample windows overloaded above LM_MODERATE: radix, value coordinate
+  uint32_t heavy[2];          // sample windows overloaded above LM_HEAVY, per coordinate
   float lo_f, inv_f;          // value coordinate: sample minimum, 1 / sample range
   uint32_t pad[3];
   float c_v[LM_KNOTS];        // knots of the value coordinate
@@ -263,9 +266,9 @@ __global__ void lm_sample_kernel(const U *keys, int64_t n, U flip, uint32_t m, u
 __global__ void lm_xhat_kernel(const unsigned long long *sample_r, uint32_t m, LearnedModel *md, float *xs,
                                float *xs_v, int vbytes, unsigned long long flip, const uint32_t *gate);
 
-// Largest bucket overload of the PL fit over windows of LM_FIT_WINDOW
-// consecutive keys of the sorted sample, per coordinate, max-reduced into
-// md->err_bits.
+// Windows of LM_FIT_WINDOW consecutive keys of the sorted sample that the PL
+// fit overloads above LM_MODERATE and LM_HEAVY, per coordinate (md->moderate,
+// md->heavy).
 __global__ void lm_fit_error_kernel(const float *xs, const float *xs_v, uint32_t m, LearnedModel *md,
                                     const uint32_t *gate);
 
