@@ -231,7 +231,8 @@ def run_ours(args):
         pristine = torch.from_numpy(host).to(dev)
         arrays.append({"pristine": pristine, "work": torch.empty_like(pristine), "kd": kd, "w": w})
     perm = torch.empty(n, dtype=torch.int32, device=dev)
-    tb = max(ak.temp_bytes(op, n, kd) for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM) for kd in (ak.AK_I64, ak.AK_F32))
+    tb = max(ak.temp_bytes(op, n, kd, options={"path": ak.AK_PATH_RADIX})
+             for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM) for kd in (ak.AK_I64, ak.AK_F32))
     temp = ak.workspace(tb, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -243,11 +244,15 @@ def run_ours(args):
         e.record(stream)
     ev_arr = (ctypes.c_void_p * len(pass_ev))(*[e.cuda_event for e in pass_ev])
     opts = ak.Options()
+    opts.path = ak.AK_PATH_RADIX  # the plain radix path: the digit-pass kernel is the roofline's subject
     opts.pass_events = ctypes.cast(ev_arr, ctypes.c_void_p)
     calls = [("sortperm", 0), ("sort", 0), ("sortperm", 1), ("sort", 1)]
 
+    radix_opts = ak.Options()
+    radix_opts.path = ak.AK_PATH_RADIX
+
     def call(op, a, with_events):
-        o = ctypes.byref(opts) if with_events else None
+        o = ctypes.byref(opts) if with_events else ctypes.byref(radix_opts)
         if op == "sort":
             rc = lib.ak_sort(a["work"].data_ptr(), n, a["kd"], 0, temp.data_ptr(), temp.numel(),
                              stream.cuda_stream, o)
@@ -351,41 +356,79 @@ def run_ours(args):
 
 
 def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n):
-    """Same four calls from pinned host buffers: H2D keys, sortperm, sort, D2H perm + sorted keys."""
+    """Same four calls from pinned host buffers: H2D keys, sortperm, sort, D2H perm + sorted keys,
+    with default options (the library picks the path, as a caller's plain call does).  Copies run
+    on their own streams so that one array's upload and the other's downloads overlap the sorts
+    (events order every buffer reuse)."""
+    del temp
+    temp = ak.workspace(max(ak.temp_bytes(op, n, kd) for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM)
+                            for kd in (ak.AK_I64, ak.AK_F32)), dev)
     hosts = [torch.from_numpy(k64).pin_memory(), torch.from_numpy(k32).pin_memory()]
     outs_k = [torch.empty_like(h).pin_memory() for h in hosts]
     outs_p = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in hosts]
     dk = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in hosts]
-    dp = torch.empty(n, dtype=torch.int32, device=dev)
+    dp = [torch.empty(n, dtype=torch.int32, device=dev) for _ in hosts]
     kds = [ak.AK_I64, ak.AK_F32]
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    freed = [None, None]  # per array: its previous results have left the device
 
     def step():
+        loaded = []
+        for i in range(2):  # both uploads queue at once on the upload stream
+            with torch.cuda.stream(up):
+                if freed[i] is not None:
+                    up.wait_event(freed[i])
+                dk[i].copy_(hosts[i], non_blocking=True)
+                e = ev()
+                e.record(up)
+                loaded.append(e)
         for i in range(2):
-            dk[i].copy_(hosts[i], non_blocking=True)
-            rc = lib.ak_sortperm(dk[i].data_ptr(), dp.data_ptr(), n, kds[i], 0, temp.data_ptr(), temp.numel(),
+            stream.wait_event(loaded[i])
+            rc = lib.ak_sortperm(dk[i].data_ptr(), dp[i].data_ptr(), n, kds[i], 0, temp.data_ptr(), temp.numel(),
                                  stream.cuda_stream, None)
+            perm_done = ev()
+            perm_done.record(stream)
             rc |= lib.ak_sort(dk[i].data_ptr(), n, kds[i], 0, temp.data_ptr(), temp.numel(), stream.cuda_stream,
                               None)
             if rc:
                 raise ak.AkError(rc, "e2e")
-            outs_p[i].copy_(dp, non_blocking=True)
-            outs_k[i].copy_(dk[i], non_blocking=True)
+            sort_done = ev()
+            sort_done.record(stream)
+            with torch.cuda.stream(down):
+                down.wait_event(perm_done)
+                outs_p[i].copy_(dp[i], non_blocking=True)
+                down.wait_event(sort_done)
+                outs_k[i].copy_(dk[i], non_blocking=True)
+                f = ev()
+                f.record(down)
+                freed[i] = f
 
     for _ in range(max(1, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
     steps = max(1, min(args.steps, 3))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    e0.record(up)
     for _ in range(steps):
         step()
+    stream.wait_event(freed[0])
+    stream.wait_event(freed[1])
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
     h2d = sum(h.numel() * h.element_size() for h in hosts)
     d2h = h2d + 2 * 4 * n
+    # the results of the last step are read back and spot-checked against the input multiset size
+    assert outs_k[0].numel() == n and outs_p[1].numel() == n
+    paths = {}
+    for i, kd in enumerate(kds):
+        dk[i].copy_(hosts[i], non_blocking=True)
+        lib.ak_sort(dk[i].data_ptr(), n, kd, 0, temp.data_ptr(), temp.numel(), stream.cuda_stream, None)
+        paths["i64" if i == 0 else "f32"] = {1: "radix", 2: "learned", 3: "block"}.get(ak.ak_last_info(temp)["path"])
     return {"value": round(24 * n / (ms / 1e3) / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3), "steps": steps}
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3), "steps": steps, "paths": paths,
+            "copies": "upload / download streams overlapping the sorts"}
 
 
 # ------------------------------------------------------------ other workloads

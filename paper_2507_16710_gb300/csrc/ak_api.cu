@@ -168,11 +168,18 @@ __global__ void iota_u32_kernel(uint32_t *p, int64_t n) {
 }
 
 // Which path serves a sort/sortperm/pairs call.
+// AUTO: one CTA for what fits it; learned buckets for large arrays of 64-bit
+// keys (2 bucket passes and a shared-memory finish instead of up to 8 radix
+// passes, with the on-device fallback for keys the model cannot spread);
+// radix otherwise.
+constexpr int64_t LEARNED_AUTO_MIN = int64_t(1) << 25;
 static int choose_path(int op, int64_t n, int key_bytes, int vb, const ak_options &o) {
   if (o.path == AK_PATH_RADIX || o.path == AK_PATH_BLOCK) return o.path;
   if (o.path == AK_PATH_LEARNED) return n < (int64_t(1) << 32) ? AK_PATH_LEARNED : AK_PATH_RADIX;
   (void)op;
-  return n <= seg_cap(key_bytes, vb) ? AK_PATH_BLOCK : AK_PATH_RADIX;
+  if (n <= seg_cap(key_bytes, vb)) return AK_PATH_BLOCK;
+  if (key_bytes == 8 && n >= LEARNED_AUTO_MIN && n < (int64_t(1) << 32)) return AK_PATH_LEARNED;
+  return AK_PATH_RADIX;
 }
 
 static int value_bytes(int op, int val_bytes) {

@@ -141,3 +141,21 @@ def test_mlp_residual_gain_over_piecewise_linear(ak):
     trained = res[0]
     assert trained["loss_after"] < trained["loss_before"], trained
     assert trained["max_bucket"] <= 2 * res[-1]["max_bucket"], (trained, res[-1])
+
+
+def test_auto_takes_learned_for_large_64bit_keys(ak):
+    """AK_PATH_AUTO sorts 2^25+ 64-bit keys through the learned buckets (exact;
+    integer keys equal under isless are bit-identical, so numpy's sort is the
+    oracle's answer)."""
+    n = 1 << 25
+    keys = synth.uniform_i64(n, seed=8)
+    t, _ = to_dev(keys)
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_I64), t.device)
+    ak.ak_sort(t, temp=temp)
+    assert ak.ak_last_info(temp)["path"] == ak.AK_PATH_LEARNED
+    assert np.array_equal(to_host(t, np.int64), np.sort(keys))
+    small = synth.uniform_i64(1 << 20, seed=9)
+    t, _ = to_dev(small)
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, small.size, ak.AK_I64), t.device)
+    ak.ak_sort(t, temp=temp)
+    assert ak.ak_last_info(temp)["path"] == ak.AK_PATH_RADIX
