@@ -100,10 +100,11 @@ static ak_options resolve_options(const ak_options *opt) {
 // AK_PATH_AUTO with no explicit tile configuration takes the autotuned choice.
 static void apply_tuning(int op, int kd, int64_t n, int val_bytes, ak_options &o) {
   if (o.path != AK_PATH_AUTO || o.tile_config != 0) return;
-  int path = 0, tc = 0;
-  if (tune_lookup(op, kd, n, op == AK_OP_SORT_PAIRS ? val_bytes : 0, &path, &tc)) {
+  int path = 0, tc = 0, bb = 0;
+  if (tune_lookup(op, kd, n, op == AK_OP_SORT_PAIRS ? val_bytes : 0, &path, &tc, &bb)) {
     o.path = path;
     o.tile_config = tc;
+    if (o.bucket_bits == 0) o.bucket_bits = bb;
   }
 }
 
@@ -296,6 +297,12 @@ static LearnedLayout learned_layout(int op, int64_t n, int key_bytes, int val_by
 
 static size_t learned_total(int op, int64_t n, int key_bytes, int val_bytes, const ak_options &o) {
   return learned_layout(op, n, key_bytes, val_bytes, o).total;
+}
+
+// Bucket bits the learned path picks by itself for this call shape.
+int learned_auto_bucket_bits(int op, int64_t n, int key_bytes, int val_bytes) {
+  ak_options o{};
+  return int(learned_layout(op, n, key_bytes, val_bytes, o).bbits);
 }
 
 static cudaError_t learned_dispatch(int key_bytes, int kind, const RadixCall &c, const LearnedCall &lc) {

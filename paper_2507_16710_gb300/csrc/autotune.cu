@@ -1,7 +1,8 @@
 // autotune.cu -- timed choice of path and tile configuration per call shape.
 //
 // ak_autotune runs every candidate (radix with each tile configuration, the
-// learned path, and the one-launch block path when n fits it) on the caller's
+// learned path with its own bucket count and with half and twice as many
+// buckets, and the one-launch block path when n fits it) on the caller's
 // buffers, restoring the inputs from a copy in the workspace before each timed
 // call, times it with CUDA events on the caller's stream and records the
 // fastest under (op, dtype, ceil(log2 n), value bytes).  AK_PATH_AUTO
@@ -23,7 +24,7 @@ namespace ak {
 namespace {
 
 struct TuneEntry {
-  int path, tile_config;
+  int path, tile_config, bucket_bits;
   float ms;
 };
 using TuneKey = std::tuple<int, int, int, int>;  // op, dtype, log2 n, value bytes
@@ -43,14 +44,16 @@ ak_status load_file(const char *path) {
   if (!f) return AK_ERR_INVALID_ARG;
   char line[512];
   while (fgets(line, sizeof line, f)) {
-    int op, dt, lg, vb, pth, tc;
+    int op, dt, lg, vb, pth, tc, bb = 0;
     float ms;
-    if (sscanf(line,
-               " {\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
-               "\"tile_config\": %d, \"ms\": %f}",
-               &op, &dt, &lg, &vb, &pth, &tc, &ms) == 7 &&
-        pth >= AK_PATH_RADIX && pth <= AK_PATH_BLOCK && tc >= 0 && tc <= AK_TILE_CONFIGS)
-      g_cache[TuneKey(op, dt, lg, vb)] = TuneEntry{pth, tc, ms};
+    // bucket_bits is optional (entries written before it existed mean "automatic")
+    const int got = sscanf(line,
+                           " {\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
+                           "\"tile_config\": %d, \"ms\": %f, \"bucket_bits\": %d}",
+                           &op, &dt, &lg, &vb, &pth, &tc, &ms, &bb);
+    if ((got == 7 || got == 8) && pth >= AK_PATH_RADIX && pth <= AK_PATH_BLOCK && tc >= 0 &&
+        tc <= AK_TILE_CONFIGS && (bb == 0 || (bb >= 8 && bb <= 16)))
+      g_cache[TuneKey(op, dt, lg, vb)] = TuneEntry{pth, tc, bb, ms};
   }
   fclose(f);
   return AK_OK;
@@ -65,13 +68,14 @@ void load_env_once() {  // caller holds g_mu
 
 }  // namespace
 
-bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config) {
+bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config, int *bucket_bits) {
   std::lock_guard<std::mutex> lock(g_mu);
   load_env_once();
   auto it = g_cache.find(TuneKey(op, dtype, log2_class(n), val_bytes));
   if (it == g_cache.end()) return false;
   *path = it->second.path;
   *tile_config = it->second.tile_config;
+  *bucket_bits = it->second.bucket_bits;
   return true;
 }
 
@@ -99,9 +103,15 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
     cands.push_back(o);
   }
   if (n >= (int64_t(1) << 16) && n < (int64_t(1) << 32)) {
-    ak_options o{};
-    o.path = AK_PATH_LEARNED;
-    cands.push_back(o);
+    const int bb = learned_auto_bucket_bits(op, n, kb, vb);
+    for (int d = -1; d <= 1; ++d) {  // its own bucket count, then half and twice as many buckets
+      const int b = d == 0 ? 0 : bb + d;
+      if (b != 0 && (b < 8 || b > 16)) continue;
+      ak_options o{};
+      o.path = AK_PATH_LEARNED;
+      o.bucket_bits = b;
+      cands.push_back(o);
+    }
   }
   if (n <= seg_cap(kb, op == AK_OP_SORTPERM ? 4 : vb)) {
     ak_options o{};
@@ -166,7 +176,8 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
   if (!isfinite(best_ms)) return result == AK_OK ? AK_ERR_CUDA : result;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    g_cache[TuneKey(op, int(kd), log2_class(n), vb)] = TuneEntry{best_o.path, best_o.tile_config, best_ms};
+    g_cache[TuneKey(op, int(kd), log2_class(n), vb)] = TuneEntry{best_o.path, best_o.tile_config, best_o.bucket_bits,
+                                                                 best_ms};
   }
   if (best) *best = best_o;
   return result;
@@ -182,8 +193,8 @@ ak_status ak_autotune_save(const char *path) {
     std::tie(op, dt, lg, vb) = kv.first;
     fprintf(f,
             "{\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
-            "\"tile_config\": %d, \"ms\": %.6f}\n",
-            op, dt, lg, vb, kv.second.path, kv.second.tile_config, kv.second.ms);
+            "\"tile_config\": %d, \"ms\": %.6f, \"bucket_bits\": %d}\n",
+            op, dt, lg, vb, kv.second.path, kv.second.tile_config, kv.second.ms, kv.second.bucket_bits);
   }
   fclose(f);
   return AK_OK;

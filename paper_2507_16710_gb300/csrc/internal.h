@@ -131,6 +131,8 @@ cudaError_t seg_launch_u64_float(const SegCall &c);
 int device_sm_count();
 
 // Autotune cache: the tuned path and tile configuration of a call shape.
-bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config);
+bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config, int *bucket_bits);
+// Bucket bits the learned path picks by itself for a call shape.
+int learned_auto_bucket_bits(int op, int64_t n, int key_bytes, int val_bytes);
 
 }  // namespace ak

@@ -97,3 +97,19 @@ def test_autotune_cache_roundtrip_and_auto_sizing(lib, tmp_path):
     assert len(rows) == 1 and rows[0]["path"] == ak.AK_PATH_LEARNED and rows[0]["log2n"] == 22
     lib.ak_autotune_clear()
     assert ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64) == base
+    # a tuned bucket count travels with the entry; out-of-range counts are skipped
+    learned9 = ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64, options={"path": ak.AK_PATH_LEARNED, "bucket_bits": 9})
+    assert learned9 != learned
+    src.write_text(
+        json.dumps({"op": 0, "dtype": ak.AK_F64, "log2n": 22, "val_bytes": 0, "path": ak.AK_PATH_LEARNED,
+                    "tile_config": 0, "ms": 1.5, "bucket_bits": 9}) + "\n" +
+        json.dumps({"op": 0, "dtype": ak.AK_F32, "log2n": 22, "val_bytes": 0, "path": ak.AK_PATH_LEARNED,
+                    "tile_config": 0, "ms": 1.5, "bucket_bits": 30}) + "\n")
+    ak.ak_autotune_load(str(src))
+    assert ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64) == learned9
+    assert ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F32) == ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F32,
+                                                                       options={"path": ak.AK_PATH_RADIX})
+    ak.ak_autotune_save(str(out))
+    rows = [json.loads(x) for x in out.read_text().splitlines()]
+    assert len(rows) == 1 and rows[0]["bucket_bits"] == 9
+    lib.ak_autotune_clear()
