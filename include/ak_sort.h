@@ -239,19 +239,24 @@ size_t ak_learned_grad_temp_bytes(int64_t m);
  * AK_TUNE_CACHE names a cache file loaded on first use. */
 
 /*
- * Tunes one call shape (op = AK_OP_SORT, AK_OP_SORTPERM or AK_OP_SORT_PAIRS).
+ * Tunes one call shape (op = AK_OP_SORT, AK_OP_SORTPERM or AK_OP_SORT_PAIRS):
+ * times the radix path in each tile configuration, the learned path at its own
+ * bucket count and at half and twice as many buckets, and the block path when n
+ * fits one CTA, and caches the fastest (path, tile configuration, bucket bits).
  * d_keys (and d_vals for pairs, d_perm for sortperm) are the call's buffers: they
  * are restored from a copy before every timed call and hold the original inputs
- * again on return.  d_temp must hold the largest candidate's workspace
- * (ak_sort_temp_bytes with path AK_PATH_LEARNED or AK_PATH_RADIX, whichever is
- * larger, rounded up to 256 bytes) plus n * (key bytes + value bytes) for the
- * copy.  Synchronises `stream`.  `best` (optional) receives the chosen options.
+ * again on return.  d_temp must hold ak_autotune_temp_bytes bytes (the largest
+ * candidate's workspace, rounded up to 256 bytes, plus n * (key bytes + value
+ * bytes) for the copy).  Synchronises `stream`.  `best` (optional) receives the
+ * chosen options.
  */
 ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order order,
                       void *d_keys, void *d_vals, uint32_t *d_perm, void *d_temp,
                       size_t temp_bytes, ak_stream_t stream, ak_options *best);
+/* Workspace ak_autotune needs for this call shape (host only). */
+ak_status ak_autotune_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, size_t *bytes);
 /* The cache as JSON lines {"op", "dtype", "log2n", "val_bytes", "path",
- * "tile_config", "ms"}: save, load (merging; malformed lines are skipped), clear. */
+ * "tile_config", "ms", "bucket_bits"} (bucket_bits optional, 0 = automatic): save, load (merging; malformed lines are skipped), clear. */
 ak_status ak_autotune_save(const char *path);
 ak_status ak_autotune_load(const char *path);
 void ak_autotune_clear(void);

@@ -32,7 +32,7 @@ EXPORTED = (
     "ak_status_check", "ak_last_info", "ak_status_string", "ak_learned_knots",
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
     "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
-    "ak_segment_capacity",
+    "ak_segment_capacity", "ak_autotune_temp_bytes",
 )
 
 
@@ -96,6 +96,7 @@ def load() -> ctypes.CDLL:
                 "ak_version": ([], ctypes.c_char_p),
                 "ak_sort_static_scratch": ([p, i64, i32, i32, p], i32),
                 "ak_segment_capacity": ([i32, i32], i64),
+                "ak_autotune_temp_bytes": ([i32, i64, i32, i32, ctypes.POINTER(sz)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -307,10 +308,9 @@ def ak_learned_loss_grad(x: torch.Tensor, y: torch.Tensor, c: torch.Tensor, para
 
 def autotune_temp_bytes(op: int, n: int, kd: int, val_bytes: int = 0) -> int:
     """Workspace ak_autotune needs: the largest candidate plus a copy of the inputs."""
-    need = max(temp_bytes(op, n, kd, val_bytes, 0, {"path": p}) for p in (AK_PATH_RADIX, AK_PATH_LEARNED))
-    need = (need + 255) // 256 * 256
-    kb = {AK_U16: 2, AK_I16: 2, AK_U32: 4, AK_I32: 4, AK_F32: 4}.get(kd, 8)
-    return need + n * (kb + (val_bytes if op == AK_OP_SORT_PAIRS else 0))
+    out = ctypes.c_size_t(0)
+    _check(load().ak_autotune_temp_bytes(op, n, kd, val_bytes, ctypes.byref(out)), "ak_autotune_temp_bytes")
+    return out.value
 
 
 def ak_autotune(op: int, keys: torch.Tensor, order="ascending", vals=None, perm=None, temp=None,

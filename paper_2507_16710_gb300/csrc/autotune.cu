@@ -83,24 +83,21 @@ bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *ti
 
 using namespace ak;
 
-extern "C" {
-
-ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order order, void *d_keys, void *d_vals,
-                      uint32_t *d_perm, void *d_temp, size_t temp_bytes, ak_stream_t stream, ak_options *best) {
+// Candidates of one call shape and the workspace ak_autotune needs for them:
+// the largest candidate's temporaries (256-byte aligned), then a copy of the inputs.
+static ak_status candidates(int op, int64_t n, ak_dtype kd, int val_bytes, std::vector<ak_options> *cands,
+                            size_t *need, size_t *input_bytes) {
   if (op != AK_OP_SORT && op != AK_OP_SORTPERM && op != AK_OP_SORT_PAIRS) return AK_ERR_INVALID_ARG;
-  if (n <= 0 || !d_keys || !d_temp || (op == AK_OP_SORT_PAIRS && !d_vals) || (op == AK_OP_SORTPERM && !d_perm))
-    return AK_ERR_INVALID_ARG;
+  if (n <= 0 || int(kd) < int(AK_U16) || int(kd) > int(AK_F64)) return AK_ERR_INVALID_ARG;
   const int kb = (kd <= AK_I16) ? 2 : (kd <= AK_I32 || kd == AK_F32) ? 4 : 8;
   const int vb = (op == AK_OP_SORT_PAIRS) ? val_bytes : 0;
   if (op == AK_OP_SORT_PAIRS && vb != 1 && vb != 2 && vb != 4 && vb != 8) return AK_ERR_INVALID_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // candidates
-  std::vector<ak_options> cands;
+  cands->clear();
   for (int tc = 1; tc <= AK_TILE_CONFIGS; ++tc) {
     ak_options o{};
     o.path = AK_PATH_RADIX;
     o.tile_config = tc;
-    cands.push_back(o);
+    cands->push_back(o);
   }
   if (n >= (int64_t(1) << 16) && n < (int64_t(1) << 32)) {
     const int bb = learned_auto_bucket_bits(op, n, kb, vb);
@@ -110,21 +107,49 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
       ak_options o{};
       o.path = AK_PATH_LEARNED;
       o.bucket_bits = b;
-      cands.push_back(o);
+      cands->push_back(o);
     }
   }
   if (n <= seg_cap(kb, op == AK_OP_SORTPERM ? 4 : vb)) {
     ak_options o{};
     o.path = AK_PATH_BLOCK;
-    cands.push_back(o);
+    cands->push_back(o);
   }
-  // the workspace holds the largest candidate's temporaries, then a copy of the inputs
-  size_t need = 0;
-  for (const ak_options &o : cands) {
+  size_t m = 0;
+  for (const ak_options &o : *cands) {
     size_t b = 0;
-    if (ak_sort_temp_bytes(op, n, kd, val_bytes, 0, &o, &b) == AK_OK && b > need) need = b;
+    if (ak_sort_temp_bytes(op, n, kd, val_bytes, 0, &o, &b) == AK_OK && b > m) m = b;
   }
-  need = (need + 255) & ~size_t(255);
+  *need = (m + 255) & ~size_t(255);
+  *input_bytes = size_t(n) * kb + size_t(n) * vb;
+  return AK_OK;
+}
+
+
+extern "C" {
+
+ak_status ak_autotune_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, size_t *bytes) {
+  if (!bytes) return AK_ERR_INVALID_ARG;
+  std::vector<ak_options> cands;
+  size_t need = 0, in = 0;
+  const ak_status s = candidates(op, n, kd, val_bytes, &cands, &need, &in);
+  if (s != AK_OK) return s;
+  *bytes = need + in;
+  return AK_OK;
+}
+
+ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order order, void *d_keys, void *d_vals,
+                      uint32_t *d_perm, void *d_temp, size_t temp_bytes, ak_stream_t stream, ak_options *best) {
+  std::vector<ak_options> cands;
+  size_t need = 0, inb = 0;
+  const ak_status cs = candidates(op, n, kd, val_bytes, &cands, &need, &inb);
+  if (cs != AK_OK) return cs;
+  (void)inb;
+  if (!d_keys || !d_temp || (op == AK_OP_SORT_PAIRS && !d_vals) || (op == AK_OP_SORTPERM && !d_perm))
+    return AK_ERR_INVALID_ARG;
+  const int kb = (kd <= AK_I16) ? 2 : (kd <= AK_I32 || kd == AK_F32) ? 4 : 8;
+  const int vb = (op == AK_OP_SORT_PAIRS) ? val_bytes : 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t kbytes = size_t(n) * kb, vbytes = size_t(n) * vb;
   if (temp_bytes < need + kbytes + vbytes) return AK_ERR_WORKSPACE_TOO_SMALL;
   uint8_t *copy_k = static_cast<uint8_t *>(d_temp) + need;

@@ -48,6 +48,20 @@ def test_segment_capacity_query(lib):
     assert lib.ak_segment_capacity(3, 0) == 0 and lib.ak_segment_capacity(4, 3) == 0
 
 
+def test_autotune_workspace_query(lib):
+    """ak_autotune_temp_bytes covers every candidate plus the input copy."""
+    import paper_2507_16710_gb300 as ak
+    n = 1 << 20
+    for op, vb in ((ak.AK_OP_SORT, 0), (ak.AK_OP_SORTPERM, 0), (ak.AK_OP_SORT_PAIRS, 4)):
+        need = ak.autotune_temp_bytes(op, n, ak.AK_F64, vb)
+        copy = n * (8 + (vb if op == ak.AK_OP_SORT_PAIRS else 0))
+        for opts in ({"path": ak.AK_PATH_RADIX, "tile_config": 3}, {"path": ak.AK_PATH_LEARNED}):
+            assert need >= ak.temp_bytes(op, n, ak.AK_F64, vb, options=opts) + copy
+    out = ctypes.c_size_t(0)
+    assert lib.ak_autotune_temp_bytes(ak.AK_OP_SORT_SEGMENTED, n, ak.AK_F64, 0, ctypes.byref(out)) == 1
+    assert lib.ak_autotune_temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64, 0, None) == 1
+
+
 def test_host_side_argument_checks(lib):
     import paper_2507_16710_gb300 as ak
     out = ctypes.c_size_t(0)
