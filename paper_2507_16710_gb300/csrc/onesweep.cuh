@@ -24,7 +24,6 @@
 #include "common.cuh"
 #include "learned.cuh"
 
-
 namespace ak {
 
 constexpr uint32_t INACTIVE = 0xFFFFFFFFu;
@@ -375,7 +374,6 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
         const int idx = wbase + i * 32 + lane;
         dr[i] = (FULL || idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
       }
-      uint32_t my_cnt = 0;
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         const uint32_t d = dr[i];
@@ -395,7 +393,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
       __syncthreads();  // A: every warp row complete
 
       // ---- tile counts, publish, digit scan
-      uint32_t inc = 0;
+      uint32_t my_cnt = 0, inc = 0;
       uint32_t *hrow = whist32 + tid * L::HSTRIDE;
       if (tid < RADIX) {
 #pragma unroll
