@@ -75,8 +75,13 @@ typedef enum ak_path {
 /* Optional tuning knobs.  Pass NULL for defaults; zero fields mean "default". */
 typedef struct ak_options {
     int32_t path;          /* ak_path */
-    int32_t tile_config;   /* onesweep tile variant: 0 = default, 1..AK_TILE_CONFIGS */
-    int32_t bucket_bits;   /* learned path: log2(bucket count incl. NaN bucket), 0 = auto */
+    int32_t tile_config;   /* digit-pass variant, 0 = default (1), else 1..AK_TILE_CONFIGS:
+                              1 persistent 512-thread CTAs, 32 KB tiles; 2 persistent
+                              384-thread CTAs, 24 KB tiles; 3 one 512-thread CTA per
+                              32 KB tile with an L2 prefetch one wave ahead */
+    int32_t bucket_bits;   /* learned path: log2 of the bucket count, 8..16 (NaN keys share
+                              the last bucket); 0 = auto, about half the shared-memory
+                              finish capacity (ak_segment_capacity) per bucket */
     uint32_t seed;         /* learned path: seed of the sample index stream */
     uint64_t timeout_ns;   /* bound on every device-side wait, 0 = 1 s */
     int32_t train_steps;   /* learned path: Adam steps of the residual MLP, 0 = default (32),
@@ -94,7 +99,8 @@ typedef struct ak_options {
  * that reaches it waits until timeout_ns and the call ends with AK_ERR_TIMEOUT
  * (the keys are then unspecified).  Exercises the bounded-wait error path. */
 #define AK_DEBUG_SKIP_FIRST_TILE 1
-/* Tuning hook: no L2 prefetch of upcoming tiles in the digit passes. */
+/* Tuning hook: no L2 prefetch one wave ahead in tile configuration 3 (the
+ * persistent configurations prefetch each claimed tile, unaffected). */
 #define AK_DEBUG_NO_PREFETCH 2
 
 #define AK_TILE_CONFIGS 3
