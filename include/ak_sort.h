@@ -84,7 +84,7 @@ typedef struct ak_options {
                               finish capacity (ak_segment_capacity) per bucket */
     uint32_t seed;         /* learned path: seed of the sample index stream */
     uint64_t timeout_ns;   /* bound on every device-side wait, 0 = 1 s */
-    int32_t train_steps;   /* learned path: Adam steps of the residual MLP, 0 = default (32),
+    int32_t train_steps;   /* learned path: Adam steps of the residual MLP, 0 = default (16),
                               -1 = no MLP (piecewise-linear CDF only) */
     int32_t debug_flags;   /* test hooks, 0 in normal use (AK_DEBUG_*) */
     void **pass_events;    /* optional: 2*AK_MAX_PASSES cudaEvent_t created by the caller;

@@ -387,7 +387,7 @@ static ak_status run_learned(int op, void *keys, const void *k_in, void *vals, i
   sc.timeout_ns = o.timeout_ns;
   sc.stream = stream;
   lc.partials = reinterpret_cast<float *>(t + L.partials);
-  lc.train_steps = o.train_steps < 0 ? 0 : (o.train_steps > 0 ? o.train_steps : 32);
+  lc.train_steps = o.train_steps < 0 ? 0 : (o.train_steps > 0 ? o.train_steps : 16);
   lc.lr = 1e-2f;
   lc.nbuckets = uint32_t(nb);
   lc.bucket_bits = L.bbits;

@@ -357,44 +357,76 @@ __global__ void __launch_bounds__(1024) lm_plan_kernel(const uint32_t *counts, i
                                                        RadixPlan *plan, DevHeader *hdr, int64_t *seg_off,
                                                        int64_t cap) {
   if (md->use_plain) return;
+  constexpr int NWARP = 1024 / 32;
   __shared__ unsigned long long d0[RADIX], d1[RADIX], scr[33];
-  __shared__ unsigned long long s_over, s_max;
+  __shared__ unsigned long long w_sum[NWARP], w_over[NWARP], w_max[NWARP];
   __shared__ int triv[2];
   const uint32_t nb = md->nbuckets, bb = md->bbits;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   if (t < RADIX) {
     d0[t] = 0ull;
     d1[t] = 0ull;
   }
   if (t < 2) triv[t] = 0;
-  if (t == 0) {
-    s_over = 0ull;
-    s_max = 0ull;
-  }
   __syncthreads();
-  const uint32_t per = (nb + 1023) / 1024;
-  const uint32_t b0 = uint32_t(t) * per;
+  // each warp owns a contiguous chunk of buckets and walks it 32 at a time
+  // (coalesced loads, shuffle scans); pass 1 sums, pass 2 writes offsets
+  const uint32_t chunk = (nb + NWARP - 1) / NWARP;
+  const uint32_t c0 = uint32_t(warp) * chunk, c1 = (c0 + chunk) < nb ? (c0 + chunk) : nb;
   unsigned long long sum = 0, over = 0, mx = 0;
-  for (uint32_t b = b0; b < b0 + per && b < nb; ++b) {
-    const unsigned long long c = counts[b];
+  for (uint32_t b0 = c0; b0 < c1; b0 += 32) {
+    const uint32_t b = b0 + lane;
+    const unsigned long long c = b < c1 ? counts[b] : 0ull;
     sum += c;
     if (int64_t(c) > 16 * cap) over += c;  // far above capacity: more than one split away
     mx = c > mx ? c : mx;
-    if (c) {
-      atomicAdd(&d0[b & (RADIX - 1)], c);
-      if (bb > RADIX_BITS) atomicAdd(&d1[b >> RADIX_BITS], c);
+    if (c) atomicAdd(&d0[b & (RADIX - 1)], c);  // 32 consecutive buckets: 32 distinct digits
+    if (bb > RADIX_BITS) {
+      // high-byte digit: the bucket count is a power of two >= 512, so chunks
+      // (nb / 32 >= 16 buckets) and their 32-bucket groups are aligned and never
+      // straddle a 256-bucket block: one digit per group
+      unsigned long long hi = c;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
+      if (lane == 0 && hi) atomicAdd(&d1[b0 >> RADIX_BITS], hi);
     }
   }
-  if (over) atomicAdd(&s_over, over);
-  if (mx) atomicMax(&s_max, mx);
-  unsigned long long tot;
-  unsigned long long run = block_exclusive_scan<1024>(sum, scr, &tot);
-  for (uint32_t b = b0; b < b0 + per && b < nb; ++b) {
-    seg_off[b] = int64_t(run);
-    run += counts[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    over += __shfl_xor_sync(0xffffffffu, over, o);
+    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = m2 > mx ? m2 : mx;
+  }
+  if (lane == 0) {
+    w_sum[warp] = sum;
+    w_over[warp] = over;
+    w_max[warp] = mx;
+  }
+  __syncthreads();
+  unsigned long long base = 0, s_over = 0, s_max = 0;
+  for (int w = 0; w < NWARP; ++w) {
+    if (w < warp) base += w_sum[w];
+    s_over += w_over[w];
+    s_max = w_max[w] > s_max ? w_max[w] : s_max;
+  }
+  // offsets: warp-level exclusive scans over the chunk, 32 buckets at a time
+  unsigned long long run = base;
+  for (uint32_t b0 = c0; b0 < c1; b0 += 32) {
+    const uint32_t b = b0 + lane;
+    const unsigned long long c = b < c1 ? counts[b] : 0ull;
+    unsigned long long inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (b < c1) seg_off[b] = int64_t(run + inc - c);
+    run += __shfl_sync(0xffffffffu, inc, 31);
   }
   if (t == 0) seg_off[nb] = n;
   __syncthreads();
+  unsigned long long tot;
   const int passes = int((bb + RADIX_BITS - 1) / RADIX_BITS);
   for (int p = 0; p < passes; ++p) {
     const unsigned long long c = t < RADIX ? (p == 0 ? d0[t] : d1[t]) : 0ull;
