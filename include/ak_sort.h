@@ -69,7 +69,9 @@ typedef enum ak_path {
     AK_PATH_AUTO = 0,     /* library choice (autotune cache, then size rules) */
     AK_PATH_RADIX = 1,    /* onesweep LSD radix: histogram + one kernel per digit */
     AK_PATH_LEARNED = 2,  /* learned-CDF bucketing + per-bucket shared-memory sort */
-    AK_PATH_BLOCK = 3     /* one-launch shared-memory sort (small n only) */
+    AK_PATH_BLOCK = 3,    /* one-launch shared-memory sort (small n only) */
+    AK_PATH_MERGE = 4     /* tiles of the shared-memory capacity sorted in one launch, then
+                             stable merge-path rounds (mid-size n) */
 } ak_path;
 
 /* Optional tuning knobs.  Pass NULL for defaults; zero fields mean "default". */
@@ -248,7 +250,8 @@ size_t ak_learned_grad_temp_bytes(int64_t m);
  * Tunes one call shape (op = AK_OP_SORT, AK_OP_SORTPERM or AK_OP_SORT_PAIRS):
  * times the radix path in each tile configuration, the learned path at its own
  * bucket count and at half and twice as many buckets, and the block path when n
- * fits one CTA, and caches the fastest (path, tile configuration, bucket bits).
+ * fits one CTA (else the merge path up to 2^26 keys), and caches the fastest
+ * (path, tile configuration, bucket bits).
  * d_keys (and d_vals for pairs, d_perm for sortperm) are the call's buffers: they
  * are restored from a copy before every timed call and hold the original inputs
  * again on return.  d_temp must hold ak_autotune_temp_bytes bytes (the largest

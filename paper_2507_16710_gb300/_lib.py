@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("AK_SORT_LIB") or os.path.join(_HERE, "lib", "libak_so
 AK_U16, AK_I16, AK_U32, AK_I32, AK_U64, AK_I64, AK_F32, AK_F64 = range(8)
 AK_ASCENDING, AK_DESCENDING = 0, 1
 AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED = range(4)
-AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK = range(4)
+AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK, AK_PATH_MERGE = range(5)
 AK_TILE_CONFIGS = 3
 AK_DEBUG_SKIP_FIRST_TILE = 1
 AK_MAX_PASSES = 8

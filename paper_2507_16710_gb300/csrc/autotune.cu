@@ -2,7 +2,8 @@
 //
 // ak_autotune runs every candidate (radix with each tile configuration, the
 // learned path with its own bucket count and with half and twice as many
-// buckets, and the one-launch block path when n fits it) on the caller's
+// buckets, the one-launch block path when n fits it, else the merge path up to
+// 2^26 keys) on the caller's
 // buffers, restoring the inputs from a copy in the workspace before each timed
 // call, times it with CUDA events on the caller's stream and records the
 // fastest under (op, dtype, ceil(log2 n), value bytes).  AK_PATH_AUTO
@@ -51,7 +52,7 @@ ak_status load_file(const char *path) {
                            " {\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
                            "\"tile_config\": %d, \"ms\": %f, \"bucket_bits\": %d}",
                            &op, &dt, &lg, &vb, &pth, &tc, &ms, &bb);
-    if ((got == 7 || got == 8) && pth >= AK_PATH_RADIX && pth <= AK_PATH_BLOCK && tc >= 0 &&
+    if ((got == 7 || got == 8) && pth >= AK_PATH_RADIX && pth <= AK_PATH_MERGE && tc >= 0 &&
         tc <= AK_TILE_CONFIGS && (bb == 0 || (bb >= 8 && bb <= 16)))
       g_cache[TuneKey(op, dt, lg, vb)] = TuneEntry{pth, tc, bb, ms};
   }
@@ -113,6 +114,10 @@ static ak_status candidates(int op, int64_t n, ak_dtype kd, int val_bytes, std::
   if (n <= seg_cap(kb, op == AK_OP_SORTPERM ? 4 : vb)) {
     ak_options o{};
     o.path = AK_PATH_BLOCK;
+    cands->push_back(o);
+  } else if (n <= (int64_t(1) << 26)) {  // a few tiles to a few thousand: tile sort + merge rounds
+    ak_options o{};
+    o.path = AK_PATH_MERGE;
     cands->push_back(o);
   }
   size_t m = 0;

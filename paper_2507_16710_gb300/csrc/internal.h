@@ -87,6 +87,7 @@ struct SegCall {
   int path_tag;            // written to ak_info.path
   const uint32_t *gate;    // if set, run only when *gate == gate_want
   uint32_t gate_want;
+  int merge;               // off == NULL: sort tiles of the shared-memory capacity, then merge them
   cudaStream_t stream;
 };
 

@@ -2,8 +2,10 @@
 #pragma once
 
 #include <algorithm>
+#include <utility>
 
 #include "internal.h"
+#include "merge.cuh"
 #include "radix_launch.cuh"
 #include "segsort.cuh"
 
@@ -25,7 +27,9 @@ cudaError_t seg_run(const SegCall &c) {
   if (e != cudaSuccess) return e;
   SegArgs<U, V> a{};
   a.off = c.off;
-  a.nseg = c.off ? c.nseg : 1;
+  // without offsets: one segment, or (merge) tiles of the shared-memory capacity
+  a.tile_len = c.off ? 0 : (c.merge ? int64_t(CAP) : c.n);
+  a.nseg = c.off ? c.nseg : (c.n + a.tile_len - 1) / a.tile_len;
   a.n = c.n;
   a.order = c.off ? c.order : nullptr;
   a.hdr = c.hdr;
@@ -46,6 +50,27 @@ cudaError_t seg_run(const SegCall &c) {
   const int64_t resident = int64_t(resident_ctas(kern, SEG_BLOCK, Lay::BYTES)) * device_sm_count();
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(a.nseg, resident)));
   kern<<<grid, SEG_BLOCK, Lay::BYTES, c.stream>>>(a);
+  if (!c.off && c.merge && c.n > CAP) {
+    // merge rounds: runs of CAP * 2^r, ping-pong between the keys and the workspace copy
+    constexpr int MB = 256, MI = 8, MCH = MB * MI;
+    auto mk = merge_pass_kernel<U, V, HAS_V, KIND, MB, MI>;
+    const int64_t mres = int64_t(resident_ctas(mk, MB, 0)) * device_sm_count();
+    U *src_k = a.keys, *dst_k = a.alt_k;
+    V *src_v = a.vals, *dst_v = a.alt_v;
+    for (int64_t w = CAP; w < c.n; w *= 2) {
+      const int64_t pairs = (c.n + 2 * w - 1) / (2 * w);
+      const int64_t cpp = (2 * w + MCH - 1) / MCH;
+      const int64_t chunks = pairs * cpp;
+      const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(chunks, mres)));
+      mk<<<g, MB, 0, c.stream>>>(src_k, src_v, dst_k, dst_v, c.n, w, a.flip, cpp, chunks);
+      std::swap(src_k, dst_k);
+      std::swap(src_v, dst_v);
+    }
+    if (src_k != a.keys) {  // an odd number of rounds: the result is in the workspace copy
+      cudaMemcpyAsync(a.keys, src_k, size_t(c.n) * sizeof(U), cudaMemcpyDeviceToDevice, c.stream);
+      if (HAS_V) cudaMemcpyAsync(a.vals, src_v, size_t(c.n) * sizeof(V), cudaMemcpyDeviceToDevice, c.stream);
+    }
+  }
   return cudaGetLastError();
 }
 

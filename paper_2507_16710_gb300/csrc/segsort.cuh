@@ -31,7 +31,8 @@ constexpr int SUB_BITS = 12;  // at most 2^SUB_BITS sub-ranges per segment
 constexpr int SUB_MAX = 48;   // largest sub-range the insertion sort takes
 
 struct SegArgsBase {
-  const int64_t *off;     // nseg + 1 offsets (clamped to [0, n] on read); NULL: one segment [0, n)
+  const int64_t *off;     // nseg + 1 offsets (clamped to [0, n] on read); NULL: tiles of tile_len
+  int64_t tile_len;       // off == NULL: segment s = [s * tile_len, (s + 1) * tile_len) within [0, n)
   int64_t nseg;
   int64_t n;
   const uint32_t *order;  // work order (segment ids), nseg entries (NULL with off == NULL)
@@ -494,8 +495,8 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
     __syncthreads();
     if (w >= a.nseg) break;
     const int64_t s = a.order ? a.order[w] : w;
-    const int64_t lo = a.off ? clamp_off(a.off[s], a.n) : 0;
-    const int64_t hi0 = a.off ? clamp_off(a.off[s + 1], a.n) : a.n;
+    const int64_t lo = a.off ? clamp_off(a.off[s], a.n) : s * a.tile_len;
+    const int64_t hi0 = a.off ? clamp_off(a.off[s + 1], a.n) : ((lo + a.tile_len) < a.n ? lo + a.tile_len : a.n);
     const int64_t hi = hi0 < lo ? lo : hi0;
     const int64_t len = hi - lo;
     if (len <= 1) continue;

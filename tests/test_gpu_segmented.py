@@ -141,7 +141,7 @@ def test_block_path_sort_perm_pairs(ak, dtype, n):
         assert_bits_equal(to_host(v, np.uint64), vals[p], "block pairs")
 
 
-def test_auto_picks_block_for_small_n(ak):
+def test_auto_picks_block_merge_radix_by_size(ak):
     keys = synth.random_keys(3000, np.uint32, seed=1)
     t, u = to_dev(keys)
     temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, 3000, ak.AK_U32), t.device)
@@ -152,3 +152,39 @@ def test_auto_picks_block_for_small_n(ak):
     temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, keys.size, ak.AK_U32), t.device)
     ak.ak_sort(t, temp=temp, unsigned=u)
     assert ak.ak_last_info(temp)["path"] == ak.AK_PATH_RADIX
+    # a few capacity tiles: the merge path, exact
+    n = 5 * ak.ak_segment_capacity(4, 0) + 17
+    keys = synth.random_keys(n, np.uint32, seed=2)
+    t, u = to_dev(keys)
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_U32), t.device)
+    ak.ak_sort(t, temp=temp, unsigned=u)
+    assert ak.ak_last_info(temp)["path"] == ak.AK_PATH_MERGE
+    assert np.array_equal(to_host(t, np.uint32), np.sort(keys))
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.int32, np.float32, np.uint64, np.float64])
+@pytest.mark.parametrize("tiles", [1.5, 2, 3.2, 8, 8.01, 77.3])
+def test_merge_path_sort_perm_pairs(ak, dtype, tiles):
+    """AK_PATH_MERGE: tiles of the shared-memory capacity sorted in one launch,
+    then stable merge-path rounds (odd and even round counts, ragged last runs)."""
+    kb = np.dtype(dtype).itemsize
+    cap = ak.ak_segment_capacity(kb, 0)
+    n = int(tiles * cap)
+    opts = {"path": ak.AK_PATH_MERGE}
+    keys = synth.random_keys(n, dtype, seed=int(tiles * 100) + kb, mode="dups" if tiles in (2, 8.01) else "bits")
+    for desc in (False, True):
+        order = "descending" if desc else "ascending"
+        p = oracle_perm(keys, desc)
+        t, u = to_dev(keys)
+        temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, n, ak.dtype_code(t, u), options=opts), t.device)
+        ak.ak_sort(t, order, temp=temp, options=opts, unsigned=u)
+        assert ak.ak_last_info(temp)["path"] == ak.AK_PATH_MERGE
+        assert_bits_equal(to_host(t, keys.dtype), oracle.gather(keys, p), "merge sort")
+        t, u = to_dev(keys)
+        perm = ak.ak_sortperm(t, order, options=opts, unsigned=u)
+        assert np.array_equal(to_host(perm, np.uint32), p.astype(np.uint32)), "merge sortperm"
+        vals = (np.arange(n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)).astype(np.uint16)
+        t, u = to_dev(keys)
+        v, _ = to_dev(vals)
+        ak.ak_sort_pairs(t, v, order, options=opts, unsigned=u)
+        assert_bits_equal(to_host(v, np.uint16), vals[p], "merge pairs")
