@@ -123,7 +123,7 @@ def test_unaligned_pointers_take_plain_loads(ak):
     base = synth.random_keys(100001, np.uint32, seed=77, mode="bits")
     t, _ = to_dev(base)
     sub = t[1:]
-    ak.ak_sort(sub, unsigned=True)
+    ak.ak_sort(sub, options={"path": ak.AK_PATH_RADIX}, unsigned=True)
     torch.cuda.synchronize()
     want = oracle.sort(base[1:])
     assert_bits_equal(to_host(sub, np.uint32), want, "unaligned")
@@ -143,14 +143,14 @@ def test_lookback_timeout_reports_status(ak):
     must give up after timeout_ns and the status word must say so."""
     keys = synth.random_keys(20000, np.uint32, seed=9, mode="bits")
     t, u = to_dev(keys)
-    opts = {"timeout_ns": 2_000_000, "debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE}
+    opts = {"path": ak.AK_PATH_RADIX, "timeout_ns": 2_000_000, "debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE}
     temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, keys.size, ak.AK_U32, options=opts), t.device)
     ak.ak_sort(t, temp=temp, options=opts, unsigned=u)
     assert ak.ak_status_check(temp) == 5
     # the context is still usable and a normal call clears the status (the
     # failed call left unspecified keys behind, so restore them first)
     t.copy_(to_dev(keys)[0])
-    ak.ak_sort(t, temp=temp, unsigned=u)
+    ak.ak_sort(t, temp=temp, options={"path": ak.AK_PATH_RADIX}, unsigned=u)
     assert ak.ak_status_check(temp) == 0
     assert_bits_equal(to_host(t, np.uint32), np.sort(keys), "after timeout")
 
@@ -179,15 +179,16 @@ def test_full_size_268M(ak, which):
     with 0.1% NaN and 0.1% -0.0; sortperm verified by the stable-sortperm
     properties, then sort compared bit-exactly with keys[perm]."""
     n = 268_435_456
+    RADIX = {"path": ak.AK_PATH_RADIX}
     keys = synth.uniform_i64(n, seed=2) if which == "i64" else synth.normal_f32_special(n, seed=3)
     for desc in (False,):
         t, u = to_dev(keys)
-        p = ak.ak_sortperm(t, "descending" if desc else "ascending", unsigned=u)
+        p = ak.ak_sortperm(t, "descending" if desc else "ascending", options=RADIX, unsigned=u)
         torch.cuda.synchronize()
         perm = to_host(p, np.uint32)
         del p
         check_perm_properties(keys, perm, desc)
-        ak.ak_sort(t, "descending" if desc else "ascending", unsigned=u)
+        ak.ak_sort(t, "descending" if desc else "ascending", options=RADIX, unsigned=u)
         torch.cuda.synchronize()
         assert_bits_equal(to_host(t, keys.dtype), keys[perm.astype(np.int64)], "full-size sort")
         del t
