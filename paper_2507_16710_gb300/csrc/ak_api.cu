@@ -243,7 +243,7 @@ static ak_status run_seg(int op, void *keys, const int64_t *off, int64_t nseg, i
 struct LearnedLayout {
   RadixLayout rad;  // the pairs/keys radix layout (fallback + bucket passes)
   size_t model, sample_r, sample_alt, xs, xs_v, s_hdr, s_counts, s_plan, s_status0, s_status1, partials, bcounts, seg_off,
-      seg_order, seg_counters, kcopy, total;
+      seg_order, seg_counters, kcopy, ids, ids_alt, total;
   uint32_t m, bbits;
 };
 
@@ -295,6 +295,10 @@ static LearnedLayout learned_layout(int op, int64_t n, int key_bytes, int val_by
   L.seg_order = take(nb * 4);
   L.seg_counters = take(256);
   if (op == AK_OP_SORTPERM) L.kcopy = take(size_t(n) * key_bytes);
+  if (op == AK_OP_SORT) {  // bucket ids carried through the passes as 16-bit values
+    L.ids = take(size_t(n) * 2);
+    L.ids_alt = take(size_t(n) * 2);
+  }
   L.total = off;
   return L;
 }
@@ -398,6 +402,8 @@ static ak_status run_learned(int op, void *keys, const void *k_in, void *vals, i
   lc.bucket_counts = reinterpret_cast<uint32_t *>(t + L.bcounts);
   lc.seg_off = reinterpret_cast<int64_t *>(t + L.seg_off);
   lc.seg_capacity = seg_cap(ki.bytes, vb);
+  lc.ids = L.ids ? reinterpret_cast<uint16_t *>(t + L.ids) : nullptr;
+  lc.ids_alt = L.ids_alt ? reinterpret_cast<uint16_t *>(t + L.ids_alt) : nullptr;
   SegCall &f = lc.finish;
   f.keys = kf;
   f.vals = vals;

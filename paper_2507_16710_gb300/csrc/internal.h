@@ -105,6 +105,7 @@ struct LearnedCall {
   uint32_t *bucket_counts;     // nbuckets, zeroed
   int64_t *seg_off;            // nbuckets + 1 bucket offsets
   int64_t seg_capacity;        // shared-memory capacity of the finish
+  uint16_t *ids, *ids_alt;     // keys-only sorts: n bucket ids and their pass copy (else NULL)
   SegCall finish;              // segmented sort over the buckets
 };
 cudaError_t learned_launch_u16_uint(const RadixCall &c, const LearnedCall &lc);

@@ -26,11 +26,13 @@ namespace ak {
 
 // Full histogram of bucket ids: 16-bit shared counters (two per word); a
 // counter that reaches 0x8000 moves 0x8000 to the global count, so no counter
-// can carry into its neighbour while up to 1024 threads increment it.
+// can carry into its neighbour while up to 1024 threads increment it.  With
+// `ids`, every key's bucket id is also stored (the passes then carry it as a
+// value instead of evaluating the model again).
 template <typename U, int KIND>
 __global__ void __launch_bounds__(1024) lm_hist_kernel(const U *__restrict__ keys, int64_t n, U flip,
                                                        const LearnedModel *md, uint32_t *counts, uint4 *zero_buf,
-                                                       int64_t zero_vec) {
+                                                       int64_t zero_vec, uint16_t *ids) {
   if (md->use_plain) return;
   extern __shared__ uint32_t hw[];
   const uint32_t nb = md->nbuckets;
@@ -41,6 +43,7 @@ __global__ void __launch_bounds__(1024) lm_hist_kernel(const U *__restrict__ key
   __syncthreads();
   for (int64_t i = gtid; i < n; i += stride) {
     const uint32_t b = lm_key_bucket<KIND>(md, keys[i], flip);
+    if (ids) ids[i] = uint16_t(b);
     const uint32_t sh = (b & 1u) * 16u;
     const uint32_t old = atomicAdd(&hw[b >> 1], 1u << sh);
     if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
@@ -82,15 +85,19 @@ template <> inline cudaError_t seg_launch_kind<uint64_t, KIND_UINT>(const SegCal
 template <> inline cudaError_t seg_launch_kind<uint64_t, KIND_SINT>(const SegCall &c) { return seg_launch_u64_sint(c); }
 template <> inline cudaError_t seg_launch_kind<uint64_t, KIND_FLOAT>(const SegCall &c) { return seg_launch_u64_float(c); }
 
-// The learned passes (digits = bytes of the bucket id) with the radix pass kernel.
-template <typename U, typename V, bool HAS_V, int KIND, typename S>
+// The learned passes (digits = bytes of the bucket id) with the radix pass
+// kernel.  DIGIT_LEARNED evaluates the model for every key in every pass;
+// DIGIT_VALUE (keys-only sorts) carries the id the histogram stored as a
+// 16-bit value instead: two extra bytes read and written per key and pass in
+// place of the model evaluation.
+template <typename U, typename V, bool HAS_V, int KIND, typename S, int DIGIT = DIGIT_LEARNED>
 cudaError_t lm_passes(const RadixCall &c, const LearnedCall &lc) {
   constexpr int CFG = 0;
   constexpr int BLOCK = CFG_BLOCK[CFG];
   constexpr int ITEMS = tile_items(sizeof(U), HAS_V ? sizeof(V) : 0, CFG);
   constexpr bool PERSIST = CFG_PERSIST[CFG];
   using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
-  auto kern = onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, PERSIST, DIGIT_LEARNED>;
+  auto kern = onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, PERSIST, DIGIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::BYTES));
   if (e != cudaSuccess) return e;
   const int64_t tiles = (c.n + L::TILE - 1) / L::TILE;
@@ -99,9 +106,15 @@ cudaError_t lm_passes(const RadixCall &c, const LearnedCall &lc) {
   a.k_final = reinterpret_cast<U *>(c.k_final);
   a.k_alt0 = reinterpret_cast<U *>(c.k_alt0);
   a.k_alt1 = reinterpret_cast<U *>(c.k_alt1);
-  a.v_in = reinterpret_cast<const V *>(c.v_in);
-  a.v_final = reinterpret_cast<V *>(c.v_final);
-  a.v_alt = reinterpret_cast<V *>(c.v_alt);
+  if constexpr (DIGIT == DIGIT_VALUE) {  // ids: histogram -> pass 1 -> pass 2 (-> the first array again)
+    a.v_in = reinterpret_cast<const V *>(lc.ids);
+    a.v_final = reinterpret_cast<V *>(lc.ids);
+    a.v_alt = reinterpret_cast<V *>(lc.ids_alt);
+  } else {
+    a.v_in = reinterpret_cast<const V *>(c.v_in);
+    a.v_final = reinterpret_cast<V *>(c.v_final);
+    a.v_alt = reinterpret_cast<V *>(c.v_alt);
+  }
   a.n = c.n;
   a.kind = c.kind;
   a.flip = c.descending ? U(~U(0)) : U(0);
@@ -122,7 +135,7 @@ cudaError_t lm_passes(const RadixCall &c, const LearnedCall &lc) {
     if (e != cudaSuccess) return e;
     hk<<<device_sm_count(), 1024, hsm, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, a.flip, lc.model,
                                                    lc.bucket_counts, reinterpret_cast<uint4 *>(c.status[0]),
-                                                   zero_vec);
+                                                   zero_vec, DIGIT == DIGIT_VALUE ? lc.ids : nullptr);
   }
   lm_plan_kernel<<<1, 1024, 0, c.stream>>>(lc.bucket_counts, c.n, lc.model, c.plan, c.hdr, lc.seg_off, lc.seg_capacity);
   const int passes = int((lc.bucket_bits + RADIX_BITS - 1) / RADIX_BITS);
@@ -145,6 +158,10 @@ cudaError_t lm_passes(const RadixCall &c, const LearnedCall &lc) {
 
 template <typename U, typename V, bool HAS_V, int KIND>
 cudaError_t lm_passes_s(const RadixCall &c, const LearnedCall &lc) {
+  if (!HAS_V && lc.ids && lc.ids_alt) {  // keys only: carry the bucket id as a 16-bit value
+    if (c.status_wide) return lm_passes<U, uint16_t, true, KIND, unsigned long long, DIGIT_VALUE>(c, lc);
+    return lm_passes<U, uint16_t, true, KIND, uint32_t, DIGIT_VALUE>(c, lc);
+  }
   if (c.status_wide) return lm_passes<U, V, HAS_V, KIND, unsigned long long>(c, lc);
   return lm_passes<U, V, HAS_V, KIND, uint32_t>(c, lc);
 }

@@ -75,8 +75,10 @@ struct PassArgs {
   int64_t prefetch_ahead;     // one-tile CTAs: L2-prefetch the tile this many ids ahead (0: off)
 };
 
-// Digit of a key in a pass: a radix digit, or a byte of the learned bucket id.
-enum DigitSource : int { DIGIT_RADIX = 0, DIGIT_LEARNED = 1 };
+// Digit of a key in a pass: a radix digit, a byte of the learned bucket id
+// evaluated from the key, or a byte of the value (a bucket id computed once and
+// carried along as the value).
+enum DigitSource : int { DIGIT_RADIX = 0, DIGIT_LEARNED = 1, DIGIT_VALUE = 2 };
 
 // ------------------------------------------------------------------ histogram
 template <typename U, int BLOCK>
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   constexpr int HROW = L::HROW;
   constexpr int H2 = 2 * L::HSTRIDE;  // u16 slots per digit row
   static_assert(BLOCK >= RADIX, "one digit per thread in the scan and look-back");
+  static_assert(DIGIT != DIGIT_VALUE || HAS_V, "a value-carried digit needs the value stream");
   extern __shared__ __align__(128) uint8_t smem[];
   U *sk = reinterpret_cast<U *>(smem);
   V *sv = reinterpret_cast<V *>(smem + L::KEYS);
@@ -372,7 +375,10 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         const int idx = wbase + i * 32 + lane;
-        dr[i] = (FULL || idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
+        if constexpr (DIGIT == DIGIT_VALUE)
+          dr[i] = (FULL || idx < tile_n) ? ((uint32_t(sv[idx]) >> shift) & uint32_t(RADIX - 1)) : uint32_t(RADIX);
+        else
+          dr[i] = (FULL || idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
       }
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
