@@ -174,6 +174,23 @@ def cpu_oracle_rate(k64: np.ndarray, k32: np.ndarray, sample: int, threads: int)
     return nbytes / dt / 1e9, dt
 
 
+def job_ms(local_ms, world, device=None):
+    """Job time: the slowest rank's time (max over ranks; barrier-synchronised
+    steps), all-reduced so every rank holds it."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbps(world, bytes_per_rank_step, steps, total_ms):
+    """Whole-job throughput: every rank's bytes over the job time (weak scaling)."""
+    return world * bytes_per_rank_step * steps / (total_ms / 1e3) / 1e9
+
+
 def base_line(args, world, cfg):
     return {"metric": METRIC, "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -306,13 +323,9 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
 
-    total_ms = sum(call_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_ms(sum(call_ms), world, dev)
     step_bytes = 24 * n
-    value = world * step_bytes * args.steps / (total_ms / 1e3) / 1e9
+    value = job_gbps(world, step_bytes, args.steps, total_ms)
 
     # dominant kernel: onesweep_pass (digit passes)
     peak, peak_kind = load_peaks()
