@@ -4,6 +4,8 @@
 
 #include <type_traits>
 
+#include <atomic>
+
 #include "internal.h"
 #include "learned.cuh"
 #include "onesweep.cuh"
@@ -11,14 +13,16 @@
 namespace ak {
 
 int device_sm_count() {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64];  // zero-initialised (static storage); one value per device
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  if (dev >= 0 && dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c) return c;
+  }
   int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms <= 0) sms = 152;
-  if (dev >= 0 && dev < 64) cache[dev] = sms;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  if (dev >= 0 && dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
   return sms;
 }
 

@@ -175,15 +175,17 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
     float tot = 0.f;
     bool ok = true;
     for (int rep = 0; rep < 4 && ok; ++rep) {  // one warm-up, three timed
-      cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st);
-      if (vbytes) cudaMemcpyAsync(d_vals, copy_v, vbytes, cudaMemcpyDeviceToDevice, st);
-      cudaEventRecord(e0, st);
+      if (cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          (vbytes && cudaMemcpyAsync(d_vals, copy_v, vbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) ||
+          cudaEventRecord(e0, st) != cudaSuccess) {
+        ok = false;
+        break;
+      }
       ak_status s = AK_OK;
       if (op == AK_OP_SORT) s = ak_sort(d_keys, n, kd, order, d_temp, need, stream, &o);
       else if (op == AK_OP_SORTPERM) s = ak_sortperm(d_keys, d_perm, n, kd, order, d_temp, need, stream, &o);
       else s = ak_sort_pairs(d_keys, d_vals, val_bytes, n, kd, order, d_temp, need, stream, &o);
-      cudaEventRecord(e1, st);
-      if (s != AK_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      if (s != AK_OK || cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
         ok = false;
         break;
       }
@@ -198,8 +200,9 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
     }
   }
   // leave the inputs as they were
-  cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st);
-  if (vbytes) cudaMemcpyAsync(d_vals, copy_v, vbytes, cudaMemcpyDeviceToDevice, st);
+  if (cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      (vbytes && cudaMemcpyAsync(d_vals, copy_v, vbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess))
+    result = AK_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) result = AK_ERR_CUDA;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

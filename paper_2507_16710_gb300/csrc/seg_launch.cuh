@@ -67,8 +67,10 @@ cudaError_t seg_run(const SegCall &c) {
       std::swap(src_v, dst_v);
     }
     if (src_k != a.keys) {  // an odd number of rounds: the result is in the workspace copy
-      cudaMemcpyAsync(a.keys, src_k, size_t(c.n) * sizeof(U), cudaMemcpyDeviceToDevice, c.stream);
-      if (HAS_V) cudaMemcpyAsync(a.vals, src_v, size_t(c.n) * sizeof(V), cudaMemcpyDeviceToDevice, c.stream);
+      e = cudaMemcpyAsync(a.keys, src_k, size_t(c.n) * sizeof(U), cudaMemcpyDeviceToDevice, c.stream);
+      if (e == cudaSuccess && HAS_V)
+        e = cudaMemcpyAsync(a.vals, src_v, size_t(c.n) * sizeof(V), cudaMemcpyDeviceToDevice, c.stream);
+      if (e != cudaSuccess) return e;
     }
   }
   return cudaGetLastError();
