@@ -181,6 +181,29 @@ def test_segmented_equals_per_segment_sort():
         assert np.array_equal(got[a:b], a + oracle.sortperm(keys[a:b]))
 
 
+@pytest.mark.parametrize("desc", [False, True])
+def test_segmented_matches_numpy_per_segment(desc):
+    """Independent of the merge sort: per segment, numpy's stable argsort of
+    unsigned keys (descending: of their bitwise complement, which reverses the
+    order and keeps ties in input order); equal keys on both sides of a segment
+    boundary must not mix."""
+    off = synth.lognormal_segments(300, seed=22, median=40.0, max_len=3000)
+    n = int(off[-1])
+    keys = (synth.splitmix64(23, n) % np.uint64(7)).astype(np.uint32)  # heavy ties everywhere
+    got = oracle.sortperm_segmented(keys, off, "descending" if desc else "ascending")
+    for s in range(off.size - 1):
+        a, b = int(off[s]), int(off[s + 1])
+        seg = ~keys[a:b] if desc else keys[a:b]
+        assert np.array_equal(got[a:b], a + np.argsort(seg, kind="stable"))
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.uint32, np.uint64])
+def test_descending_matches_numpy_on_complement(dtype):
+    """Descending stable order of unsigned keys is numpy's stable argsort of ~k."""
+    keys = synth.random_keys(40000, dtype, seed=6, mode="dups")
+    assert np.array_equal(oracle.sortperm(keys, "descending"), np.argsort(~keys, kind="stable"))
+
+
 def test_segmented_rejects_bad_offsets():
     keys = np.arange(10, dtype=np.int32)
     with pytest.raises(RuntimeError):
