@@ -74,7 +74,11 @@ typedef enum ak_path {
                              stable merge-path rounds (mid-size n) */
 } ak_path;
 
-/* Optional tuning knobs.  Pass NULL for defaults; zero fields mean "default". */
+/* Optional tuning knobs.  Pass NULL for defaults; zero fields mean "default".
+ * A field outside its documented range (unknown path, tile configuration or
+ * debug flag, bucket_bits not 0 or 8..16, train_steps below -1, a nonzero
+ * reserved word) makes the call return AK_ERR_INVALID_ARG with nothing
+ * enqueued. */
 typedef struct ak_options {
     int32_t path;          /* ak_path */
     int32_t tile_config;   /* digit-pass variant, 0 = default (1), else 1..AK_TILE_CONFIGS:

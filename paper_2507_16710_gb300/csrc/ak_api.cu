@@ -94,11 +94,20 @@ static RadixLayout radix_layout(int op, int64_t n, int key_bytes, int val_bytes,
   return L;
 }
 
-static ak_options resolve_options(const ak_options *opt) {
-  ak_options o{};
-  if (opt) o = *opt;
-  if (o.timeout_ns == 0) o.timeout_ns = 1000000000ull;
-  return o;
+// Copies the caller's options (or the defaults) into *o; false when a field is
+// out of its documented range.
+static bool resolve_options(const ak_options *opt, ak_options *o) {
+  *o = ak_options{};
+  if (opt) *o = *opt;
+  if (o->path < AK_PATH_AUTO || o->path > AK_PATH_MERGE) return false;
+  if (o->tile_config < 0 || o->tile_config > AK_TILE_CONFIGS) return false;
+  if (o->bucket_bits != 0 && (o->bucket_bits < 8 || o->bucket_bits > 16)) return false;
+  if (o->train_steps < -1) return false;
+  if (o->debug_flags & ~(AK_DEBUG_SKIP_FIRST_TILE | AK_DEBUG_NO_PREFETCH)) return false;
+  for (int r : o->reserved)
+    if (r != 0) return false;
+  if (o->timeout_ns == 0) o->timeout_ns = 1000000000ull;
+  return true;
 }
 
 // AK_PATH_AUTO with no explicit tile configuration takes the autotuned choice.
@@ -507,7 +516,8 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
   if (op == AK_OP_SORT_PAIRS && val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8)
     return AK_ERR_INVALID_ARG;
   if (op == AK_OP_SORT_SEGMENTED && nseg < 0) return AK_ERR_INVALID_ARG;
-  ak_options o = resolve_options(opt);
+  ak_options o;
+  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   if (op != AK_OP_SORT_SEGMENTED) apply_tuning(op, kd, n, val_bytes, o);
   *bytes = temp_for(op, n, ki.bytes, val_bytes, nseg, o);
   return AK_OK;
@@ -520,7 +530,8 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_
   if (n == 0) return AK_OK;
   if (!d_keys || !aligned(d_keys, ki.bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  ak_options o = resolve_options(opt);
+  ak_options o;
+  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   apply_tuning(AK_OP_SORT, kd, n, 0, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORT, n, ki.bytes, 0, o);
@@ -540,7 +551,8 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
   if (n > int64_t(0xFFFFFFFFll)) return AK_ERR_INDEX_OVERFLOW;
   if (!d_keys || !d_perm || !aligned(d_keys, ki.bytes) || !aligned(d_perm, 4)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  ak_options o = resolve_options(opt);
+  ak_options o;
+  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   apply_tuning(AK_OP_SORTPERM, kd, n, 4, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORTPERM, n, ki.bytes, 4, o);
@@ -560,7 +572,8 @@ ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak
   if (n == 0) return AK_OK;
   if (!d_keys || !d_vals || !aligned(d_keys, ki.bytes) || !aligned(d_vals, val_bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  ak_options o = resolve_options(opt);
+  ak_options o;
+  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   apply_tuning(AK_OP_SORT_PAIRS, kd, n, val_bytes, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORT_PAIRS, n, ki.bytes, val_bytes, o);
@@ -583,7 +596,8 @@ ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg
   if (n > int64_t(0xFFFFFFFFll) || nseg > int64_t(0xFFFFFFFFll)) return AK_ERR_UNSUPPORTED;
   if (!d_keys || !d_offsets || !aligned(d_keys, ki.bytes) || !aligned(d_offsets, 8)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  (void)opt;
+  ak_options o;  // the segmented sort has no options of its own; malformed ones are still refused
+  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   return run_seg(AK_OP_SORT_SEGMENTED, d_keys, d_offsets, nseg, n, nullptr, nullptr, 0, ki, order, d_temp,
                  temp_bytes, reinterpret_cast<cudaStream_t>(stream));
 }

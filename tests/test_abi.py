@@ -62,6 +62,28 @@ def test_autotune_workspace_query(lib):
     assert lib.ak_autotune_temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64, 0, None) == 1
 
 
+def test_options_out_of_range_are_refused(lib):
+    """Every documented option range is enforced at the boundary (host only)."""
+    import paper_2507_16710_gb300 as ak
+    out = ctypes.c_size_t(0)
+
+    def query(**fields):
+        o = ak.Options()
+        for k, v in fields.items():
+            setattr(o, k, v)
+        return lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 1 << 20, ak.AK_F64, 0, 0, ctypes.byref(o), ctypes.byref(out))
+
+    for good in ({}, {"path": ak.AK_PATH_MERGE}, {"tile_config": 3}, {"bucket_bits": 8}, {"bucket_bits": 16},
+                 {"train_steps": -1}, {"debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE | 2}, {"timeout_ns": 5}):
+        assert query(**good) == 0, good
+    for bad in ({"path": 5}, {"path": -1}, {"tile_config": 4}, {"bucket_bits": 7}, {"bucket_bits": 17},
+                {"train_steps": -2}, {"debug_flags": 4}):
+        assert query(**bad) == 1, bad
+    o = ak.Options()
+    o.reserved[2] = 1
+    assert lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 10, ak.AK_U32, 0, 0, ctypes.byref(o), ctypes.byref(out)) == 1
+
+
 def test_host_side_argument_checks(lib):
     import paper_2507_16710_gb300 as ak
     out = ctypes.c_size_t(0)
