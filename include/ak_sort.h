@@ -78,7 +78,8 @@ typedef enum ak_path {
  * A field outside its documented range (unknown path, tile configuration or
  * debug flag, bucket_bits not 0 or 8..16, train_steps below -1, a nonzero
  * reserved word) makes the call return AK_ERR_INVALID_ARG with nothing
- * enqueued. */
+ * enqueued; the options are checked before the n = 0 early return, so an
+ * empty call with malformed options is refused too. */
 typedef struct ak_options {
     int32_t path;          /* ak_path */
     int32_t tile_config;   /* digit-pass variant, 0 = default (1), else 1..AK_TILE_CONFIGS:

@@ -526,12 +526,11 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
 ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_temp, size_t temp_bytes,
                   ak_stream_t stream, const ak_options *opt) {
   KeyInfo ki;
-  if (n < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  ak_options o;
+  if (n < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   if (n == 0) return AK_OK;
   if (!d_keys || !aligned(d_keys, ki.bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  ak_options o;
-  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   apply_tuning(AK_OP_SORT, kd, n, 0, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORT, n, ki.bytes, 0, o);
@@ -546,13 +545,12 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_
 ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
                       void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt) {
   KeyInfo ki;
-  if (n < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  ak_options o;
+  if (n < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   if (n == 0) return AK_OK;
   if (n > int64_t(0xFFFFFFFFll)) return AK_ERR_INDEX_OVERFLOW;
   if (!d_keys || !d_perm || !aligned(d_keys, ki.bytes) || !aligned(d_perm, 4)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  ak_options o;
-  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   apply_tuning(AK_OP_SORTPERM, kd, n, 4, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORTPERM, n, ki.bytes, 4, o);
@@ -567,13 +565,12 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
 ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak_dtype kd, ak_order order,
                         void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt) {
   KeyInfo ki;
-  if (n < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  ak_options o;
+  if (n < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   if (val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8) return AK_ERR_INVALID_ARG;
   if (n == 0) return AK_OK;
   if (!d_keys || !d_vals || !aligned(d_keys, ki.bytes) || !aligned(d_vals, val_bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  ak_options o;
-  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   apply_tuning(AK_OP_SORT_PAIRS, kd, n, val_bytes, o);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int path = choose_path(AK_OP_SORT_PAIRS, n, ki.bytes, val_bytes, o);
@@ -591,13 +588,13 @@ ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg
                             ak_order order, void *d_temp, size_t temp_bytes, ak_stream_t stream,
                             const ak_options *opt) {
   KeyInfo ki;
-  if (n < 0 || nseg < 0 || !key_info(kd, &ki) || !valid_order(order)) return AK_ERR_INVALID_ARG;
+  ak_options o;  // the segmented sort has no options of its own; malformed ones are still refused
+  if (n < 0 || nseg < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o))
+    return AK_ERR_INVALID_ARG;
   if (n == 0 || nseg == 0) return AK_OK;
   if (n > int64_t(0xFFFFFFFFll) || nseg > int64_t(0xFFFFFFFFll)) return AK_ERR_UNSUPPORTED;
   if (!d_keys || !d_offsets || !aligned(d_keys, ki.bytes) || !aligned(d_offsets, 8)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
-  ak_options o;  // the segmented sort has no options of its own; malformed ones are still refused
-  if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   return run_seg(AK_OP_SORT_SEGMENTED, d_keys, d_offsets, nseg, n, nullptr, nullptr, 0, ki, order, d_temp,
                  temp_bytes, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -82,6 +82,14 @@ def test_options_out_of_range_are_refused(lib):
     o = ak.Options()
     o.reserved[2] = 1
     assert lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 10, ak.AK_U32, 0, 0, ctypes.byref(o), ctypes.byref(out)) == 1
+    # malformed options are refused even by the n = 0 no-op of every entry point (no pointer touched)
+    assert lib.ak_sort(None, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
+    assert lib.ak_sortperm(None, None, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
+    assert lib.ak_sort_pairs(None, None, 4, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
+    assert lib.ak_sort_segmented(None, None, 0, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
+    o.reserved[2] = 0
+    assert lib.ak_sort(None, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 0
+    assert lib.ak_sort_segmented(None, None, 0, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 0
 
 
 def test_host_side_argument_checks(lib):
