@@ -6,7 +6,8 @@ never calls it.
 
 ``ak_oracle.c`` is a plain top-down stable merge sort under Julia ``isless`` (the
 sort, sortperm and by-key sort of Sec. II-B, used as the rank-local sort of the
-sample sort in Sec. IV-A).  ``learned.py`` restates the learned-CDF model in
+sample sort in Sec. IV-A), and a textbook bisection for the binary searches of
+Sec. II-B (searchsortedfirst / searchsortedlast).  ``learned.py`` restates the learned-CDF model in
 float64 numpy.  This module compiles the C file with gcc on first use and wraps
 it with ctypes over numpy arrays.
 """
@@ -57,9 +58,10 @@ def _load():
             lib.oracle_sortperm_segmented.argtypes = [p, p, i64, i64, i32, i32, p]
             lib.oracle_gather.argtypes = [p, p, i64, i32, p]
             lib.oracle_isless_pairs.argtypes = [p, p, i64, i32, p]
+            lib.oracle_searchsorted.argtypes = [p, i64, p, i64, i32, i32, i32, p]
             for f in (lib.oracle_sortperm, lib.oracle_sortperm_threaded,
                       lib.oracle_sortperm_segmented, lib.oracle_gather,
-                      lib.oracle_isless_pairs):
+                      lib.oracle_isless_pairs, lib.oracle_searchsorted):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -141,3 +143,22 @@ def isless(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     if _load().oracle_isless_pairs(_ptr(a), _ptr(b), a.size, _code(a), _ptr(out)):
         raise RuntimeError("oracle_isless_pairs failed")
     return out.astype(bool)
+
+
+def searchsorted(v: np.ndarray, x: np.ndarray, side: str = "first", order="ascending") -> np.ndarray:
+    """Binary search of Sec. II-B over a v already in the order's sequence.
+
+    side 'first': index of the first v element not coming before x (n if none);
+    side 'last' : index of the last v element x does not come before (-1 if none).
+    Both 0-based (Julia's searchsortedfirst / searchsortedlast minus one), int64.
+    """
+    vv = np.ascontiguousarray(v)
+    xx = np.ascontiguousarray(x, dtype=vv.dtype)
+    if side not in ("first", "last"):
+        raise ValueError(side)
+    out = np.empty(xx.size, dtype=np.int64)
+    rc = _load().oracle_searchsorted(_ptr(vv), vv.size, _ptr(xx), xx.size, _code(vv), _desc(order),
+                                     0 if side == "first" else 1, _ptr(out))
+    if rc:
+        raise RuntimeError(f"oracle_searchsorted failed ({rc})")
+    return out

@@ -19,6 +19,11 @@
  * Julia isless on integers is <.  On IEEE floats: every NaN compares after every
  * non-NaN and all NaNs are equivalent; -0.0 comes before +0.0; otherwise <.
  *
+ *   searchsortedfirst / searchsortedlast (Sec. II-B, binary search) -> for a v
+ *   already in the order's sequence, the 0-based index of the first element of
+ *   v that does not come before x, and of the last element that x does not come
+ *   before (Julia's 1-based results minus one).
+ *
  * How: a textbook top-down merge sort on an index array.  The merge takes the
  * right element only when it is strictly less than the left one, so ties keep
  * input order.  A threaded variant sorts equal chunks in parallel and merges
@@ -55,19 +60,24 @@ static int isless_float(float a, float b) {
     return 0;
 }
 
-/* isless(key[i], key[j]) */
-static int key_isless(const oracle_ctx *c, int64_t i, int64_t j) {
-    switch (c->dtype) {
-    case OD_U16: return ((const uint16_t *)c->keys)[i] < ((const uint16_t *)c->keys)[j];
-    case OD_I16: return ((const int16_t *)c->keys)[i] < ((const int16_t *)c->keys)[j];
-    case OD_U32: return ((const uint32_t *)c->keys)[i] < ((const uint32_t *)c->keys)[j];
-    case OD_I32: return ((const int32_t *)c->keys)[i] < ((const int32_t *)c->keys)[j];
-    case OD_U64: return ((const uint64_t *)c->keys)[i] < ((const uint64_t *)c->keys)[j];
-    case OD_I64: return ((const int64_t *)c->keys)[i] < ((const int64_t *)c->keys)[j];
-    case OD_F32: return isless_float(((const float *)c->keys)[i], ((const float *)c->keys)[j]);
-    case OD_F64: return isless_double(((const double *)c->keys)[i], ((const double *)c->keys)[j]);
+/* isless(a[i], b[j]) for keys of one dtype held in two arrays */
+static int isless_at(int dtype, const void *a, int64_t i, const void *b, int64_t j) {
+    switch (dtype) {
+    case OD_U16: return ((const uint16_t *)a)[i] < ((const uint16_t *)b)[j];
+    case OD_I16: return ((const int16_t *)a)[i] < ((const int16_t *)b)[j];
+    case OD_U32: return ((const uint32_t *)a)[i] < ((const uint32_t *)b)[j];
+    case OD_I32: return ((const int32_t *)a)[i] < ((const int32_t *)b)[j];
+    case OD_U64: return ((const uint64_t *)a)[i] < ((const uint64_t *)b)[j];
+    case OD_I64: return ((const int64_t *)a)[i] < ((const int64_t *)b)[j];
+    case OD_F32: return isless_float(((const float *)a)[i], ((const float *)b)[j]);
+    case OD_F64: return isless_double(((const double *)a)[i], ((const double *)b)[j]);
     }
     return 0;
+}
+
+/* isless(key[i], key[j]) */
+static int key_isless(const oracle_ctx *c, int64_t i, int64_t j) {
+    return isless_at(c->dtype, c->keys, i, c->keys, j);
 }
 
 /* the order's strict "comes before": isless, or isless with operands swapped */
@@ -218,5 +228,36 @@ int oracle_isless_pairs(const void *a, const void *b, int64_t n, int dtype, uint
         out[i] = (uint8_t)key_isless(&c, 0, 1);
     }
     free(buf);
+    return 0;
+}
+
+/* Binary search, Sec. II-B (searchsortedfirst / searchsortedlast), over keys
+ * v[0..n) that are already in the order's sequence (isless ascending, or its
+ * reverse for descending).  For every query x[i]:
+ *   side 0: out[i] = index of the first v element that does not come before
+ *           x[i], n if there is none (Julia's searchsortedfirst minus one);
+ *   side 1: out[i] = index of the last v element that x[i] does not come
+ *           before, -1 if there is none (Julia's searchsortedlast minus one).
+ * Textbook bisection on [lo, hi): the predicate "v[mid] comes before x" (side
+ * 0) or "x does not come before v[mid]" (side 1) holds on a prefix of a sorted
+ * v, and lo ends at the length of that prefix. */
+int oracle_searchsorted(const void *v, int64_t n, const void *x, int64_t m, int dtype,
+                        int descending, int side, int64_t *out) {
+    if (n < 0 || m < 0 || dtype < 0 || dtype >= OD_COUNT || (side != 0 && side != 1)) return -1;
+    if ((n > 0 && !v) || (m > 0 && (!x || !out))) return -1;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            int in_prefix;
+            if (side == 0)   /* v[mid] before x */
+                in_prefix = descending ? isless_at(dtype, x, i, v, mid) : isless_at(dtype, v, mid, x, i);
+            else             /* x not before v[mid] */
+                in_prefix = !(descending ? isless_at(dtype, v, mid, x, i) : isless_at(dtype, x, i, v, mid));
+            if (in_prefix) lo = mid + 1;
+            else hi = mid;
+        }
+        out[i] = side == 0 ? lo : lo - 1;
+    }
     return 0;
 }

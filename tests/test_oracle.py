@@ -228,3 +228,77 @@ def test_generators_are_reproducible_and_shaped():
     top = synth.fmix32(np.array([0], dtype=np.uint32))[0]
     frac = (z == top).mean()
     assert 0.04 < frac < 0.08   # ~5.75% of keys equal the top rank
+
+
+# ------------------------------------------------------------ binary search
+# Sec. II-B: searchsortedfirst / searchsortedlast (0-based here: Julia's value
+# minus one).  Pinned against the brute-force count that defines them, numpy's
+# searchsorted where isless is plain <, and hand-derived special values.
+
+def _order_before(a, b, desc):
+    """a comes strictly before b in the order (isless, or reversed isless)."""
+    return oracle.isless(b, a) if desc else oracle.isless(a, b)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("desc", [False, True])
+def test_searchsorted_brute_force_count(dtype, desc):
+    order = "descending" if desc else "ascending"
+    keys = np.concatenate([synth.random_keys(150, dtype, seed=71, mode="dups"), synth.special_values(dtype)])
+    v = oracle.sort(keys, order)
+    x = np.concatenate([synth.random_keys(60, dtype, seed=72, mode="dups"), synth.random_keys(20, dtype, seed=73),
+                        synth.special_values(dtype)])
+    first, last = oracle.searchsorted(v, x, "first", order), oracle.searchsorted(v, x, "last", order)
+    for i in range(x.size):
+        xi = np.full(v.size, x[i], dtype=v.dtype)
+        n_before = int(np.count_nonzero(_order_before(v, xi, desc)))       # v[j] before x
+        n_not_after = int(np.count_nonzero(~_order_before(xi, v, desc)))  # x not before v[j]
+        assert first[i] == n_before, (i, x[i])
+        assert last[i] == n_not_after - 1, (i, x[i])
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float64, np.int16])
+def test_searchsorted_matches_numpy(dtype):
+    """Without NaN or -0.0, isless is <: numpy's searchsorted gives both sides;
+    a descending v is the ascending one reversed (counts from the other end)."""
+    raw = synth.random_keys(5000, dtype, seed=74, mode="narrow")
+    if np.dtype(dtype).kind == "f":
+        raw = np.abs(raw)
+    asc = np.sort(raw, kind="stable")
+    x = np.concatenate([raw[:700], synth.random_keys(300, dtype, seed=75, mode="narrow")])
+    if np.dtype(dtype).kind == "f":
+        x = np.abs(x)
+    n = asc.size
+    assert np.array_equal(oracle.searchsorted(asc, x, "first"), np.searchsorted(asc, x, "left"))
+    assert np.array_equal(oracle.searchsorted(asc, x, "last"), np.searchsorted(asc, x, "right") - 1)
+    desc = asc[::-1].copy()
+    assert np.array_equal(oracle.searchsorted(desc, x, "first", "descending"), n - np.searchsorted(asc, x, "right"))
+    assert np.array_equal(oracle.searchsorted(desc, x, "last", "descending"),
+                          n - np.searchsorted(asc, x, "left") - 1)
+
+
+def test_searchsorted_special_values_by_hand():
+    """Worked from Julia isless: -0.0 before 0.0, all NaNs tie after +Inf."""
+    v = np.array([-np.inf, -1.0, -0.0, -0.0, 0.0, 1.0, np.inf, np.nan, np.nan])
+    x = np.array([-0.0, 0.0, np.nan, -np.inf, 5.0, -2.0])
+    assert oracle.searchsorted(v, x, "first").tolist() == [2, 4, 7, 0, 6, 1]
+    assert oracle.searchsorted(v, x, "last").tolist() == [3, 4, 8, 0, 5, 0]
+    vd = v[::-1].copy()  # the descending sequence (rev=true)
+    assert oracle.searchsorted(vd, x, "first", "descending").tolist() == [5, 4, 0, 8, 3, 8]
+    assert oracle.searchsorted(vd, x, "last", "descending").tolist() == [6, 4, 1, 8, 2, 7]
+    # negative NaN payloads tie with positive ones
+    neg_nan = np.array([0xFFF8000000000001], dtype=np.uint64).view(np.float64)
+    assert oracle.searchsorted(v, neg_nan, "first").tolist() == [7]
+    assert oracle.searchsorted(v, neg_nan, "last").tolist() == [8]
+
+
+def test_searchsorted_empty_and_degenerate():
+    x = np.array([3, 1, 7], dtype=np.int32)
+    empty = np.array([], dtype=np.int32)
+    assert oracle.searchsorted(empty, x, "first").tolist() == [0, 0, 0]
+    assert oracle.searchsorted(empty, x, "last").tolist() == [-1, -1, -1]
+    assert oracle.searchsorted(np.array([1, 3, 5], dtype=np.int32), empty).size == 0
+    same = np.full(10, 4, dtype=np.int32)  # all equal: first = 0 or n, last = -1 or n - 1
+    q = np.array([3, 4, 5], dtype=np.int32)
+    assert oracle.searchsorted(same, q, "first").tolist() == [0, 0, 10]
+    assert oracle.searchsorted(same, q, "last").tolist() == [-1, 9, 9]
