@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=FULL_N, help="keys per array (default: the full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted"],
                     help="c2 (default): the headline line; the others print their own lines")
     ap.add_argument("--segments", type=int, default=65536, help="c4: number of segments")
     return ap.parse_args()
@@ -600,6 +600,65 @@ def run_workload(args):
                "learned_ms": round(ml, 3), "learned_path_taken": info["path"] == ak.AK_PATH_LEARNED,
                "overfull_frac": round(info["overfull_keys"] / n, 4),
                "keys_plus_values_GBps_plain": round(2 * gp, 3), "keys_plus_values_GBps_learned": round(2 * gl, 3)})
+    elif args.workload == "searchsorted":
+        run_searchsorted(args, torch, ak, synth, dev, stream, flush, peak)
+
+
+def run_searchsorted(args, torch, ak, synth, dev, stream, flush, peak):
+    """Batched binary search (Sec. II-B): 2^26 float64 queries against 2^27
+    ascending float64 keys (1 GiB, 25% equal neighbours), once with queries
+    uniform over the keys' range (independent random searches) and once with
+    the queries themselves ascending.  value = queries per second over the
+    first and last searches of the random queries."""
+    import oracle
+    n, m = 1 << 27, 1 << 26
+    v = synth.ascending_f64(n, seed=40)
+    xr = synth.u01_f64(92, m) * v[-1]
+    xs = synth.ascending_f64(m, seed=93)
+    xs *= v[-1] / xs[-1]
+    tv = torch.from_numpy(v).to(dev)
+    out = torch.empty(m, dtype=torch.int64, device=dev)
+    lib = ak.load()
+    res, ms_random = {}, 0.0
+    for qname, xh in (("random", xr), ("ascending", xs)):
+        tx = torch.from_numpy(xh).to(dev)
+        for side in ("first", "last"):
+            f = lib.ak_searchsortedfirst if side == "first" else lib.ak_searchsortedlast
+
+            def call(f=f, tx=tx):
+                rc = f(tv.data_ptr(), n, tx.data_ptr(), m, ak.AK_F64, 0, out.data_ptr(), stream.cuda_stream)
+                if rc:
+                    raise ak.AkError(rc, "searchsorted")
+
+            ms = _timed(torch, stream, flush, lambda: None, call, args.warmup, args.steps)
+            res[f"{qname}_{side}"] = {"ms": round(ms, 4), "Gq_per_s": round(m / (ms / 1e3) / 1e9, 3)}
+            if qname == "random":
+                ms_random += ms
+        del tx
+    value = 2 * m / (ms_random / 1e3) / 1e9
+    # algorithmic bytes: each query read (8 B) and its index written (8 B)
+    achieved = 2 * m * 16 / (ms_random / 1e3) / 1e9
+    table = 2048  # pivot keys per CTA for 8-byte keys
+    steps = int(np.ceil(np.log2(n / (table + 1))))
+    cpu = None
+    if not args.no_cpu:
+        sample = 1 << 20
+        t0 = time.perf_counter()
+        oracle.searchsorted(v, xr[:sample], "first")
+        oracle.searchsorted(v, xr[:sample], "last")
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(2 * sample / dt / 1e9, 5), "unit": "G queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"first and last of the first {sample:,} random queries against all {n:,} keys"}
+    _line(args, f"{m:,} float64 queries against {n:,} ascending float64 keys (1 GiB), searchsortedfirst + "
+          "searchsortedlast", value,
+          {"metric": "searchsorted queries/s (device-timed, 1 GB300)", "unit": "G queries/s", "dtype": "f64",
+           "results": res,
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "note": f"latency bound: after the shared-memory table each query makes {steps} "
+                                "dependent loads into the 1 GiB key array; bytes counted are the query "
+                                "read and the index write (16 B per query)"},
+           "cpu_baseline": cpu})
 
 
 def main():

@@ -200,6 +200,36 @@ ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg
 #define AK_STATIC_SCRATCH_BYTES (32u << 20)
 ak_status ak_sort_static_scratch(void *d_keys, int64_t n, ak_dtype kd, ak_order order, ak_stream_t stream);
 
+/* ------------------------------------------------------------------------- */
+/* Binary search (Sec. II-B, searchsortedfirst / searchsortedlast).          */
+
+/*
+ * For each of m query keys d_x[i], its place among the n keys d_v, which must
+ * already be in `order`'s sequence (as ak_sort leaves them with that order).
+ * "Comes before" is the sort's order: Julia isless, or its reverse for
+ * AK_DESCENDING (all NaNs equivalent, -0.0 before +0.0).  Results are 0-based:
+ *   ak_searchsortedfirst: d_out[i] = index of the first d_v element that does
+ *     not come before d_x[i], n if none (Julia's searchsortedfirst minus one):
+ *     the insertion index in front of every key equivalent to d_x[i];
+ *   ak_searchsortedlast:  d_out[i] = index of the last d_v element that d_x[i]
+ *     does not come before, -1 if none (Julia's searchsortedlast minus one);
+ *     plus one it is the insertion index behind every equivalent key.
+ * d_v (n keys) and d_x (m keys) are device arrays of dtype kd aligned to the
+ * key size; they may be the same array.  d_out is m int64 on the device,
+ * 8-byte aligned, overlapping neither.  Both functions only enqueue one kernel
+ * on `stream`: no workspace, no allocation, no synchronisation (graph
+ * capturable).  If d_v is not in order the results are unspecified but stay in
+ * [0, n] (first) or [-1, n - 1] (last), and nothing outside d_v[0, n) is read.
+ * n = 0 is valid (every result 0, or -1); m = 0 enqueues nothing.
+ * Returns AK_ERR_INVALID_ARG for a negative n or m, a bad dtype or order, or a
+ * NULL or misaligned pointer that would be read or written; AK_ERR_CUDA if the
+ * launch fails.
+ */
+ak_status ak_searchsortedfirst(const void *d_v, int64_t n, const void *d_x, int64_t m, ak_dtype kd,
+                               ak_order order, int64_t *d_out, ak_stream_t stream);
+ak_status ak_searchsortedlast(const void *d_v, int64_t n, const void *d_x, int64_t m, ak_dtype kd,
+                              ak_order order, int64_t *d_out, ak_stream_t stream);
+
 /*
  * Synchronises `stream` and returns the device-side status of the last call that
  * used d_temp (AK_OK, or e.g. AK_ERR_TIMEOUT).  AK_ERR_CUDA if the copy fails.

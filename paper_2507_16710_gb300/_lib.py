@@ -32,7 +32,7 @@ EXPORTED = (
     "ak_status_check", "ak_last_info", "ak_status_string", "ak_learned_knots",
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
     "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
-    "ak_segment_capacity", "ak_autotune_temp_bytes",
+    "ak_segment_capacity", "ak_autotune_temp_bytes", "ak_searchsortedfirst", "ak_searchsortedlast",
 )
 
 
@@ -97,6 +97,8 @@ def load() -> ctypes.CDLL:
                 "ak_sort_static_scratch": ([p, i64, i32, i32, p], i32),
                 "ak_segment_capacity": ([i32, i32], i64),
                 "ak_autotune_temp_bytes": ([i32, i64, i32, i32, ctypes.POINTER(sz)], i32),
+                "ak_searchsortedfirst": ([p, i64, p, i64, i32, i32, p, p], i32),
+                "ak_searchsortedlast": ([p, i64, p, i64, i32, i32, p, p], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -245,6 +247,38 @@ def ak_sort_segmented(keys: torch.Tensor, offsets: torch.Tensor, order="ascendin
                                     order_code(order), temp.data_ptr(), temp.numel(),
                                     _stream_ptr(stream), _opts(options)), "ak_sort_segmented")
     return keys
+
+
+def _searchsorted(name: str, v: torch.Tensor, x: torch.Tensor, order, out, stream, unsigned: bool):
+    _contig_cuda(v, "v")
+    _contig_cuda(x, "x")
+    if x.dtype != v.dtype:
+        raise TypeError(f"queries ({x.dtype}) and sorted keys ({v.dtype}) differ in dtype")
+    kd = dtype_code(v, unsigned)
+    if out is None:
+        out = torch.empty(x.numel(), dtype=torch.int64, device=x.device)
+    else:
+        _contig_cuda(out, "out")
+        if out.dtype != torch.int64 or out.numel() != x.numel():
+            raise ValueError("out must be an int64 tensor with one element per query")
+    _check(getattr(load(), name)(v.data_ptr(), v.numel(), x.data_ptr(), x.numel(), kd, order_code(order),
+                                 out.data_ptr(), _stream_ptr(stream)), name)
+    return out
+
+
+def ak_searchsortedfirst(v: torch.Tensor, x: torch.Tensor, order="ascending", *, out=None, stream=None,
+                         unsigned: bool = False) -> torch.Tensor:
+    """0-based index of the first element of the sorted `v` not coming before
+    each query (len(v) if none): Julia's searchsortedfirst minus one.  Fills
+    `out` (int64, one per query) when given, else allocates it."""
+    return _searchsorted("ak_searchsortedfirst", v, x, order, out, stream, unsigned)
+
+
+def ak_searchsortedlast(v: torch.Tensor, x: torch.Tensor, order="ascending", *, out=None, stream=None,
+                        unsigned: bool = False) -> torch.Tensor:
+    """0-based index of the last element of the sorted `v` that each query does
+    not come before (-1 if none): Julia's searchsortedlast minus one."""
+    return _searchsorted("ak_searchsortedlast", v, x, order, out, stream, unsigned)
 
 
 def ak_sort_temp_bytes(op: int, n: int, kd: int, val_bytes: int = 0, nseg: int = 0, options=None) -> int:

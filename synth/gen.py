@@ -20,6 +20,10 @@ with the dtypes of Sec. IV and the sizes of Sec. IV-C):
                           median 2,048 clipped to [1, 2^20]
 * ``zipf_mix_u32``        50/50 mix of Zipf(s=1.1, 2^24 ranks, bijectively mixed)
                           and uniform u32
+* ``ascending_f64``       keys already in ascending order by construction (a
+                          running sum of non-negative steps, a fraction of them
+                          zero for runs of equal keys): the sorted input of the
+                          binary searches of Sec. II-B, with no sort involved
 """
 from __future__ import annotations
 
@@ -31,7 +35,7 @@ __all__ = [
     "splitmix64", "u01_f64", "normal_f64", "uniform_u32", "uniform_i64",
     "normal_f32_special", "dist_f64", "F64_DISTS", "lognormal_segments",
     "zipf_mix_u32", "distinct_positions", "fmix32", "special_values",
-    "random_keys",
+    "random_keys", "ascending_f64",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -281,3 +285,20 @@ def random_keys(n: int, dtype, seed: int, mode: str = "bits") -> np.ndarray:
             return (raw % np.uint64(1000)).astype(dt)
         return (1.0 + (raw >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)).astype(dt)
     raise ValueError(mode)
+
+
+def ascending_f64(n: int, seed: int = 40, zero_frac: float = 0.25) -> np.ndarray:
+    """n float64 keys in ascending order by construction: the running sum of
+    steps uniform on [0, 1), a ``zero_frac`` share of them set to 0 (runs of
+    equal keys).  A running sum of non-negative float64 terms never decreases,
+    so no sort is involved; the values are non-negative and finite."""
+    out = np.empty(n, dtype=np.float64)
+    acc = 0.0
+    for lo in range(0, n, _CHUNK):
+        hi = min(n, lo + _CHUNK)
+        step = u01_f64(seed, hi - lo, lo)
+        step[u01_f64(seed + 1, hi - lo, lo) < zero_frac] = 0.0
+        np.cumsum(step, out=out[lo:hi])
+        out[lo:hi] += acc
+        acc = float(out[hi - 1])
+    return out

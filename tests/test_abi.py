@@ -115,6 +115,26 @@ def test_host_side_argument_checks(lib):
     assert lib.ak_status_string(5) == b"device-side wait timed out"
 
 
+def test_searchsorted_host_checks(lib):
+    """Argument checks of the binary search return before any launch."""
+    import paper_2507_16710_gb300 as ak
+    out = ctypes.c_void_p(8192)
+    x, v = ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20)
+    for f in (lib.ak_searchsortedfirst, lib.ak_searchsortedlast):
+        assert f(v, 10, x, 0, ak.AK_F64, 0, None, None) == 0           # m = 0: nothing to do
+        assert f(None, 0, None, 0, ak.AK_F64, 0, None, None) == 0
+        assert f(v, -1, x, 5, ak.AK_F64, 0, out, None) == 1            # negative n
+        assert f(v, 10, x, -5, ak.AK_F64, 0, out, None) == 1           # negative m
+        assert f(v, 10, x, 5, 8, 0, out, None) == 1                    # bad dtype
+        assert f(v, 10, x, 5, ak.AK_F64, 2, out, None) == 1            # bad order
+        assert f(v, 10, None, 5, ak.AK_F64, 0, out, None) == 1         # NULL queries
+        assert f(v, 10, x, 5, ak.AK_F64, 0, None, None) == 1           # NULL output
+        assert f(None, 10, x, 5, ak.AK_F64, 0, out, None) == 1         # NULL keys with n > 0
+        assert f(ctypes.c_void_p(4100), 10, x, 5, ak.AK_F64, 0, out, None) == 1  # misaligned keys
+        assert f(v, 10, ctypes.c_void_p(4098), 5, ak.AK_U32, 0, out, None) == 1  # misaligned queries
+        assert f(v, 10, x, 5, ak.AK_U16, 0, ctypes.c_void_p(8196), None) == 1    # misaligned output
+
+
 def test_autotune_cache_roundtrip_and_auto_sizing(lib, tmp_path):
     """The tuning cache persists as JSON lines, skips malformed lines, and an
     AK_PATH_AUTO workspace query follows a cached choice (no GPU needed)."""
