@@ -15,6 +15,7 @@ are larger than L2 as well.  SM clocks are sampled with nvidia-smi during the
 timed steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       python bench.py --workload c1|c3|c4|c5|searchsorted   (their own lines)
 Under torchrun every rank sorts its own replica of the workload on its own GPU
 (the sort has no exchange step on one node here: replicas, weak scaling).
 """

@@ -7,7 +7,8 @@ never calls it.
 ``ak_oracle.c`` is a plain top-down stable merge sort under Julia ``isless`` (the
 sort, sortperm and by-key sort of Sec. II-B, used as the rank-local sort of the
 sample sort in Sec. IV-A), and a textbook bisection for the binary searches of
-Sec. II-B (searchsortedfirst / searchsortedlast).  ``learned.py`` restates the learned-CDF model in
+Sec. II-B (searchsortedfirst / searchsortedlast) and a left-to-right prefix scan
+for its accumulate.  ``learned.py`` restates the learned-CDF model in
 float64 numpy.  This module compiles the C file with gcc on first use and wraps
 it with ctypes over numpy arrays.
 """
@@ -59,9 +60,10 @@ def _load():
             lib.oracle_gather.argtypes = [p, p, i64, i32, p]
             lib.oracle_isless_pairs.argtypes = [p, p, i64, i32, p]
             lib.oracle_searchsorted.argtypes = [p, i64, p, i64, i32, i32, i32, p]
+            lib.oracle_accumulate.argtypes = [p, i64, i32, i32, i32, p, p]
             for f in (lib.oracle_sortperm, lib.oracle_sortperm_threaded,
                       lib.oracle_sortperm_segmented, lib.oracle_gather,
-                      lib.oracle_isless_pairs, lib.oracle_searchsorted):
+                      lib.oracle_isless_pairs, lib.oracle_searchsorted, lib.oracle_accumulate):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -162,3 +164,38 @@ def searchsorted(v: np.ndarray, x: np.ndarray, side: str = "first", order="ascen
     if rc:
         raise RuntimeError(f"oracle_searchsorted failed ({rc})")
     return out
+
+
+ACCUMULATE_OPS = {"add": 0, "max": 1, "min": 2}
+
+
+def accumulate(x: np.ndarray, op: str = "add", inclusive: bool = True, init=None) -> np.ndarray:
+    """Prefix scan of Sec. II-B (accumulate), left to right from ``init``.
+
+    inclusive: out[i] = init op x[0] op ... op x[i]; exclusive: the same up to
+    x[i-1] (out[0] = init).  op 'add' wraps for integers and is a compensated
+    float64 sum rounded once per output for floats; 'max' / 'min' are Julia's
+    (NaN wins, -0.0 below +0.0).  ``init`` defaults to the op's identity.
+    """
+    xx = np.ascontiguousarray(x)
+    code = ACCUMULATE_OPS[op]
+    if init is None:
+        init = identity(xx.dtype, op)
+    iv = np.array([init], dtype=xx.dtype)
+    out = np.empty_like(xx)
+    rc = _load().oracle_accumulate(_ptr(xx), xx.size, _code(xx), code, 1 if inclusive else 0, _ptr(iv), _ptr(out))
+    if rc:
+        raise RuntimeError(f"oracle_accumulate failed ({rc})")
+    return out
+
+
+def identity(dtype, op: str):
+    """The start value that changes nothing: 0 for add; the dtype's lowest
+    (max) or highest (min) value, -Inf / +Inf for floats."""
+    dt = np.dtype(dtype)
+    if op == "add":
+        return dt.type(0)
+    if dt.kind == "f":
+        return dt.type(-np.inf if op == "max" else np.inf)
+    info = np.iinfo(dt)
+    return dt.type(info.min if op == "max" else info.max)

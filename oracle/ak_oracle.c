@@ -23,6 +23,8 @@
  *   already in the order's sequence, the 0-based index of the first element of
  *   v that does not come before x, and of the last element that x does not come
  *   before (Julia's 1-based results minus one).
+ *   accumulate (Sec. II-B, prefix scan) -> inclusive or exclusive running
+ *   +, max or min from a start value, left to right (details at the function).
  *
  * How: a textbook top-down merge sort on an index array.  The merge takes the
  * right element only when it is strictly less than the left one, so ties keep
@@ -258,6 +260,114 @@ int oracle_searchsorted(const void *v, int64_t n, const void *x, int64_t m, int 
             else hi = mid;
         }
         out[i] = side == 0 ? lo : lo - 1;
+    }
+    return 0;
+}
+
+/* -------------------------------------------------------------- accumulate -- */
+/* Prefix scan, Sec. II-B (accumulate), with a start value `init`:
+ *   inclusive: out[i] = init (+) x[0] (+) ... (+) x[i]
+ *   exclusive: out[i] = init (+) x[0] (+) ... (+) x[i-1]   (out[0] = init)
+ * for (+) one of
+ *   OA_ADD  integer +, wrapping in the key's width (Julia's integer +); float
+ *           +, summed in float64 with Neumaier's compensation (Neumaier 1974,
+ *           "Rundungsfehleranalyse einiger Verfahren zur Summation endlicher
+ *           Summen") and each output rounded once to the key's type -- the
+ *           mathematical prefix sum to well within one rounding.  While the
+ *           compensation is zero the output is the running float64 sum itself
+ *           (so sums of -0.0 stay -0.0); once that running sum is not finite
+ *           (a NaN or an infinity in the prefix, or overflow) the output is
+ *           that running sum;
+ *   OA_MAX  Julia max: NaN if either operand is NaN, +0.0 above -0.0;
+ *   OA_MIN  Julia min: NaN if either operand is NaN, -0.0 below +0.0.
+ * Written strictly left to right, one element at a time. */
+enum { OA_ADD = 0, OA_MAX = 1, OA_MIN = 2 };
+
+static double julia_max(double a, double b) {
+    if (isnan(a)) return a;
+    if (isnan(b)) return b;
+    if (a == b) return signbit(a) ? b : a;   /* max(-0.0, 0.0) = 0.0 */
+    return a > b ? a : b;
+}
+
+static double julia_min(double a, double b) {
+    if (isnan(a)) return a;
+    if (isnan(b)) return b;
+    if (a == b) return signbit(a) ? a : b;   /* min(-0.0, 0.0) = -0.0 */
+    return a < b ? a : b;
+}
+
+static double float_at(int dtype, const void *p, int64_t i) {
+    return dtype == OD_F32 ? (double)((const float *)p)[i] : ((const double *)p)[i];
+}
+
+static void float_put(int dtype, void *p, int64_t i, double v) {
+    if (dtype == OD_F32) ((float *)p)[i] = (float)v;
+    else ((double *)p)[i] = v;
+}
+
+/* integer element i as its raw bits (zero-extended), and as a signed value */
+static uint64_t int_bits(int dtype, const void *p, int64_t i) {
+    switch (dtype) {
+    case OD_U16: case OD_I16: return ((const uint16_t *)p)[i];
+    case OD_U32: case OD_I32: return ((const uint32_t *)p)[i];
+    default: return ((const uint64_t *)p)[i];
+    }
+}
+
+static void int_put(int dtype, void *p, int64_t i, uint64_t bits) {
+    switch (dtype) {
+    case OD_U16: case OD_I16: ((uint16_t *)p)[i] = (uint16_t)bits; break;
+    case OD_U32: case OD_I32: ((uint32_t *)p)[i] = (uint32_t)bits; break;
+    default: ((uint64_t *)p)[i] = bits; break;
+    }
+}
+
+/* a < b on raw bits of one integer dtype, by its signedness */
+static int int_less(int dtype, uint64_t a, uint64_t b) {
+    switch (dtype) {
+    case OD_I16: return (int16_t)a < (int16_t)b;
+    case OD_I32: return (int32_t)a < (int32_t)b;
+    case OD_I64: return (int64_t)a < (int64_t)b;
+    default: return a < b;
+    }
+}
+
+int oracle_accumulate(const void *x, int64_t n, int dtype, int op, int inclusive, const void *init,
+                      void *out) {
+    if (n < 0 || dtype < 0 || dtype >= OD_COUNT || op < OA_ADD || op > OA_MIN || !init) return -1;
+    if (n > 0 && (!x || !out)) return -1;
+    if (dtype == OD_F32 || dtype == OD_F64) {
+        double s = float_at(dtype, init, 0), c = 0.0, plain = s;
+#define OA_VALUE (!isfinite(plain) ? plain : (c == 0.0 ? s : s + c))
+        for (int64_t i = 0; i < n; ++i) {
+            if (!inclusive) float_put(dtype, out, i, OA_VALUE);
+            const double v = float_at(dtype, x, i);
+            if (op == OA_ADD) {
+                const double t = s + v;
+                if (fabs(s) >= fabs(v)) c += (s - t) + v;
+                else c += (v - t) + s;
+                s = t;
+                plain = plain + v;
+            } else {
+                s = op == OA_MAX ? julia_max(s, v) : julia_min(s, v);
+                plain = s;
+            }
+            if (inclusive) float_put(dtype, out, i, OA_VALUE);
+        }
+#undef OA_VALUE
+        return 0;
+    }
+    uint64_t acc = int_bits(dtype, init, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!inclusive) int_put(dtype, out, i, acc);
+        const uint64_t v = int_bits(dtype, x, i);
+        if (op == OA_ADD) acc = acc + v;   /* wraps; int_put keeps the key's width */
+        else if (op == OA_MAX) acc = int_less(dtype, acc, v) ? v : acc;
+        else acc = int_less(dtype, v, acc) ? v : acc;
+        if (dtype == OD_U16 || dtype == OD_I16) acc &= 0xFFFFu;
+        else if (dtype == OD_U32 || dtype == OD_I32) acc &= 0xFFFFFFFFu;
+        if (inclusive) int_put(dtype, out, i, acc);
     }
     return 0;
 }

@@ -302,3 +302,107 @@ def test_searchsorted_empty_and_degenerate():
     q = np.array([3, 4, 5], dtype=np.int32)
     assert oracle.searchsorted(same, q, "first").tolist() == [0, 0, 10]
     assert oracle.searchsorted(same, q, "last").tolist() == [-1, 9, 9]
+
+
+# ------------------------------------------------------------ accumulate
+# Sec. II-B: accumulate (prefix scan), inclusive and exclusive.  Pinned against
+# numpy's cumulative routines where they agree with the definition, exact
+# rational prefix sums (math.fsum), hand-worked Julia max/min facts, and the
+# exclusive = shifted inclusive invariant.
+
+INT_DTYPES = [np.uint16, np.int16, np.uint32, np.int32, np.uint64, np.int64]
+
+
+@pytest.mark.parametrize("dtype", INT_DTYPES)
+def test_accumulate_integers_match_numpy(dtype):
+    """Wrapping + and plain max/min on integers are numpy's cumsum (in the
+    key's width) and maximum/minimum.accumulate."""
+    x = synth.random_keys(3000, dtype, seed=101)
+    assert np.array_equal(oracle.accumulate(x, "add"), np.cumsum(x, dtype=dtype))
+    assert np.array_equal(oracle.accumulate(x, "max"), np.maximum.accumulate(x))
+    assert np.array_equal(oracle.accumulate(x, "min"), np.minimum.accumulate(x))
+    # a start value enters every prefix
+    init = dtype(7)
+    with np.errstate(over="ignore"):
+        want = (np.cumsum(x, dtype=dtype) + init).astype(dtype)
+    assert np.array_equal(oracle.accumulate(x, "add", init=init), want)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("op", ["add", "max", "min"])
+def test_exclusive_is_shifted_inclusive(dtype, op):
+    x = synth.random_keys(500, dtype, seed=102, mode="dups")
+    if np.dtype(dtype).kind == "f":
+        x = x[~np.isnan(x)]
+        x = x[np.isfinite(x)] if op == "add" else x
+    init = oracle.identity(dtype, op)
+    inc = oracle.accumulate(x, op, True, init)
+    exc = oracle.accumulate(x, op, False, init)
+    assert bits_equal(exc[:1], np.array([init], dtype=dtype))
+    assert bits_equal(exc[1:], inc[:-1])
+
+
+def bits_equal(a, b):
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    if a.shape != b.shape:
+        return False
+    u = np.dtype(f"u{a.dtype.itemsize}")
+    return bool(np.array_equal(a.view(u), b.view(u)))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_accumulate_float_add_against_exact_prefix_sums(dtype):
+    """Each output is the exact prefix sum (math.fsum, correctly rounded in
+    float64) rounded to the key's type, to within one float64 rounding before
+    that last step: equal for float32, within 2 ulp for float64.  Mixed signs
+    and magnitudes make a plain float64 running sum visibly worse."""
+    n = 1500
+    u = synth.u01_f64(103, n)
+    mag = np.exp2(np.floor(synth.u01_f64(104, n) * 40) - 20)
+    x = ((u - 0.5) * mag).astype(dtype)
+    got = oracle.accumulate(x, "add")
+    xs = x.astype(np.float64).tolist()
+    exact = np.array([math.fsum(xs[: i + 1]) for i in range(n)])
+    if dtype == np.float32:
+        assert np.array_equal(got, exact.astype(np.float32))
+    else:
+        assert np.all(np.abs(got - exact) <= 2 * np.spacing(np.abs(exact)))
+
+
+def test_accumulate_integer_valued_floats_are_exact():
+    """Sums of small integers are exact in any order: numpy's cumsum agrees bit
+    for bit, and so does the exclusive form from a start value."""
+    x = (synth.splitmix64(105, 4000) % np.uint64(2001)).astype(np.float64) - 1000.0
+    assert np.array_equal(oracle.accumulate(x, "add"), np.cumsum(x))
+    ex = oracle.accumulate(x.astype(np.float32), "add", inclusive=False, init=np.float32(5))
+    assert np.array_equal(ex, np.concatenate([[5.0], 5.0 + np.cumsum(x)[:-1]]).astype(np.float32))
+
+
+def test_accumulate_julia_max_min_and_specials_by_hand():
+    """Julia facts: max(-0.0, 0.0) == 0.0, min(-0.0, 0.0) == -0.0, a NaN operand
+    makes max and min NaN; IEEE: Inf + 1 = Inf, Inf + (-Inf) = NaN, and a sum
+    of negative zeros stays -0.0."""
+    nan, inf = np.nan, np.inf
+    got = oracle.accumulate(np.array([-0.0, 0.0, -0.0]), "max", init=-0.0)
+    assert bits_equal(got, np.array([-0.0, 0.0, 0.0]))
+    got = oracle.accumulate(np.array([0.0, -0.0, 0.0]), "min", init=0.0)
+    assert bits_equal(got, np.array([0.0, -0.0, -0.0]))
+    got = oracle.accumulate(np.array([1.0, nan, 5.0], np.float32), "max")
+    assert got[0] == 1.0 and np.isnan(got[1]) and np.isnan(got[2])
+    got = oracle.accumulate(np.array([3.0, 2.0, nan, -9.0]), "min")
+    assert got[:2].tolist() == [3.0, 2.0] and np.isnan(got[2:]).all()
+    got = oracle.accumulate(np.array([1.0, inf, 2.0, -inf, 3.0]), "add")
+    assert got[:3].tolist() == [1.0, inf, inf] and np.isnan(got[3:]).all()
+    assert bits_equal(oracle.accumulate(np.array([-0.0, -0.0]), "add", init=-0.0), np.array([-0.0, -0.0]))
+    # identities: the lowest / highest value of the type, -Inf / +Inf for floats
+    assert oracle.identity(np.int16, "max") == -32768 and oracle.identity(np.uint32, "min") == 2**32 - 1
+    assert oracle.identity(np.float64, "max") == -inf and oracle.identity(np.float32, "add") == 0
+
+
+def test_accumulate_empty_and_single():
+    for dtype in DTYPES:
+        e = np.array([], dtype=dtype)
+        assert oracle.accumulate(e, "add").size == 0
+        one = synth.random_keys(1, dtype, seed=106, mode="narrow")
+        assert bits_equal(oracle.accumulate(one, "max"), one)
+        assert bits_equal(oracle.accumulate(one, "add", inclusive=False, init=dtype(3)), np.array([3], dtype=dtype))
