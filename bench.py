@@ -15,7 +15,7 @@ are larger than L2 as well.  SM clocks are sampled with nvidia-smi during the
 timed steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-       python bench.py --workload c1|c3|c4|c5|searchsorted   (their own lines)
+       python bench.py --workload c1|c3|c4|c5|searchsorted|accumulate   (their own lines)
 Under torchrun every rank sorts its own replica of the workload on its own GPU
 (the sort has no exchange step on one node here: replicas, weak scaling).
 """
@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=FULL_N, help="keys per array (default: the full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted", "accumulate"],
                     help="c2 (default): the headline line; the others print their own lines")
     ap.add_argument("--segments", type=int, default=65536, help="c4: number of segments")
     return ap.parse_args()
@@ -603,6 +603,49 @@ def run_workload(args):
                "keys_plus_values_GBps_plain": round(2 * gp, 3), "keys_plus_values_GBps_learned": round(2 * gl, 3)})
     elif args.workload == "searchsorted":
         run_searchsorted(args, torch, ak, synth, dev, stream, flush, peak)
+    elif args.workload == "accumulate":
+        run_accumulate(args, torch, ak, synth, dev, stream, flush, peak)
+
+
+def run_accumulate(args, torch, ak, synth, dev, stream, flush, peak):
+    """Inclusive + scan (Sec. II-B accumulate) of 268,435,456 int64 keys (2 GiB
+    in, 2 GiB out) and of the same bits as float64.  value = bytes read and
+    written per second by the scan kernel (the HBM roofline's own units)."""
+    import oracle
+    n = 1 << 28
+    xh = synth.uniform_i64(n, seed=117)
+    x = torch.from_numpy(xh).to(dev)
+    out = torch.empty_like(x)
+    lib = ak.load()
+    res = {}
+    for name, kd in (("i64_add", ak.AK_I64), ("f64_add", ak.AK_F64)):
+        temp = ak.workspace(ak.accumulate_temp_bytes(n, kd), dev)
+
+        def call(kd=kd, temp=temp):
+            rc = lib.ak_accumulate(x.data_ptr(), out.data_ptr(), n, kd, 0, 1, None, temp.data_ptr(), temp.numel(),
+                                   stream.cuda_stream, None)
+            if rc:
+                raise ak.AkError(rc, "ak_accumulate")
+
+        ms = _timed(torch, stream, flush, lambda: None, call, args.warmup, args.steps)
+        if ak.ak_status_check(temp) != 0:
+            raise RuntimeError("ak_accumulate: device status not clean")
+        res[name] = {"ms": round(ms, 4), "GBps": round(2 * n * 8 / (ms / 1e3) / 1e9, 1)}
+    gbs = res["i64_add"]["GBps"]
+    cpu = None
+    if not args.no_cpu:
+        sample = 1 << 26
+        t0 = time.perf_counter()
+        oracle.accumulate(xh[:sample], "add")
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(2 * sample * 8 / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"inclusive + over the first {sample:,} int64 keys"}
+    _line(args, f"{n:,} int64 keys, inclusive + scan (ak_accumulate), out of place; float64 on the same bits alongside",
+          gbs, {"metric": "accumulate GB/s read + written (device-timed, 1 GB300)", "dtype": "i64",
+                "results": res,
+                "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                             "frac": round(gbs / peak, 4), "traffic": None},
+                "cpu_baseline": cpu})
 
 
 def run_searchsorted(args, torch, ak, synth, dev, stream, flush, peak):

@@ -230,6 +230,44 @@ ak_status ak_searchsortedfirst(const void *d_v, int64_t n, const void *d_x, int6
 ak_status ak_searchsortedlast(const void *d_v, int64_t n, const void *d_x, int64_t m, ak_dtype kd,
                               ak_order order, int64_t *d_out, ak_stream_t stream);
 
+/* ------------------------------------------------------------------------- */
+/* Accumulate (Sec. II-B: prefix scan, inclusive and exclusive, with          */
+/* decoupled look-back).                                                      */
+
+typedef enum ak_scan_op { AK_SCAN_ADD = 0, AK_SCAN_MAX = 1, AK_SCAN_MIN = 2 } ak_scan_op;
+
+/*
+ * Prefix scan of the n keys d_x into d_out, both of dtype kd:
+ *   inclusive = 1: d_out[i] = init (+) d_x[0] (+) ... (+) d_x[i]
+ *   inclusive = 0: d_out[i] = init (+) d_x[0] (+) ... (+) d_x[i-1], d_out[0] = init
+ * where (+) is
+ *   AK_SCAN_ADD  integer + wrapping in the key's width; IEEE float + in the key's
+ *                precision, in an order of its own (results differ from a left
+ *                to right sum by rounding only: the bound is that of a sum of
+ *                depth at most 64 / key bytes + 32 + 2 ceil(n / tile), a tile
+ *                being 32 KB of keys);
+ *   AK_SCAN_MAX  Julia max: a NaN operand gives NaN, +0.0 is above -0.0;
+ *   AK_SCAN_MIN  Julia min: a NaN operand gives NaN, -0.0 is below +0.0.
+ * Integer results and max/min are exact.
+ * h_init is a HOST pointer to one key of dtype kd, or NULL for the operator's
+ * identity (0 or -0.0 for +; the lowest value or -Inf for max; the highest
+ * or +Inf for min).  d_out may be d_x (in place) but must not otherwise
+ * overlap it.  Pointers are aligned to the key size (16-byte alignment of both
+ * enables vector loads).  d_temp: a 256-byte aligned workspace of
+ * ak_accumulate_temp_bytes bytes, whose first bytes hold the status word that
+ * ak_status_check reads (AK_ERR_TIMEOUT when a look-back wait expired,
+ * opt->timeout_ns); opt may be NULL (only timeout_ns and debug_flags apply).
+ * Enqueues one memset and one kernel on `stream`; allocates nothing.
+ * Returns AK_ERR_INVALID_ARG for a negative n, a bad dtype, op or inclusive
+ * flag, malformed options, or a NULL or misaligned pointer with n > 0;
+ * AK_ERR_WORKSPACE_TOO_SMALL; AK_ERR_CUDA if a launch fails.  n = 0 is a no-op.
+ */
+ak_status ak_accumulate(const void *d_x, void *d_out, int64_t n, ak_dtype kd, ak_scan_op op, int inclusive,
+                        const void *h_init, void *d_temp, size_t temp_bytes, ak_stream_t stream,
+                        const ak_options *opt);
+/* Workspace bytes ak_accumulate needs for n keys of dtype kd (host only). */
+ak_status ak_accumulate_temp_bytes(int64_t n, ak_dtype kd, size_t *bytes);
+
 /*
  * Synchronises `stream` and returns the device-side status of the last call that
  * used d_temp (AK_OK, or e.g. AK_ERR_TIMEOUT).  AK_ERR_CUDA if the copy fails.

@@ -190,11 +190,12 @@ def accumulate(x: np.ndarray, op: str = "add", inclusive: bool = True, init=None
 
 
 def identity(dtype, op: str):
-    """The start value that changes nothing: 0 for add; the dtype's lowest
+    """The start value that changes nothing, bit for bit: 0 for integer add
+    and -0.0 for float add (x + -0.0 is x, -0.0 included); the dtype's lowest
     (max) or highest (min) value, -Inf / +Inf for floats."""
     dt = np.dtype(dtype)
     if op == "add":
-        return dt.type(0)
+        return dt.type(-0.0) if dt.kind == "f" else dt.type(0)
     if dt.kind == "f":
         return dt.type(-np.inf if op == "max" else np.inf)
     info = np.iinfo(dt)

@@ -13,5 +13,5 @@ from ._lib import (  # noqa: F401
     AkError, Info, Options, ak_autotune, autotune_temp_bytes, ak_autotune_clear, ak_autotune_load, ak_autotune_save,
     ak_last_info, ak_learned_knots, ak_learned_loss_grad, ak_sort, ak_sort_pairs,
     ak_sort_segmented, ak_sort_static_scratch, ak_sort_temp_bytes, ak_sortperm, ak_status_check, ak_status_string,
-    ak_searchsortedfirst, ak_searchsortedlast, ak_segment_capacity, ak_version, dtype_code, load, order_code, temp_bytes, workspace,
+    ak_accumulate, accumulate_temp_bytes, ak_searchsortedfirst, ak_searchsortedlast, ak_segment_capacity, ak_version, dtype_code, load, order_code, temp_bytes, workspace,
 )

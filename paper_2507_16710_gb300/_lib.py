@@ -11,6 +11,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -33,6 +34,7 @@ EXPORTED = (
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
     "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
     "ak_segment_capacity", "ak_autotune_temp_bytes", "ak_searchsortedfirst", "ak_searchsortedlast",
+    "ak_accumulate", "ak_accumulate_temp_bytes",
 )
 
 
@@ -99,6 +101,8 @@ def load() -> ctypes.CDLL:
                 "ak_autotune_temp_bytes": ([i32, i64, i32, i32, ctypes.POINTER(sz)], i32),
                 "ak_searchsortedfirst": ([p, i64, p, i64, i32, i32, p, p], i32),
                 "ak_searchsortedlast": ([p, i64, p, i64, i32, i32, p, p], i32),
+                "ak_accumulate": ([p, p, i64, i32, i32, i32, p, p, sz, p, opt], i32),
+                "ak_accumulate_temp_bytes": ([i64, i32, ctypes.POINTER(sz)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -279,6 +283,41 @@ def ak_searchsortedlast(v: torch.Tensor, x: torch.Tensor, order="ascending", *, 
     """0-based index of the last element of the sorted `v` that each query does
     not come before (-1 if none): Julia's searchsortedlast minus one."""
     return _searchsorted("ak_searchsortedlast", v, x, order, out, stream, unsigned)
+
+
+SCAN_OPS = {"add": 0, "max": 1, "min": 2}
+_NP_DTYPE = {AK_U16: np.uint16, AK_I16: np.int16, AK_U32: np.uint32, AK_I32: np.int32,
+             AK_U64: np.uint64, AK_I64: np.int64, AK_F32: np.float32, AK_F64: np.float64}
+
+
+def accumulate_temp_bytes(n: int, kd: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().ak_accumulate_temp_bytes(n, kd, ctypes.byref(out)), "ak_accumulate_temp_bytes")
+    return out.value
+
+
+def ak_accumulate(x: torch.Tensor, op: str = "add", inclusive: bool = True, *, init=None, out=None, temp=None,
+                  stream=None, options=None, unsigned: bool = False) -> torch.Tensor:
+    """Prefix scan of a 1-D CUDA tensor (Sec. II-B accumulate): 'add', 'max'
+    or 'min' from `init` (a host number; None = the operator's identity).
+    Writes `out` when given (``out=x`` scans in place), else allocates it."""
+    _contig_cuda(x, "x")
+    kd = dtype_code(x, unsigned)
+    if out is None:
+        out = torch.empty_like(x)
+    else:
+        _contig_cuda(out, "out")
+        if out.dtype != x.dtype or out.numel() != x.numel():
+            raise ValueError("out must match x in dtype and size")
+    n = x.numel()
+    if temp is None:
+        temp = workspace(accumulate_temp_bytes(n, kd), x.device)
+    init_arr = None if init is None else np.array([init]).astype(_NP_DTYPE[kd])
+    init_ptr = None if init_arr is None else init_arr.ctypes.data_as(ctypes.c_void_p)
+    _check(load().ak_accumulate(x.data_ptr(), out.data_ptr(), n, kd, SCAN_OPS[op], 1 if inclusive else 0,
+                                init_ptr, temp.data_ptr(), temp.numel(), _stream_ptr(stream), _opts(options)),
+           "ak_accumulate")
+    return out
 
 
 def ak_sort_temp_bytes(op: int, n: int, kd: int, val_bytes: int = 0, nseg: int = 0, options=None) -> int:

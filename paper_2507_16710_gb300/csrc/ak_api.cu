@@ -96,7 +96,7 @@ static RadixLayout radix_layout(int op, int64_t n, int key_bytes, int val_bytes,
 
 // Copies the caller's options (or the defaults) into *o; false when a field is
 // out of its documented range.
-static bool resolve_options(const ak_options *opt, ak_options *o) {
+bool resolve_options(const ak_options *opt, ak_options *o) {
   *o = ak_options{};
   if (opt) *o = *opt;
   if (o->path < AK_PATH_AUTO || o->path > AK_PATH_MERGE) return false;

@@ -132,6 +132,10 @@ cudaError_t seg_launch_u64_float(const SegCall &c);
 
 int device_sm_count();
 
+// Copies the caller's options (or the defaults) into *o; false when a field is
+// out of its documented range.
+bool resolve_options(const ak_options *opt, ak_options *o);
+
 // Autotune cache: the tuned path and tile configuration of a call shape.
 bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config, int *bucket_bits);
 // Bucket bits the learned path picks by itself for a call shape.

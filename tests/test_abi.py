@@ -135,6 +135,32 @@ def test_searchsorted_host_checks(lib):
         assert f(v, 10, x, 5, ak.AK_U16, 0, ctypes.c_void_p(8196), None) == 1    # misaligned output
 
 
+def test_accumulate_host_checks(lib):
+    """Workspace query and argument checks of the scan return before any launch."""
+    import paper_2507_16710_gb300 as ak
+    out = ctypes.c_size_t(0)
+    assert lib.ak_accumulate_temp_bytes(1 << 20, ak.AK_F32, ctypes.byref(out)) == 0
+    tiles = (1 << 20) // 8192  # 32 KB tiles of float32
+    assert out.value >= tiles * (4 + 8 + 8) and out.value % 256 == 0
+    assert lib.ak_accumulate_temp_bytes(-1, ak.AK_F32, ctypes.byref(out)) == 1
+    assert lib.ak_accumulate_temp_bytes(10, 8, ctypes.byref(out)) == 1
+    x, y, t = ctypes.c_void_p(1 << 16), ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 24)
+    f = lib.ak_accumulate
+    assert f(None, None, 0, ak.AK_I32, 0, 1, None, None, 0, None, None) == 0        # n = 0: nothing to do
+    assert f(x, y, -1, ak.AK_I32, 0, 1, None, t, 1 << 20, None, None) == 1          # negative n
+    assert f(x, y, 10, 8, 0, 1, None, t, 1 << 20, None, None) == 1                  # bad dtype
+    assert f(x, y, 10, ak.AK_I32, 3, 1, None, t, 1 << 20, None, None) == 1          # bad operator
+    assert f(x, y, 10, ak.AK_I32, 0, 2, None, t, 1 << 20, None, None) == 1          # bad inclusive flag
+    assert f(None, y, 10, ak.AK_I32, 0, 1, None, t, 1 << 20, None, None) == 1       # NULL input
+    assert f(ctypes.c_void_p((1 << 16) + 2), y, 10, ak.AK_I32, 0, 1, None, t, 1 << 20, None, None) == 1
+    assert f(x, y, 10, ak.AK_I32, 0, 1, None, ctypes.c_void_p((1 << 24) + 8), 1 << 20, None, None) == 1
+    assert f(x, y, 10, ak.AK_I32, 0, 1, None, None, 0, None, None) == 3             # no workspace
+    assert f(x, y, 10, ak.AK_I32, 0, 1, None, t, 16, None, None) == 3               # workspace too small
+    o = ak.Options()
+    o.path = 9
+    assert f(None, None, 0, ak.AK_I32, 0, 1, None, None, 0, None, ctypes.byref(o)) == 1  # malformed options
+
+
 def test_autotune_cache_roundtrip_and_auto_sizing(lib, tmp_path):
     """The tuning cache persists as JSON lines, skips malformed lines, and an
     AK_PATH_AUTO workspace query follows a cached choice (no GPU needed)."""
