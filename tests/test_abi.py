@@ -203,3 +203,25 @@ def test_autotune_cache_roundtrip_and_auto_sizing(lib, tmp_path):
     rows = [json.loads(x) for x in out.read_text().splitlines()]
     assert len(rows) == 1 and rows[0]["bucket_bits"] == 9
     lib.ak_autotune_clear()
+
+
+def test_binding_refuses_host_tensors_and_mismatches(lib):
+    """The Python binding checks its tensors before calling the library: host
+    (CPU) tensors, mismatched query dtypes and wrong-sized outputs raise."""
+    import torch
+
+    import paper_2507_16710_gb300 as ak
+    cpu = torch.arange(8, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        ak.ak_sort(cpu)
+    with pytest.raises(ValueError):
+        ak.ak_searchsortedfirst(cpu, cpu)
+    with pytest.raises(ValueError):
+        ak.ak_accumulate(cpu)
+    with pytest.raises(TypeError):
+        ak.dtype_code(torch.zeros(2, dtype=torch.bool))
+    with pytest.raises(ValueError):
+        ak.order_code("sideways")
+    assert ak.accumulate_temp_bytes(0, ak.AK_F64) >= 256
+    with pytest.raises(ak.AkError):
+        ak.accumulate_temp_bytes(-1, ak.AK_F64)
