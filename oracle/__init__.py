@@ -32,8 +32,9 @@ _lib = None
 _DTYPE_CODE = {
     np.dtype(np.uint16): 0, np.dtype(np.int16): 1, np.dtype(np.uint32): 2,
     np.dtype(np.int32): 3, np.dtype(np.uint64): 4, np.dtype(np.int64): 5,
-    np.dtype(np.float32): 6, np.dtype(np.float64): 7,
+    np.dtype(np.float32): 6, np.dtype(np.float64): 7, np.dtype(np.float16): 8,
 }
+BF16_CODE = 9  # bfloat16 keys travel as their uint16 bits: pass as_dtype="bfloat16"
 
 
 def build(force: bool = False) -> str:
@@ -69,7 +70,13 @@ def _load():
     return _lib
 
 
-def _code(a: np.ndarray) -> int:
+def _code(a: np.ndarray, as_dtype=None) -> int:
+    if as_dtype == "bfloat16":
+        if a.dtype != np.uint16:
+            raise TypeError("bfloat16 keys are passed as their uint16 bits")
+        return BF16_CODE
+    if as_dtype is not None:
+        raise ValueError(as_dtype)
     try:
         return _DTYPE_CODE[a.dtype]
     except KeyError:
@@ -88,15 +95,15 @@ def _desc(order) -> int:
     raise ValueError(order)
 
 
-def sortperm(keys: np.ndarray, order="ascending", threads: int = 1) -> np.ndarray:
+def sortperm(keys: np.ndarray, order="ascending", threads: int = 1, as_dtype=None) -> np.ndarray:
     """Stable sorting permutation (int64, 0-based)."""
     k = np.ascontiguousarray(keys)
     perm = np.empty(k.size, dtype=np.int64)
     lib = _load()
     if threads > 1:
-        rc = lib.oracle_sortperm_threaded(_ptr(k), k.size, _code(k), _desc(order), _ptr(perm), threads)
+        rc = lib.oracle_sortperm_threaded(_ptr(k), k.size, _code(k, as_dtype), _desc(order), _ptr(perm), threads)
     else:
-        rc = lib.oracle_sortperm(_ptr(k), k.size, _code(k), _desc(order), _ptr(perm))
+        rc = lib.oracle_sortperm(_ptr(k), k.size, _code(k, as_dtype), _desc(order), _ptr(perm))
     if rc:
         raise RuntimeError(f"oracle_sortperm failed ({rc})")
     return perm
@@ -112,42 +119,42 @@ def gather(src: np.ndarray, perm: np.ndarray) -> np.ndarray:
     return out
 
 
-def sort(keys: np.ndarray, order="ascending", threads: int = 1) -> np.ndarray:
-    return gather(keys, sortperm(keys, order, threads))
+def sort(keys: np.ndarray, order="ascending", threads: int = 1, as_dtype=None) -> np.ndarray:
+    return gather(keys, sortperm(keys, order, threads, as_dtype))
 
 
-def sort_pairs(keys: np.ndarray, vals: np.ndarray, order="ascending", threads: int = 1):
-    p = sortperm(keys, order, threads)
+def sort_pairs(keys: np.ndarray, vals: np.ndarray, order="ascending", threads: int = 1, as_dtype=None):
+    p = sortperm(keys, order, threads, as_dtype)
     return gather(keys, p), gather(vals, p)
 
 
-def sortperm_segmented(keys: np.ndarray, offsets: np.ndarray, order="ascending") -> np.ndarray:
+def sortperm_segmented(keys: np.ndarray, offsets: np.ndarray, order="ascending", as_dtype=None) -> np.ndarray:
     """Global-index permutation sorting each CSR segment on its own."""
     k = np.ascontiguousarray(keys)
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     perm = np.empty(k.size, dtype=np.int64)
-    rc = _load().oracle_sortperm_segmented(_ptr(k), _ptr(off), off.size - 1, k.size, _code(k),
+    rc = _load().oracle_sortperm_segmented(_ptr(k), _ptr(off), off.size - 1, k.size, _code(k, as_dtype),
                                            _desc(order), _ptr(perm))
     if rc:
         raise RuntimeError(f"oracle_sortperm_segmented failed ({rc})")
     return perm
 
 
-def sort_segmented(keys: np.ndarray, offsets: np.ndarray, order="ascending") -> np.ndarray:
-    return gather(keys, sortperm_segmented(keys, offsets, order))
+def sort_segmented(keys: np.ndarray, offsets: np.ndarray, order="ascending", as_dtype=None) -> np.ndarray:
+    return gather(keys, sortperm_segmented(keys, offsets, order, as_dtype))
 
 
-def isless(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+def isless(a: np.ndarray, b: np.ndarray, as_dtype=None) -> np.ndarray:
     """Elementwise Julia isless(a[i], b[i]) as computed by the oracle."""
     a = np.ascontiguousarray(a)
     b = np.ascontiguousarray(b, dtype=a.dtype)
     out = np.empty(a.size, dtype=np.uint8)
-    if _load().oracle_isless_pairs(_ptr(a), _ptr(b), a.size, _code(a), _ptr(out)):
+    if _load().oracle_isless_pairs(_ptr(a), _ptr(b), a.size, _code(a, as_dtype), _ptr(out)):
         raise RuntimeError("oracle_isless_pairs failed")
     return out.astype(bool)
 
 
-def searchsorted(v: np.ndarray, x: np.ndarray, side: str = "first", order="ascending") -> np.ndarray:
+def searchsorted(v: np.ndarray, x: np.ndarray, side: str = "first", order="ascending", as_dtype=None) -> np.ndarray:
     """Binary search of Sec. II-B over a v already in the order's sequence.
 
     side 'first': index of the first v element not coming before x (n if none);
@@ -159,7 +166,7 @@ def searchsorted(v: np.ndarray, x: np.ndarray, side: str = "first", order="ascen
     if side not in ("first", "last"):
         raise ValueError(side)
     out = np.empty(xx.size, dtype=np.int64)
-    rc = _load().oracle_searchsorted(_ptr(vv), vv.size, _ptr(xx), xx.size, _code(vv), _desc(order),
+    rc = _load().oracle_searchsorted(_ptr(vv), vv.size, _ptr(xx), xx.size, _code(vv, as_dtype), _desc(order),
                                      0 if side == "first" else 1, _ptr(out))
     if rc:
         raise RuntimeError(f"oracle_searchsorted failed ({rc})")

@@ -18,6 +18,8 @@
  *
  * Julia isless on integers is <.  On IEEE floats: every NaN compares after every
  * non-NaN and all NaNs are equivalent; -0.0 comes before +0.0; otherwise <.
+ * Key types: 16/32/64-bit integers, float32, float64, and the 16-bit floats
+ * (IEEE binary16 and bfloat16, compared through their exact float32 values).
  *
  *   searchsortedfirst / searchsortedlast (Sec. II-B, binary search) -> for a v
  *   already in the order's sequence, the 0-based index of the first element of
@@ -37,7 +39,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OD_U16 = 0, OD_I16, OD_U32, OD_I32, OD_U64, OD_I64, OD_F32, OD_F64, OD_COUNT };
+enum { OD_U16 = 0, OD_I16, OD_U32, OD_I32, OD_U64, OD_I64, OD_F32, OD_F64, OD_F16, OD_BF16, OD_COUNT };
 
 typedef struct {
     const void *keys;
@@ -62,6 +64,26 @@ static int isless_float(float a, float b) {
     return 0;
 }
 
+/* IEEE 754 binary16 bits -> the same value as a float (exact): sign, 5-bit
+ * exponent (bias 15), 10-bit fraction; exponent 0 is zero or subnormal
+ * (fraction x 2^-24), exponent 31 is Inf (fraction 0) or NaN. */
+static float half_to_float(uint16_t h) {
+    const int e = (h >> 10) & 0x1F, m = h & 0x3FF;
+    float v;
+    if (e == 0) v = ldexpf((float)m, -24);
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = ldexpf((float)(m | 0x400), e - 25);   /* (1024 + m) x 2^(e - 25) */
+    return (h >> 15) ? -v : v;
+}
+
+/* bfloat16 bits are the top half of a float32's bits (exact). */
+static float bf16_to_float(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return f;
+}
+
 /* isless(a[i], b[j]) for keys of one dtype held in two arrays */
 static int isless_at(int dtype, const void *a, int64_t i, const void *b, int64_t j) {
     switch (dtype) {
@@ -73,6 +95,8 @@ static int isless_at(int dtype, const void *a, int64_t i, const void *b, int64_t
     case OD_I64: return ((const int64_t *)a)[i] < ((const int64_t *)b)[j];
     case OD_F32: return isless_float(((const float *)a)[i], ((const float *)b)[j]);
     case OD_F64: return isless_double(((const double *)a)[i], ((const double *)b)[j]);
+    case OD_F16: return isless_float(half_to_float(((const uint16_t *)a)[i]), half_to_float(((const uint16_t *)b)[j]));
+    case OD_BF16: return isless_float(bf16_to_float(((const uint16_t *)a)[i]), bf16_to_float(((const uint16_t *)b)[j]));
     }
     return 0;
 }
@@ -220,7 +244,8 @@ int oracle_gather(const void *src, const int64_t *perm, int64_t n, int elem_byte
 /* isless(a[i], b[i]) for n pairs, exposed so tests can pin the comparator itself. */
 int oracle_isless_pairs(const void *a, const void *b, int64_t n, int dtype, uint8_t *out) {
     if (n < 0 || dtype < 0 || dtype >= OD_COUNT) return -1;
-    size_t w = (dtype <= OD_I16) ? 2 : (dtype <= OD_I32 || dtype == OD_F32) ? 4 : 8;
+    size_t w = (dtype <= OD_I16 || dtype == OD_F16 || dtype == OD_BF16) ? 2
+             : (dtype <= OD_I32 || dtype == OD_F32) ? 4 : 8;
     unsigned char *buf = (unsigned char *)malloc(2 * w);
     if (!buf) return -2;
     oracle_ctx c = {buf, dtype, 0};
@@ -335,7 +360,7 @@ static int int_less(int dtype, uint64_t a, uint64_t b) {
 
 int oracle_accumulate(const void *x, int64_t n, int dtype, int op, int inclusive, const void *init,
                       void *out) {
-    if (n < 0 || dtype < 0 || dtype >= OD_COUNT || op < OA_ADD || op > OA_MIN || !init) return -1;
+    if (n < 0 || dtype < 0 || dtype > OD_F64 || op < OA_ADD || op > OA_MIN || !init) return -1;  /* 16-bit floats: not defined here */
     if (n > 0 && (!x || !out)) return -1;
     if (dtype == OD_F32 || dtype == OD_F64) {
         double s = float_at(dtype, init, 0), c = 0.0, plain = s;

@@ -249,6 +249,10 @@ def special_values(dtype) -> np.ndarray:
         if dt.kind == "i":
             vals += [-1, -2]
         return np.array(vals, dtype=dt)
+    if dt == np.float16:
+        bits = np.array([0x0000, 0x8000, 0x7C00, 0xFC00, 0x7E00, 0xFE01, 0x7E5A, 0x7C01,
+                         0x0001, 0x8001, 0x3C00, 0xBC00, 0x7BFF, 0xFBFF], dtype=np.uint16)
+        return bits.view(np.float16)
     if dt == np.float32:
         bits = np.array([0x00000000, 0x80000000, 0x7F800000, 0xFF800000, 0x7FC00000,
                          0xFFC00001, 0x7FC12345, 0x7F800001, 0x00000001, 0x80000001,

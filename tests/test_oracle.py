@@ -406,3 +406,73 @@ def test_accumulate_empty_and_single():
         one = synth.random_keys(1, dtype, seed=106, mode="narrow")
         assert bits_equal(oracle.accumulate(one, "max"), one)
         assert bits_equal(oracle.accumulate(one, "add", inclusive=False, init=dtype(3)), np.array([3], dtype=dtype))
+
+
+# ------------------------------------------------------------ 16-bit floats
+# IEEE binary16 (numpy float16) and bfloat16 (its uint16 bits, as_dtype=
+# "bfloat16"), ordered by Julia isless through their exact float32 values.
+
+def _bf16_value(bits):
+    """bfloat16 bits -> float32 values: the bits are the top half of a float32."""
+    return (np.asarray(bits, dtype=np.uint32) << np.uint32(16)).view(np.float32)
+
+
+def test_float16_isless_facts_by_hand():
+    """Bit patterns read off the binary16 layout (sign | 5-bit exponent |
+    10-bit fraction): -0.0 before +0.0; every NaN after +Inf and tied; the
+    smallest subnormal above +0.0; 65504 the largest finite value."""
+    pairs = [(0x8000, 0x0000, True), (0x0000, 0x8000, False), (0x7C00, 0x7E00, True),
+             (0x7E00, 0x7C00, False), (0x7E00, 0xFE01, False), (0xFE01, 0x7E00, False),
+             (0x0000, 0x0001, True), (0x7BFF, 0x7C00, True), (0xFC00, 0xFBFF, True),
+             (0x3C00, 0x4000, True), (0xBC00, 0x3C00, True), (0x8001, 0x8000, True)]
+    a = np.array([p[0] for p in pairs], np.uint16).view(np.float16)
+    b = np.array([p[1] for p in pairs], np.uint16).view(np.float16)
+    assert oracle.isless(a, b).tolist() == [p[2] for p in pairs]
+
+
+def test_bfloat16_isless_facts_by_hand():
+    """bfloat16 = the top 16 bits of a float32: 0x3F80 is 1.0, 0x7F80 +Inf,
+    0x7FC0 a NaN, 0x8000 -0.0, 0x0001 the smallest subnormal."""
+    pairs = [(0x8000, 0x0000, True), (0x7F80, 0x7FC0, True), (0xFFC0, 0x7FC0, False),
+             (0x3F80, 0x4000, True), (0xBF80, 0x0000, True), (0x0000, 0x0001, True),
+             (0x7F7F, 0x7F80, True), (0xFF80, 0xFF7F, True)]
+    a = np.array([p[0] for p in pairs], np.uint16)
+    b = np.array([p[1] for p in pairs], np.uint16)
+    assert oracle.isless(a, b, as_dtype="bfloat16").tolist() == [p[2] for p in pairs]
+    assert _bf16_value(np.array([0x3F80]))[0] == 1.0
+
+
+def test_float16_matches_numpy_comparison():
+    """Off NaNs and signed zeros, isless is numpy's float16 <."""
+    a = synth.random_keys(20000, np.float16, seed=121)
+    b = synth.random_keys(20000, np.float16, seed=122)
+    ok = ~np.isnan(a) & ~np.isnan(b) & ~((a == 0) & (b == 0))
+    assert np.array_equal(oracle.isless(a[ok], b[ok]), a[ok] < b[ok])
+
+
+@pytest.mark.parametrize("mode", ["bits", "dups", "narrow"])
+@pytest.mark.parametrize("desc", [False, True])
+def test_16bit_floats_match_python_timsort(mode, desc):
+    h = synth.random_keys(3000, np.float16, seed=123, mode=mode)
+    pyvals = [float(v) for v in h]
+    want = sorted(range(h.size), key=lambda i: _py_key(pyvals[i]), reverse=desc)
+    assert np.array_equal(oracle.sortperm(h, "descending" if desc else "ascending"), np.array(want))
+    bits = synth.random_keys(3000, np.uint16, seed=124, mode="bits" if mode == "bits" else "dups")
+    vals = [float(v) for v in _bf16_value(bits)]
+    want = sorted(range(bits.size), key=lambda i: _py_key(vals[i]), reverse=desc)
+    got = oracle.sortperm(bits, "descending" if desc else "ascending", as_dtype="bfloat16")
+    assert np.array_equal(got, np.array(want))
+
+
+def test_16bit_floats_search_brute_force():
+    v = oracle.sort(synth.random_keys(300, np.float16, seed=125, mode="dups"))
+    x = np.concatenate([synth.special_values(np.float16), synth.random_keys(50, np.float16, seed=126)])
+    for side in ("first", "last"):
+        got = oracle.searchsorted(v, x, side)
+        for i in range(x.size):
+            xi = np.full(v.size, x[i], dtype=v.dtype)
+            want = np.count_nonzero(oracle.isless(v, xi)) if side == "first" \
+                else np.count_nonzero(~oracle.isless(xi, v)) - 1
+            assert got[i] == want
+    with pytest.raises(RuntimeError):
+        oracle.accumulate(v, "add")  # 16-bit float scans are not defined in the oracle
