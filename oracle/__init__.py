@@ -35,6 +35,9 @@ _DTYPE_CODE = {
     np.dtype(np.float32): 6, np.dtype(np.float64): 7, np.dtype(np.float16): 8,
 }
 BF16_CODE = 9  # bfloat16 keys travel as their uint16 bits: pass as_dtype="bfloat16"
+# 128-bit integer keys travel as 16-byte void elements (np.dtype("V16"), low 8
+# bytes first): pass as_dtype="int128" or "uint128"
+I128_CODES = {"int128": 10, "uint128": 11}
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +78,10 @@ def _code(a: np.ndarray, as_dtype=None) -> int:
         if a.dtype != np.uint16:
             raise TypeError("bfloat16 keys are passed as their uint16 bits")
         return BF16_CODE
+    if as_dtype in I128_CODES:
+        if a.dtype.itemsize != 16 or a.dtype.kind != "V":
+            raise TypeError("128-bit keys are passed as 16-byte void elements (np.dtype('V16'))")
+        return I128_CODES[as_dtype]
     if as_dtype is not None:
         raise ValueError(as_dtype)
     try:
@@ -207,3 +214,26 @@ def identity(dtype, op: str):
         return dt.type(-np.inf if op == "max" else np.inf)
     info = np.iinfo(dt)
     return dt.type(info.min if op == "max" else info.max)
+
+
+def _word_bits(v) -> np.ndarray:
+    """64-bit words as uint64 bits: integer arrays by two's complement, other
+    sequences element by element as Python ints (either sign)."""
+    if isinstance(v, np.ndarray) and v.dtype.kind in "iu":
+        return v.astype(np.uint64)
+    return np.array([int(t) & 0xFFFFFFFFFFFFFFFF for t in v], dtype=np.uint64)
+
+
+def int128_from_words(lo, hi) -> np.ndarray:
+    """128-bit keys (V16 elements) from their low and high 64-bit words."""
+    lo, hi = _word_bits(lo), _word_bits(hi)
+    w = np.empty((lo.size, 2), dtype=np.uint64)
+    w[:, 0] = lo
+    w[:, 1] = hi
+    return w.view(np.dtype("V16")).reshape(-1)
+
+
+def int128_words(keys: np.ndarray):
+    """(low, high) uint64 words of V16 keys."""
+    w = np.ascontiguousarray(keys).view(np.uint64).reshape(-1, 2)
+    return w[:, 0].copy(), w[:, 1].copy()

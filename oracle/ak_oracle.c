@@ -18,7 +18,7 @@
  *
  * Julia isless on integers is <.  On IEEE floats: every NaN compares after every
  * non-NaN and all NaNs are equivalent; -0.0 comes before +0.0; otherwise <.
- * Key types: 16/32/64-bit integers, float32, float64, and the 16-bit floats
+ * Key types: 16/32/64/128-bit integers, float32, float64, and the 16-bit floats
  * (IEEE binary16 and bfloat16, compared through their exact float32 values).
  *
  *   searchsortedfirst / searchsortedlast (Sec. II-B, binary search) -> for a v
@@ -39,7 +39,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OD_U16 = 0, OD_I16, OD_U32, OD_I32, OD_U64, OD_I64, OD_F32, OD_F64, OD_F16, OD_BF16, OD_COUNT };
+enum { OD_U16 = 0, OD_I16, OD_U32, OD_I32, OD_U64, OD_I64, OD_F32, OD_F64, OD_F16, OD_BF16,
+       OD_I128, OD_U128, OD_COUNT };
 
 typedef struct {
     const void *keys;
@@ -84,6 +85,19 @@ static float bf16_to_float(uint16_t b) {
     return f;
 }
 
+/* 128-bit integers, 16 bytes each (low 8 bytes first), read with memcpy so
+ * that any alignment of the caller's array is fine. */
+static __int128 load_i128(const void *p, int64_t i) {
+    __int128 v;
+    memcpy(&v, (const unsigned char *)p + (size_t)i * 16, 16);
+    return v;
+}
+static unsigned __int128 load_u128(const void *p, int64_t i) {
+    unsigned __int128 v;
+    memcpy(&v, (const unsigned char *)p + (size_t)i * 16, 16);
+    return v;
+}
+
 /* isless(a[i], b[j]) for keys of one dtype held in two arrays */
 static int isless_at(int dtype, const void *a, int64_t i, const void *b, int64_t j) {
     switch (dtype) {
@@ -97,6 +111,8 @@ static int isless_at(int dtype, const void *a, int64_t i, const void *b, int64_t
     case OD_F64: return isless_double(((const double *)a)[i], ((const double *)b)[j]);
     case OD_F16: return isless_float(half_to_float(((const uint16_t *)a)[i]), half_to_float(((const uint16_t *)b)[j]));
     case OD_BF16: return isless_float(bf16_to_float(((const uint16_t *)a)[i]), bf16_to_float(((const uint16_t *)b)[j]));
+    case OD_I128: return load_i128(a, i) < load_i128(b, j);
+    case OD_U128: return load_u128(a, i) < load_u128(b, j);
     }
     return 0;
 }
@@ -245,7 +261,8 @@ int oracle_gather(const void *src, const int64_t *perm, int64_t n, int elem_byte
 int oracle_isless_pairs(const void *a, const void *b, int64_t n, int dtype, uint8_t *out) {
     if (n < 0 || dtype < 0 || dtype >= OD_COUNT) return -1;
     size_t w = (dtype <= OD_I16 || dtype == OD_F16 || dtype == OD_BF16) ? 2
-             : (dtype <= OD_I32 || dtype == OD_F32) ? 4 : 8;
+             : (dtype <= OD_I32 || dtype == OD_F32) ? 4
+             : (dtype == OD_I128 || dtype == OD_U128) ? 16 : 8;
     unsigned char *buf = (unsigned char *)malloc(2 * w);
     if (!buf) return -2;
     oracle_ctx c = {buf, dtype, 0};

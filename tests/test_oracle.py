@@ -476,3 +476,67 @@ def test_16bit_floats_search_brute_force():
             assert got[i] == want
     with pytest.raises(RuntimeError):
         oracle.accumulate(v, "add")  # 16-bit float scans are not defined in the oracle
+
+
+# ------------------------------------------------------------ 128-bit integers
+# Int128 / UInt128 keys (the paper's best AcceleratedKernels case, Sec. IV-C),
+# 16-byte elements, low word first.
+
+def _i128_keys(n, seed, mode):
+    lo = synth.splitmix64(seed, n)
+    if mode == "bits":
+        hi = synth.splitmix64(seed + 1, n)
+    else:  # few distinct high words, many ties on the whole key
+        hi = synth.special_values(np.int64)[(synth.splitmix64(seed + 1, n) % np.uint64(8)).astype(np.int64)]
+        lo = lo % np.uint64(5)
+    return oracle.int128_from_words(lo, hi)
+
+
+def _py_int(lo, hi, signed):
+    v = (int(hi) << 64) | int(lo)
+    return v - (1 << 128) if signed and v >> 127 else v
+
+
+@pytest.mark.parametrize("signed", [True, False])
+@pytest.mark.parametrize("mode", ["bits", "dups"])
+@pytest.mark.parametrize("desc", [False, True])
+def test_int128_matches_python_ints(signed, mode, desc):
+    """Python's arbitrary-precision ints and Timsort define the order."""
+    k = _i128_keys(4000, 131, mode)
+    lo, hi = oracle.int128_words(k)
+    vals = [_py_int(a, b, signed) for a, b in zip(lo.tolist(), hi.tolist())]
+    want = sorted(range(k.size), key=lambda i: vals[i], reverse=desc)
+    got = oracle.sortperm(k, "descending" if desc else "ascending", as_dtype="int128" if signed else "uint128")
+    assert np.array_equal(got, np.array(want))
+
+
+@pytest.mark.parametrize("signed", [True, False])
+def test_int128_matches_numpy_lexsort(signed):
+    """Ordering by (high word, signed for Int128; then low word unsigned) is
+    the 128-bit order; numpy's lexsort is stable."""
+    k = _i128_keys(20000, 132, "dups")
+    lo, hi = oracle.int128_words(k)
+    want = np.lexsort((lo, hi.view(np.int64) if signed else hi))
+    assert np.array_equal(oracle.sortperm(k, as_dtype="int128" if signed else "uint128"), want)
+
+
+def test_int128_search_gather_and_facts():
+    """Hand facts: -1 < 0 signed but 2^128 - 1 > 0 unsigned; 2^64 > 2^64 - 1;
+    gather moves all 16 bytes; search counts by brute force."""
+    k = oracle.int128_from_words([2**64 - 1, 0, 0, 2**64 - 1], [2**64 - 1, 0, 1, 0])  # -1, 0, 2^64, 2^64-1
+    assert oracle.isless(k[:1], k[1:2], as_dtype="int128").tolist() == [True]
+    assert oracle.isless(k[:1], k[1:2], as_dtype="uint128").tolist() == [False]
+    assert oracle.isless(k[3:4], k[2:3], as_dtype="int128").tolist() == [True]
+    s = oracle.sort(k, as_dtype="int128")
+    assert [_py_int(a, b, True) for a, b in zip(*[w.tolist() for w in oracle.int128_words(s)])] == \
+        [-1, 0, 2**64 - 1, 2**64]
+    v = oracle.sort(_i128_keys(300, 133, "dups"), as_dtype="int128")
+    x = _i128_keys(40, 134, "dups")
+    first = oracle.searchsorted(v, x, "first", as_dtype="int128")
+    last = oracle.searchsorted(v, x, "last", as_dtype="int128")
+    vl, vh = oracle.int128_words(v)
+    vv = [_py_int(a, b, True) for a, b in zip(vl.tolist(), vh.tolist())]
+    xl, xh = oracle.int128_words(x)
+    for i, (a, b) in enumerate(zip(xl.tolist(), xh.tolist())):
+        xi = _py_int(a, b, True)
+        assert first[i] == sum(e < xi for e in vv) and last[i] == sum(e <= xi for e in vv) - 1
