@@ -102,9 +102,10 @@ typedef struct ak_options {
 
 #define AK_MAX_PASSES 8
 
-/* Test hook: no CTA owns the first tile of any radix pass, so every look-back
- * that reaches it waits until timeout_ns and the call ends with AK_ERR_TIMEOUT
- * (the keys are then unspecified).  Exercises the bounded-wait error path. */
+/* Test hook: no CTA owns the first tile of any radix pass (or of an
+ * ak_accumulate scan), so every look-back that reaches it waits until
+ * timeout_ns and the call ends with AK_ERR_TIMEOUT (the output is then
+ * unspecified).  Exercises the bounded-wait error path. */
 #define AK_DEBUG_SKIP_FIRST_TILE 1
 /* Tuning hook: no L2 prefetch one wave ahead in tile configuration 3 (the
  * persistent configurations prefetch each claimed tile, unaffected). */
