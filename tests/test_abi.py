@@ -112,6 +112,14 @@ def test_host_side_argument_checks(lib):
     # UInt32 permutation limit
     assert lib.ak_sortperm(ctypes.c_void_p(4096), ctypes.c_void_p(8192), 1 << 32, ak.AK_U32, 0, None, 0,
                            None, None) == 6
+    # segmented: n or nseg past 2^32 - 1 is refused before any device access
+    off = ctypes.c_void_p(1 << 20)
+    assert lib.ak_sort_segmented(ctypes.c_void_p(4096), off, 1, 1 << 32, ak.AK_U32, 0, None, 0, None, None) == 2
+    assert lib.ak_sort_segmented(ctypes.c_void_p(4096), off, 1 << 32, 10, ak.AK_U32, 0, None, 0, None, None) == 2
+    assert lib.ak_sort_segmented(ctypes.c_void_p(4096), off, -1, 10, ak.AK_U32, 0, None, 0, None, None) == 1
+    # sortperm just below the UInt32 limit passes the size check (and stops at the workspace)
+    assert lib.ak_sortperm(ctypes.c_void_p(4096), ctypes.c_void_p(8192), (1 << 32) - 1, ak.AK_U32, 0, None, 0,
+                           None, None) == 3
     assert lib.ak_status_string(5) == b"device-side wait timed out"
 
 
