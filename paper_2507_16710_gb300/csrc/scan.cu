@@ -17,8 +17,10 @@
 //  * the tile publishes its aggregate, then warp 0 looks back over up to 32
 //    predecessors at a time, stops at the nearest inclusive prefix and
 //    publishes its own inclusive prefix;
-//  * status: a 32-bit flag (release store / acquire load, gpu scope) beside a
-//    64-bit value, so every key width uses one scheme;
+//  * status: a 32-bit flag (release store / acquire load, gpu scope) beside
+//    two write-once 64-bit slots, the aggregate and the inclusive prefix, so a
+//    reader that saw one flag value can never pick up the other slot's value
+//    (one scheme for every key width);
 //  * every wait is bounded by the globaltimer: on expiry the CTA records
 //    AK_ERR_TIMEOUT, takes the identity for the missing prefix and finishes.
 //
