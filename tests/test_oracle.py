@@ -228,6 +228,11 @@ def test_generators_are_reproducible_and_shaped():
     top = synth.fmix32(np.array([0], dtype=np.uint32))[0]
     frac = (z == top).mean()
     assert 0.04 < frac < 0.08   # ~5.75% of keys equal the top rank
+    # ascending by construction, across chunk boundaries, with ~25% equal neighbours
+    asc = synth.ascending_f64((1 << 23) + 1000, seed=40)
+    assert np.array_equal(asc, synth.ascending_f64((1 << 23) + 1000, seed=40))
+    assert np.all(np.diff(asc) >= 0) and np.isfinite(asc).all() and asc[0] >= 0
+    assert 0.24 < (np.diff(asc) == 0).mean() < 0.26
 
 
 # ------------------------------------------------------------ binary search
