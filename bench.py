@@ -39,11 +39,11 @@ FULL_N = 268_435_456
 METRIC = "keys GB/s sorted (device-timed, 1 GB300) and % of 2×bytes/8TB/s roofline; learned vs plain"
 NOMINAL_HBM_GBS = 8000.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of onesweep_pass, averaged
-# over the 24 digit-pass launches of one step at 33,554,432 keys per array
-# (profiles/onesweep_pass_traffic_33M.md): (keys per array, bytes per launch).
-# Traffic grows in proportion to the keys, so it is scaled to the run's n.  Set
-# to None whenever the digit-pass kernel changes until it is captured again.
-NCU_TRAFFIC = (33_554_432, 522_239_040)
+# over the digit-pass launches of one step of this workload at a smaller n
+# (keys per array, bytes per launch).  Traffic grows in proportion to the keys,
+# so it is scaled to the run's n.  None whenever the digit-pass kernel has
+# changed since the counters were taken.
+NCU_TRAFFIC = None
 
 
 def parse_args():
@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=FULL_N, help="keys per array (default: the full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison of the headline")
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted", "accumulate"],
                     help="c2 (default): the headline line; the others print their own lines")
     ap.add_argument("--segments", type=int, default=65536, help="c4: number of segments")
@@ -159,6 +160,139 @@ def onesweep_bytes(op: str, n: int, w: int, passes: int) -> list[int]:
         else:
             out.append(2 * n * w + 8 * n)
     return out
+
+
+# ------------------------------------------------------------ output checks
+# Every GB/s printed comes from a call whose output was checked on the host.
+# These checks are the bench's own (numpy, no library code): the order of Julia
+# isless as unsigned integers, an order-independent hash of the raw bits for the
+# multiset, and the three properties that make a permutation THE stable one.
+
+def _order_key(a: np.ndarray) -> np.ndarray:
+    """Unsigned integers of a's width ordered like Julia isless: unsigned as is,
+    signed with the sign bit flipped, floats negative -> all bits flipped,
+    non-negative -> sign bit flipped, every NaN -> the maximum."""
+    w = a.dtype.itemsize
+    ut = np.dtype(f"u{w}")
+    u = a.view(ut)
+    if a.dtype.kind == "u":
+        return u
+    sign = ut.type(1 << (8 * w - 1))
+    if a.dtype.kind == "i":
+        return u ^ sign
+    out = np.where((u & sign) != 0, ~u, u ^ sign).astype(ut)
+    out[np.isnan(a)] = np.iinfo(ut).max
+    return out
+
+
+def _bits_hash(a: np.ndarray) -> int:
+    """Sum over elements of a 64-bit mix of their raw bits (mod 2^64): equal for
+    any two orderings of the same multiset."""
+    z = a.view(np.dtype(f"u{a.dtype.itemsize}")).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(31))) * np.uint64(0x7FB5D329728EA185)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x81DADEF4BC2DD44D)
+        z ^= z >> np.uint64(33)
+        return int(z.sum(dtype=np.uint64))
+
+
+def check_sorted(inp: np.ndarray, out: np.ndarray, desc: bool = False) -> bool:
+    """out is inp's multiset, in isless order (reversed when desc)."""
+    if out.shape != inp.shape:
+        return False
+    r = _order_key(out)
+    ok = bool(np.all(r[1:] <= r[:-1])) if desc else bool(np.all(r[1:] >= r[:-1]))
+    return ok and _bits_hash(inp) == _bits_hash(out)
+
+
+def check_perm(inp: np.ndarray, perm: np.ndarray, desc: bool = False, sorted_out: np.ndarray | None = None) -> bool:
+    """perm is the stable sortperm of inp: a permutation, listing keys in order,
+    equivalent neighbours in increasing index; sorted_out (if given) = inp[perm]."""
+    p = perm.astype(np.int64)
+    n = inp.size
+    if p.size != n or (n and (p.min() < 0 or p.max() >= n)):
+        return False
+    if n and not np.all(np.bincount(p, minlength=n) == 1):
+        return False
+    r = _order_key(inp)[p]
+    if desc:
+        r = ~r
+    if not np.all(r[1:] >= r[:-1]):
+        return False
+    tie = r[1:] == r[:-1]
+    if not np.all(p[1:][tie] > p[:-1][tie]):
+        return False
+    if sorted_out is not None:
+        w = np.dtype(f"u{inp.dtype.itemsize}")
+        return bool(np.array_equal(sorted_out.view(w), inp.view(w)[p]))
+    return True
+
+
+def time_sort(torch, ak, dev, stream, flush, host, kd, opts, op="sort", vals=None, order="ascending",
+              warmup=3, steps=5, check=True):
+    """Median device time of one ak_sort / ak_sortperm / ak_sort_pairs call on
+    `host` keys (restored from a pristine device copy and L2 flushed before
+    every call, both outside the events).  Returns (key GB/s, ms, ak_info, ok),
+    ok from the host check of the last call's output."""
+    unsigned = host.dtype.kind == "u"
+    view = {2: np.int16, 4: np.int32, 8: np.int64}[host.itemsize] if unsigned else host.dtype
+    pristine = torch.from_numpy(host.view(view)).to(dev)
+    work = torch.empty_like(pristine)
+    o = ak.Options()
+    for k, v in (opts or {}).items():
+        setattr(o, k, v)
+    vp = vw = perm = None
+    if op == "pairs":
+        vp = torch.from_numpy(vals.view(np.int32)).to(dev)
+        vw = torch.empty_like(vp)
+        tb = ak.temp_bytes(ak.AK_OP_SORT_PAIRS, host.size, kd, 4, options=o)
+    elif op == "sortperm":
+        perm = torch.empty(host.size, dtype=torch.int32, device=dev)
+        tb = ak.temp_bytes(ak.AK_OP_SORTPERM, host.size, kd, options=o)
+    else:
+        tb = ak.temp_bytes(ak.AK_OP_SORT, host.size, kd, options=o)
+    temp = ak.workspace(tb, dev)
+    lib = ak.load()
+    od = ak.order_code(order)
+
+    def restore():
+        work.copy_(pristine)
+        if vw is not None:
+            vw.copy_(vp)
+
+    def call():
+        if op == "pairs":
+            rc = lib.ak_sort_pairs(work.data_ptr(), vw.data_ptr(), 4, host.size, kd, od, temp.data_ptr(),
+                                   temp.numel(), stream.cuda_stream, ctypes.byref(o))
+        elif op == "sortperm":
+            rc = lib.ak_sortperm(work.data_ptr(), perm.data_ptr(), host.size, kd, od, temp.data_ptr(), temp.numel(),
+                                 stream.cuda_stream, ctypes.byref(o))
+        else:
+            rc = lib.ak_sort(work.data_ptr(), host.size, kd, od, temp.data_ptr(), temp.numel(),
+                             stream.cuda_stream, ctypes.byref(o))
+        if rc:
+            raise ak.AkError(rc, op)
+
+    ms = _timed(torch, stream, flush, restore, call, warmup, steps)
+    info = ak.ak_last_info(temp)
+    ok = None
+    if check:
+        desc = od == ak.AK_DESCENDING
+        if op == "sortperm":
+            ok = check_perm(host, perm.cpu().numpy().view(np.uint32), desc)
+        else:
+            out = work.cpu().numpy().view(host.dtype)
+            ok = check_sorted(host, out, desc)
+            if ok and op == "pairs":
+                v_out = vw.cpu().numpy().view(np.uint32)
+                ok = check_perm(host, v_out, desc, sorted_out=out)  # values = input index
+        ok = ok and info["status"] == 0
+    del pristine, work, temp, vp, vw, perm
+    torch.cuda.empty_cache()
+    return host.nbytes / (ms / 1e3) / 1e9, ms, info, ok
+
+
+PATH_NAMES = {1: "radix", 2: "learned", 3: "block", 4: "merge"}
 
 
 def cpu_oracle_rate(k64: np.ndarray, k32: np.ndarray, sample: int, threads: int) -> tuple[float, float]:
@@ -345,10 +479,48 @@ def run_ours(args):
              "per_call_ms": {k: round(statistics.median(v), 4) for k, v in per_call.items()},
              "wall_s_timed_region": round(wall, 3)}
 
+    # the last step's outputs: sorted int64 and float32 keys, the float32 sortperm
+    verified = {"i64_sort": check_sorted(k64, arrays[0]["work"].cpu().numpy()),
+                "f32_sort_and_sortperm": check_perm(k32, perm.cpu().numpy().view(np.uint32),
+                                                    sorted_out=arrays[1]["work"].cpu().numpy())}
+    if not all(verified.values()):
+        raise RuntimeError(f"output check failed: {verified}")
+    extra["output_checked"] = verified
+
+    # learned-CDF buckets vs plain radix, same run, outputs checked: the int64
+    # arrays (the library's own choice for them) and smooth float64 at this n
+    if not args.no_learned:
+        flush2 = flush
+        lvp = {}
+        cases = [("i64_uniform_sort", k64, ak.AK_I64, "sort"), ("i64_uniform_sortperm", k64, ak.AK_I64, "sortperm")]
+        for dist in ("uniform", "normal"):
+            cases.append((f"f64_{dist}_sort", synth.dist_f64(n, dist, seed=10 + synth.F64_DISTS.index(dist)),
+                          ak.AK_F64, "sort"))
+        del temp
+        torch.cuda.empty_cache()
+        for name, host, kd, op in cases:
+            r = {}
+            for pname, path in (("plain", ak.AK_PATH_RADIX), ("learned", ak.AK_PATH_LEARNED)):
+                gbs, ms, info, ok = time_sort(torch, ak, dev, stream, flush2, host, kd, {"path": path}, op,
+                                              warmup=args.warmup, steps=min(args.steps, 5))
+                if not ok:
+                    raise RuntimeError(f"output check failed: {name} {pname}")
+                r[f"{pname}_GBps"] = round(gbs, 2)
+                r[f"{pname}_ms"] = round(ms, 3)
+                if pname == "learned":
+                    r["learned_path_taken"] = PATH_NAMES.get(info["path"])
+            r["output_checked"] = True
+            r["learned_over_plain"] = round(r["learned_GBps"] / r["plain_GBps"], 3)
+            lvp[name] = r
+        extra["learned_vs_plain"] = lvp
+        temp = None
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n)
+        # the headline's own algorithm (plain radix), then the library's default choice
+        e2e = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n, path=ak.AK_PATH_RADIX)
+        extra["e2e_default_options"] = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, None, n)
 
     cpu = None
     if world == 1 and not args.no_cpu:
@@ -369,13 +541,18 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n):
+def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n, path=None):
     """Same four calls from pinned host buffers: H2D keys, sortperm, sort, D2H perm + sorted keys,
-    with default options (the library picks the path, as a caller's plain call does).  Copies run
+    through `path` (None: the library's own choice, as a caller's plain call gets).  Copies run
     on their own streams so that one array's upload and the other's downloads overlap the sorts
-    (events order every buffer reuse)."""
+    (events order every buffer reuse).  The last step's outputs are checked on the host."""
     del temp
-    temp = ak.workspace(max(ak.temp_bytes(op, n, kd) for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM)
+    opts = None
+    if path is not None:
+        opts = ak.Options()
+        opts.path = path
+    oref = ctypes.byref(opts) if opts is not None else None
+    temp = ak.workspace(max(ak.temp_bytes(op, n, kd, options=opts) for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM)
                             for kd in (ak.AK_I64, ak.AK_F32)), dev)
     hosts = [torch.from_numpy(k64).pin_memory(), torch.from_numpy(k32).pin_memory()]
     outs_k = [torch.empty_like(h).pin_memory() for h in hosts]
@@ -400,11 +577,11 @@ def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n):
         for i in range(2):
             stream.wait_event(loaded[i])
             rc = lib.ak_sortperm(dk[i].data_ptr(), dp[i].data_ptr(), n, kds[i], 0, temp.data_ptr(), temp.numel(),
-                                 stream.cuda_stream, None)
+                                 stream.cuda_stream, oref)
             perm_done = ev()
             perm_done.record(stream)
             rc |= lib.ak_sort(dk[i].data_ptr(), n, kds[i], 0, temp.data_ptr(), temp.numel(), stream.cuda_stream,
-                              None)
+                              oref)
             if rc:
                 raise ak.AkError(rc, "e2e")
             sort_done = ev()
@@ -433,16 +610,22 @@ def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n):
     ms = e0.elapsed_time(e1) / steps
     h2d = sum(h.numel() * h.element_size() for h in hosts)
     d2h = h2d + 2 * 4 * n
-    # the results of the last step are read back and spot-checked against the input multiset size
-    assert outs_k[0].numel() == n and outs_p[1].numel() == n
+    # the last step's results, read back to the host: each sortperm is THE stable one and the
+    # sorted keys are keys[perm]
+    ok = all(check_perm(src, outs_p[i].numpy().view(np.uint32), sorted_out=outs_k[i].numpy())
+             for i, src in enumerate((k64, k32)))
+    if not ok:
+        raise RuntimeError("e2e output check failed")
     paths = {}
     for i, kd in enumerate(kds):
         dk[i].copy_(hosts[i], non_blocking=True)
-        lib.ak_sort(dk[i].data_ptr(), n, kd, 0, temp.data_ptr(), temp.numel(), stream.cuda_stream, None)
-        paths["i64" if i == 0 else "f32"] = {1: "radix", 2: "learned", 3: "block"}.get(ak.ak_last_info(temp)["path"])
+        lib.ak_sort(dk[i].data_ptr(), n, kd, 0, temp.data_ptr(), temp.numel(), stream.cuda_stream, oref)
+        paths["i64" if i == 0 else "f32"] = PATH_NAMES.get(ak.ak_last_info(temp)["path"])
+    del dk, dp, temp
+    torch.cuda.empty_cache()
     return {"value": round(24 * n / (ms / 1e3) / 1e9, 3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(ms, 3), "steps": steps, "paths": paths,
-            "copies": "upload / download streams overlapping the sorts"}
+            "output_checked": True, "copies": "upload / download streams overlapping the sorts"}
 
 
 # ------------------------------------------------------------ other workloads
@@ -485,52 +668,18 @@ def run_workload(args):
     W, K = args.warmup, args.steps
 
     def sort_gbs(host, kd, opts, op="sort", vals=None, order="ascending"):
-        """Key GB/s of one operation on `host` keys (device-timed)."""
-        unsigned = host.dtype.kind == "u"
-        view = {1: np.int8, 2: np.int16, 4: np.int32, 8: np.int64}[host.itemsize] if unsigned else host.dtype
-        pristine = torch.from_numpy(host.view(view)).to(dev)
-        work = torch.empty_like(pristine)
-        o = ak.Options()
-        for k, v in (opts or {}).items():
-            setattr(o, k, v)
-        if op == "pairs":
-            vp = torch.from_numpy(vals.view(np.int32)).to(dev)
-            vw = torch.empty_like(vp)
-            tb = ak.temp_bytes(ak.AK_OP_SORT_PAIRS, host.size, kd, 4, options=o)
-        else:
-            vp = vw = None
-            tb = ak.temp_bytes(ak.AK_OP_SORT, host.size, kd, options=o)
-        temp = ak.workspace(tb, dev)
-        lib = ak.load()
-        od = ak.order_code(order)
-
-        def restore():
-            work.copy_(pristine)
-            if vw is not None:
-                vw.copy_(vp)
-
-        def call():
-            if op == "pairs":
-                rc = lib.ak_sort_pairs(work.data_ptr(), vw.data_ptr(), 4, host.size, kd, od, temp.data_ptr(),
-                                       temp.numel(), stream.cuda_stream, ctypes.byref(o))
-            else:
-                rc = lib.ak_sort(work.data_ptr(), host.size, kd, od, temp.data_ptr(), temp.numel(),
-                                 stream.cuda_stream, ctypes.byref(o))
-            if rc:
-                raise ak.AkError(rc, op)
-
-        ms = _timed(torch, stream, flush, restore, call, W, K)
-        info = ak.ak_last_info(temp)
-        del pristine, work, temp, vp, vw
-        torch.cuda.empty_cache()
-        return host.nbytes / (ms / 1e3) / 1e9, ms, info
+        """Key GB/s of one operation on `host` keys (device-timed; output checked)."""
+        gbs, ms, info, ok = time_sort(torch, ak, dev, stream, flush, host, kd, opts, op, vals, order, W, K)
+        if not ok:
+            raise RuntimeError(f"output check failed: {op} {host.dtype} {opts}")
+        return gbs, ms, info
 
     if args.workload == "c1":
         keys = synth.uniform_u32(1 << 20, seed=1)
         res = {}
         for name, opts in (("auto", None), ("radix", {"path": ak.AK_PATH_RADIX}), ("block", {"path": ak.AK_PATH_BLOCK})):
             gbs, ms, info = sort_gbs(keys, ak.AK_U32, opts)
-            res[name] = {"GBps": round(gbs, 2), "ms": round(ms, 4), "path": info["path"]}
+            res[name] = {"GBps": round(gbs, 2), "ms": round(ms, 4), "path": info["path"], "output_checked": True}
         best = max(v["GBps"] for v in res.values())
         _line(args, "1,048,576 u32 uniform, ak_sort ascending (L2-resident)", best,
               {"dtype": "u32", "results": res})
@@ -585,9 +734,17 @@ def run_workload(args):
 
         ms = _timed(torch, torch.cuda.current_stream(dev), flush, restore, call, W, K)
         gbs = keys.nbytes / (ms / 1e3) / 1e9
+        # output check: every segment is its own sorted multiset ((segment, key) as one u64)
+        got = work.cpu().numpy().view(np.uint32)
+        seg = np.repeat(np.arange(off.size - 1, dtype=np.uint64), np.diff(off))
+        comb = (seg << np.uint64(32)) | got.astype(np.uint64)
+        ok = bool(np.all(comb[1:] >= comb[:-1])) and _bits_hash(got) == _bits_hash(keys)
+        if not ok or ak.ak_status_check(temp) != 0:
+            raise RuntimeError("segmented output check failed")
         _line(args, f"{args.segments:,} segments, lognormal lengths (median 2,048), {n:,} u32 keys, one persistent launch "
               "replayed from a CUDA graph", gbs,
-              {"dtype": "u32", "ms": round(ms, 4), "keys": n, "roofline_2x_bytes_frac_of_measured": round(2 * gbs / peak, 4)})
+              {"dtype": "u32", "ms": round(ms, 4), "keys": n, "output_checked": True,
+               "roofline_2x_bytes_frac_of_measured": round(2 * gbs / peak, 4)})
     elif args.workload == "c5":
         n = args.n if args.n != FULL_N else 1 << 30
         keys = synth.zipf_mix_u32(n, seed=30, workers=os.cpu_count() or 1)

@@ -196,7 +196,11 @@ ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg
  * capture.  All calls share the one array: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller.  Results,
  * ordering and stability are those of ak_sort; device-side timeouts are recorded
- * only in the shared array and are not returned.
+ * only in the shared array and are not returned (a caller that needs them uses
+ * ak_sort with its own workspace and ak_status_check).  The cached address is
+ * that of the device's current context: a device reset (cudaDeviceReset, or
+ * the primary context destroyed and re-created) is not supported for this entry
+ * point within the same process.
  */
 #define AK_STATIC_SCRATCH_BYTES (32u << 20)
 ak_status ak_sort_static_scratch(void *d_keys, int64_t n, ak_dtype kd, ak_order order, ak_stream_t stream);

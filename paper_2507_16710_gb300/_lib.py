@@ -168,6 +168,10 @@ def _contig_cuda(t: torch.Tensor, what: str):
         raise ValueError(f"{what} must be a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{what} must be contiguous")
+    # the library launches on the current device with the current device's stream
+    if t.device.index is not None and t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{what} is on {t.device}, but the current CUDA device is "
+                         f"cuda:{torch.cuda.current_device()}; call under torch.cuda.device({t.device})")
 
 
 def temp_bytes(op: int, n: int, kd: int, val_bytes: int = 0, nseg: int = 0, options=None) -> int:

@@ -1,0 +1,51 @@
+"""The bench's own output checks (host only): they accept the oracle's results
+and reject planted mistakes, so a GB/s figure can only come from a correct sort."""
+import numpy as np
+import pytest
+
+import bench
+import oracle
+import synth
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.int32, np.float32, np.int64, np.float64])
+@pytest.mark.parametrize("desc", [False, True])
+def test_checks_accept_the_oracle(dtype, desc):
+    keys = synth.random_keys(20_011, dtype, seed=5, mode="dups")
+    order = "descending" if desc else "ascending"
+    p = oracle.sortperm(keys, order)
+    out = oracle.gather(keys, p)
+    assert bench.check_sorted(keys, out, desc)
+    assert bench.check_perm(keys, p.astype(np.uint32), desc, sorted_out=out)
+
+
+def test_checks_reject_planted_mistakes():
+    keys = synth.normal_f32_special(10_007, seed=9, frac=0.02)
+    p = oracle.sortperm(keys)
+    out = oracle.gather(keys, p)
+    # two neighbours swapped: out of order
+    bad = out.copy()
+    bad[[100, 101]] = bad[[101, 100]]
+    if bench._order_key(bad[100:101])[0] != bench._order_key(bad[101:102])[0]:
+        assert not bench.check_sorted(keys, bad)
+    # one key replaced by its neighbour: sorted, but not the input's multiset
+    dup = out.copy()
+    dup[200] = dup[199]
+    assert not bench.check_sorted(keys, dup)
+    # -0.0 after +0.0 is out of Julia's order
+    z = np.array([0.0, -0.0], dtype=np.float32)
+    assert not bench.check_sorted(z, z)
+    assert bench.check_sorted(z, z[::-1].copy())
+    # two NaNs (equivalent keys) swapped in the permutation: sorted, same
+    # multiset, but not stable
+    ties = np.where(np.isnan(out))[0]
+    assert ties.size >= 2
+    q = p.copy()
+    q[[ties[0], ties[1]]] = q[[ties[1], ties[0]]]
+    assert not bench.check_perm(keys, q.astype(np.uint32))
+    # not a permutation
+    r = p.copy()
+    r[0] = r[1]
+    assert not bench.check_perm(keys, r.astype(np.uint32))
+    # a permutation whose gather disagrees with the returned keys
+    assert not bench.check_perm(keys, p.astype(np.uint32), sorted_out=dup)
