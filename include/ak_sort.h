@@ -85,7 +85,9 @@ typedef struct ak_options {
     int32_t tile_config;   /* digit-pass variant, 0 = default (1), else 1..AK_TILE_CONFIGS:
                               1 persistent 512-thread CTAs, 32 KB tiles; 2 persistent
                               384-thread CTAs, 24 KB tiles; 3 one 512-thread CTA per
-                              32 KB tile with an L2 prefetch one wave ahead */
+                              32 KB tile with an L2 prefetch one wave ahead; 4 persistent
+                              512-thread CTAs whose last warp does the look-back while
+                              the others rank the next tile (three tile buffers) */
     int32_t bucket_bits;   /* learned path: log2 of the bucket count, 8..16 (NaN keys share
                               the last bucket); 0 = auto, about half the shared-memory
                               finish capacity (ak_segment_capacity) per bucket */
@@ -111,7 +113,7 @@ typedef struct ak_options {
  * persistent configurations prefetch each claimed tile, unaffected). */
 #define AK_DEBUG_NO_PREFETCH 2
 
-#define AK_TILE_CONFIGS 3
+#define AK_TILE_CONFIGS 4
 
 /* Diagnostics written by the device for the most recent call on a d_temp. */
 typedef struct ak_info {

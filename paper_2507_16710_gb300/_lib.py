@@ -21,7 +21,7 @@ AK_U16, AK_I16, AK_U32, AK_I32, AK_U64, AK_I64, AK_F32, AK_F64 = range(8)
 AK_ASCENDING, AK_DESCENDING = 0, 1
 AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED = range(4)
 AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK, AK_PATH_MERGE = range(5)
-AK_TILE_CONFIGS = 3
+AK_TILE_CONFIGS = 4
 AK_DEBUG_SKIP_FIRST_TILE = 1
 AK_MAX_PASSES = 8
 STATUS_NAMES = {0: "AK_OK", 1: "AK_ERR_INVALID_ARG", 2: "AK_ERR_UNSUPPORTED",

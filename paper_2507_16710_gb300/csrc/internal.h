@@ -57,21 +57,56 @@ cudaError_t radix_launch_u64_float(const RadixCall &c);
 // threads and a tile of about CFG_BYTES[c] bytes of keys+values (keys per
 // thread clamped to [2, 12]).  Persistent configurations launch one wave of
 // CTAs that loop over tiles, each copying its next tile in while it finishes
-// the current one; the other launches one CTA per tile.
-constexpr int CFG_BLOCK[3] = {512, 384, 512};
-constexpr int CFG_BYTES[3] = {32768, 24576, 32768};
-constexpr bool CFG_PERSIST[3] = {true, true, false};
+// the current one; configuration 2 launches one CTA per tile.  Configuration
+// 3 is the pass with a dedicated look-back warp (onesweep_ws.cuh): 15 compute
+// warps of the 16, keys per thread as many as three tile buffers allow with
+// two CTAs per SM.
+constexpr int CFG_BLOCK[4] = {512, 384, 512, 512};
+constexpr int CFG_BYTES[4] = {32768, 24576, 32768, 0};
+constexpr bool CFG_PERSIST[4] = {true, true, false, true};
+constexpr int CFG_WS = 3;
+
+constexpr int WS_BLOCK = 512;       // threads of the look-back-warp pass
+constexpr int WS_NCW = 15;          // its compute warps (the last warp looks back)
+constexpr int WS_NC = WS_NCW * 32;  // its compute threads
+constexpr size_t WS_SMEM_LIMIT = 114 * 1024;  // shared memory per CTA with two CTAs per SM
+
+// Shared memory of the look-back-warp pass (onesweep_ws.cuh: WsSmem): three
+// tile buffers, two digit arrays, per-warp digit counters, optional per-warp
+// peer words, per-digit state of two tiles.
+constexpr size_t ws_smem_bytes(int key_bytes, int val_bytes, int items, bool peer_words) {
+  const size_t tile = size_t(WS_NC) * items;
+  const size_t buf = (tile * (key_bytes + val_bytes) + 127) / 128 * 128;
+  const size_t hist = (size_t(257) * 9 * 4 + 15) / 16 * 16;
+  const size_t mask = peer_words ? (size_t(WS_NCW) * 257 * 4 + 15) / 16 * 16 : 0;
+  return 3 * buf + (2 * tile + 15) / 16 * 16 + hist + mask + 256 * 8 + 2 * 256 * 4 + 2 * 256 * 8 + 32 + 40 + 16 + 8 +
+         16;
+}
+// Keys per compute thread: its keys, values and digit/rank words stay in
+// registers from load to scatter, about 21 registers' worth; and three tile
+// buffers fit with two CTAs per SM.
+constexpr int ws_items(int key_bytes, int val_bytes, bool peer_words) {
+  const int regs = (key_bytes + 3) / 4 + (val_bytes + 3) / 4 + 1;
+  int it = 21 / regs < 12 ? 21 / regs : 12;
+  if (val_bytes == 0 && key_bytes <= 4 && it > 8) it = 8;  // more spills registers (ptxas -v)
+  while (it > 2 && ws_smem_bytes(key_bytes, val_bytes, it, peer_words) > WS_SMEM_LIMIT) --it;
+  return it;
+}
+#ifndef AK_WS_RANK
+#define AK_WS_RANK 0
+#endif
 
 constexpr int tile_items(int key_bytes, int val_bytes, int cfg) {
-  return (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) < 2    ? 2
+  return cfg == CFG_WS ? ws_items(key_bytes, val_bytes, AK_WS_RANK == 1)
+         : (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) < 2  ? 2
          : (CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes))) > 12 ? 12
                                                                                : CFG_BYTES[cfg] / (CFG_BLOCK[cfg] * (key_bytes + val_bytes));
 }
 constexpr int tile_keys(int key_bytes, int val_bytes, int cfg) {
-  return CFG_BLOCK[cfg] * tile_items(key_bytes, val_bytes, cfg);
+  return (cfg == CFG_WS ? WS_NC : CFG_BLOCK[cfg]) * tile_items(key_bytes, val_bytes, cfg);
 }
-// 64-bit look-back words (n > 2^30) are only built for configuration 0.
-constexpr int effective_cfg(int cfg, bool status_wide) { return status_wide ? 0 : cfg; }
+// 64-bit look-back words (n > 2^30) are built for configurations 0 and 3.
+constexpr int effective_cfg(int cfg, bool status_wide) { return status_wide && cfg != CFG_WS ? 0 : cfg; }
 
 // One segmented sort (or a single segment when off == NULL) on device buffers.
 struct SegCall {

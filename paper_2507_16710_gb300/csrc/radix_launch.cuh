@@ -10,6 +10,7 @@
 
 #include "internal.h"
 #include "onesweep.cuh"
+#include "onesweep_ws.cuh"
 
 namespace ak {
 
@@ -33,17 +34,38 @@ int resident_ctas(K kern, int block, size_t smem) {
   return nb;
 }
 
+// Digit-pass kernel, its block size, shared memory and tile of a configuration.
+template <typename U, typename V, bool HAS_V, int KIND, typename S, int CFG, int DIGIT = DIGIT_RADIX>
+struct PassKernel {
+  static constexpr int ITEMS = tile_items(sizeof(U), HAS_V ? sizeof(V) : 0, CFG);
+  static constexpr int BLOCK = CFG_BLOCK[CFG];
+  static constexpr bool PERSIST = CFG_PERSIST[CFG];
+  static constexpr int TILE = tile_keys(sizeof(U), HAS_V ? sizeof(V) : 0, CFG);
+  static constexpr size_t bytes() {
+    if constexpr (CFG == CFG_WS) return WsSmem<U, V, HAS_V, ITEMS, AK_WS_RANK>::BYTES;
+    else return PassSmem<U, V, HAS_V, BLOCK, ITEMS>::BYTES;
+  }
+  static constexpr size_t BYTES = bytes();
+  static auto kernel() {
+    if constexpr (CFG == CFG_WS) return onesweep_ws_pass<U, V, HAS_V, KIND, S, ITEMS, DIGIT, AK_WS_RANK>;
+    else return onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, PERSIST, DIGIT>;
+  }
+  static_assert(CFG == CFG_WS ? WsSmem<U, V, HAS_V, ITEMS, AK_WS_RANK>::TILE == TILE
+                              : PassSmem<U, V, HAS_V, BLOCK, ITEMS>::TILE == TILE,
+                "tile shape");
+};
+
 template <typename U, typename V, bool HAS_V, int KIND, typename S, int CFG>
 cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
-  constexpr int BLOCK = CFG_BLOCK[CFG];
-  constexpr int ITEMS = tile_items(sizeof(U), HAS_V ? sizeof(V) : 0, CFG);
-  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
-  static_assert(L::TILE == tile_keys(sizeof(U), HAS_V ? sizeof(V) : 0, CFG), "tile shape");
-  constexpr bool PERSIST = CFG_PERSIST[CFG];
-  auto kern = onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, PERSIST>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::BYTES));
+  using P = PassKernel<U, V, HAS_V, KIND, S, CFG>;
+  constexpr int BLOCK = P::BLOCK;
+  constexpr bool PERSIST = P::PERSIST;
+  constexpr int TILE = P::TILE;
+  constexpr size_t BYTES = P::BYTES;
+  auto kern = P::kernel();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BYTES));
   if (e != cudaSuccess) return e;
-  const int64_t tiles = (c.n + L::TILE - 1) / L::TILE;
+  const int64_t tiles = (c.n + TILE - 1) / TILE;
   a.num_tiles = tiles;
   constexpr int PASSES = sizeof(U);
   const int sms = device_sm_count();
@@ -57,7 +79,7 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
                                                    c.gate, c.gate_want);
   }
   plan_kernel<<<1, RADIX, 0, c.stream>>>(c.counts, c.n, PASSES, c.plan, c.hdr, c.path_tag, c.gate, c.gate_want);
-  const int64_t wave = int64_t(resident_ctas(kern, BLOCK, L::BYTES)) * sms;
+  const int64_t wave = int64_t(resident_ctas(kern, BLOCK, BYTES)) * sms;
   const int64_t resident = PERSIST ? wave : tiles;
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, resident)));
   a.prefetch_ahead = (PERSIST || (c.debug_flags & AK_DEBUG_NO_PREFETCH)) ? 0 : wave;
@@ -66,7 +88,7 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
     a.status_cur = c.status[p & 1];
     a.status_next = (p + 1 < PASSES) ? c.status[(p + 1) & 1] : nullptr;
     if (c.pass_events) cudaEventRecord(reinterpret_cast<cudaEvent_t>(c.pass_events[2 * p]), c.stream);
-    kern<<<grid, BLOCK, L::BYTES, c.stream>>>(a);
+    kern<<<grid, BLOCK, BYTES, c.stream>>>(a);
     if (c.pass_events) cudaEventRecord(reinterpret_cast<cudaEvent_t>(c.pass_events[2 * p + 1]), c.stream);
   }
   {
@@ -97,10 +119,14 @@ cudaError_t run_status(const RadixCall &c) {
   a.debug_skip = (c.debug_flags & AK_DEBUG_SKIP_FIRST_TILE) ? 1 : 0;
   a.gate = c.gate;
   a.gate_want = c.gate_want;
-  if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, 0>(c, a);
+  if (c.status_wide) {  // 64-bit look-back words: configurations 0 and 3
+    if (c.tile_config == CFG_WS) return run_passes<U, V, HAS_V, KIND, unsigned long long, CFG_WS>(c, a);
+    return run_passes<U, V, HAS_V, KIND, unsigned long long, 0>(c, a);
+  }
   switch (c.tile_config) {
     case 1: return run_passes<U, V, HAS_V, KIND, uint32_t, 1>(c, a);
     case 2: return run_passes<U, V, HAS_V, KIND, uint32_t, 2>(c, a);
+    case CFG_WS: return run_passes<U, V, HAS_V, KIND, uint32_t, CFG_WS>(c, a);
     default: return run_passes<U, V, HAS_V, KIND, uint32_t, 0>(c, a);
   }
 }

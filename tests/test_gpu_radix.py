@@ -77,7 +77,7 @@ def test_pairs_match_oracle(ak, dtype, vdtype, desc):
     assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), "pair values")
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4])
 @pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float32, np.uint16])
 def test_every_tile_config(ak, cfg, dtype):
     opts = {"tile_config": cfg, "path": ak.AK_PATH_RADIX}
@@ -87,6 +87,38 @@ def test_every_tile_config(ak, cfg, dtype):
             p = oracle_perm(keys, desc)
             assert_bits_equal(_run_sort(ak, keys, desc, opts), oracle.gather(keys, p), f"cfg {cfg} n={n}")
             assert np.array_equal(_run_perm(ak, keys, desc, opts), p.astype(np.uint32))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("vdtype", [None, np.uint8, np.uint16, np.uint32, np.uint64])
+def test_lookback_warp_config_tile_boundaries(ak, dtype, vdtype):
+    """Tile configuration 4 (the look-back warp): sort, sortperm and pairs of
+    every value width, both orders, at one tile -1/0/+1 and several tiles with
+    a ragged tail, on heavy-duplicate keys (long runs of equal digits)."""
+    opts = {"tile_config": 4, "path": ak.AK_PATH_RADIX}
+    kb = np.dtype(dtype).itemsize
+    vb = 0 if vdtype is None else np.dtype(vdtype).itemsize
+    regs = (kb + 3) // 4 + (vb + 3) // 4 + 1
+    items = min(21 // regs, 12)
+    if vb == 0 and kb <= 4:
+        items = min(items, 8)
+    tile = 480 * items  # smem never limits these widths below the register bound
+    for n in (tile - 1, tile, tile + 1, 7 * tile + 13):
+        keys = synth.random_keys(n, dtype, seed=7000 + n + kb, mode="dups" if n % 2 else "bits")
+        for desc in (False, True):
+            order = "descending" if desc else "ascending"
+            p = oracle_perm(keys, desc)
+            if vdtype is None:
+                assert_bits_equal(_run_sort(ak, keys, desc, opts), oracle.gather(keys, p), f"ws sort n={n}")
+                assert np.array_equal(_run_perm(ak, keys, desc, opts), p.astype(np.uint32)), f"ws sortperm n={n}"
+            else:
+                vals = synth.splitmix64(7001, n).astype(vdtype)
+                kt, ku = to_dev(keys)
+                vt, _ = to_dev(vals)
+                ak.ak_sort_pairs(kt, vt, order, options=opts, unsigned=ku)
+                torch.cuda.synchronize()
+                assert_bits_equal(to_host(kt, keys.dtype), oracle.gather(keys, p), f"ws pair keys n={n}")
+                assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), f"ws pair values n={n}")
 
 
 def test_trivial_passes_and_all_equal(ak):
@@ -138,12 +170,14 @@ def test_empty_and_errors(ak):
         ak.ak_sort(torch.zeros(10, device="cuda"), temp=torch.empty(16, dtype=torch.uint8, device="cuda"))
 
 
-def test_lookback_timeout_reports_status(ak):
+@pytest.mark.parametrize("cfg", [0, 4])
+def test_lookback_timeout_reports_status(ak, cfg):
     """The test hook leaves tile 0 of every pass unowned: tile 1's look-back
     must give up after timeout_ns and the status word must say so."""
     keys = synth.random_keys(20000, np.uint32, seed=9, mode="bits")
     t, u = to_dev(keys)
-    opts = {"path": ak.AK_PATH_RADIX, "timeout_ns": 2_000_000, "debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE}
+    opts = {"path": ak.AK_PATH_RADIX, "timeout_ns": 2_000_000, "debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE,
+            "tile_config": cfg}
     temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, keys.size, ak.AK_U32, options=opts), t.device)
     ak.ak_sort(t, temp=temp, options=opts, unsigned=u)
     assert ak.ak_status_check(temp) == 5
