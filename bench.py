@@ -487,6 +487,14 @@ def run_ours(args):
         raise RuntimeError(f"output check failed: {verified}")
     extra["output_checked"] = verified
 
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        extra["host_link_GBps"] = host_link_bandwidth(torch, dev)
+        # the headline's own algorithm (plain radix), then the library's default choice
+        e2e = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, None, n, path=ak.AK_PATH_RADIX)
+        extra["e2e_default_options"] = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, None, n)
+
     # learned-CDF buckets vs plain radix, same run, outputs checked: the int64
     # arrays (the library's own choice for them) and smooth float64 at this n
     if not args.no_learned:
@@ -515,12 +523,6 @@ def run_ours(args):
         extra["learned_vs_plain"] = lvp
         temp = None
 
-    # end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        # the headline's own algorithm (plain radix), then the library's default choice
-        e2e = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n, path=ak.AK_PATH_RADIX)
-        extra["e2e_default_options"] = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, None, n)
 
     cpu = None
     if world == 1 and not args.no_cpu:
@@ -539,6 +541,27 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def host_link_bandwidth(torch, dev, nbytes=1 << 30):
+    """Plain pinned-host <-> device copy bandwidth (GB/s) of nbytes each way, the
+    ceiling of the e2e leg's copies on this machine."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, (dst, src) in (("h2d", (d, h)), ("d2h", (h, d))):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        res[name] = round(3 * nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    del h, d
+    torch.cuda.empty_cache()
+    return res
 
 
 def measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, temp, n, path=None):

@@ -473,7 +473,9 @@ __global__ void __launch_bounds__(WS_BLOCK, 2) onesweep_ws_pass(PassArgs<U, V> a
         const uint32_t w = hrow[v];
         const uint32_t lo = run, hi = run + (w & 0xFFFFu);
         run = hi + (w >> 16);
-        hrow[v] = (lo & 0xFFFFu) | (hi << 16);
+        // column WS_NCW belongs to no compute warp: it stays 0, as the next
+        // tile's counts sum every column of the row
+        hrow[v] = (lo & 0xFFFFu) | (2 * v + 1 < WS_NCW ? (hi << 16) : 0u);
       }
     }
     named_sync(1, WS_NC);  // C9: warp bases ready

@@ -121,6 +121,25 @@ def test_lookback_warp_config_tile_boundaries(ak, dtype, vdtype):
                 assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), f"ws pair values n={n}")
 
 
+@pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float32, np.float64])
+def test_lookback_warp_config_many_tiles_per_cta(ak, dtype):
+    """Tile configuration 4 with several tiles per persistent CTA (5M keys:
+    every CTA rotates through its three tile buffers and both look-back slots
+    more than once); sort, sortperm and pairs against the oracle."""
+    opts = {"tile_config": 4, "path": ak.AK_PATH_RADIX}
+    n = 5_000_003
+    keys = synth.random_keys(n, dtype, seed=7100, mode="bits")
+    p = oracle_perm(keys, False, threads=8)
+    assert_bits_equal(_run_sort(ak, keys, False, opts), oracle.gather(keys, p), "ws sort, many tiles")
+    assert np.array_equal(_run_perm(ak, keys, False, opts), p.astype(np.uint32)), "ws sortperm, many tiles"
+    vals = np.arange(n, dtype=np.uint32)
+    kt, ku = to_dev(keys)
+    vt, _ = to_dev(vals)
+    ak.ak_sort_pairs(kt, vt, options=opts, unsigned=ku)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(vt, np.uint32), p.astype(np.uint32)), "ws pairs, many tiles"
+
+
 def test_trivial_passes_and_all_equal(ak):
     # every key equal: all passes trivial; sortperm must be the identity
     keys = np.full(70000, 7, dtype=np.int64)
