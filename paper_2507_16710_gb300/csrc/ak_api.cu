@@ -151,7 +151,7 @@ static cudaError_t seg_dispatch(int key_bytes, const SegCall &c) {
 
 // Workspace of the segmented / one-launch block path.
 struct SegLayout {
-  size_t hdr, counters, order, alt_k, alt_v, key_copy, total;
+  size_t hdr, counters, split_state, order, alt_k, alt_v, key_copy, split_big, split_tcount, split_buckets, total;
 };
 
 static SegLayout seg_layout(int op, int64_t n, int64_t nseg, int key_bytes, int vb) {
@@ -160,6 +160,8 @@ static SegLayout seg_layout(int op, int64_t n, int64_t nseg, int key_bytes, int 
   L.hdr = off;
   off += align256(sizeof(DevHeader));
   L.counters = off;
+  off += 256;
+  L.split_state = off;  // zeroed with the header
   off += 256;
   L.order = off;
   off += align256(size_t(nseg > 0 ? nseg : 1) * 4);
@@ -171,6 +173,14 @@ static SegLayout seg_layout(int op, int64_t n, int64_t nseg, int key_bytes, int 
   if (op == AK_OP_SORTPERM) {  // the keys are read-only: sort a copy
     L.key_copy = off;
     off += align256(size_t(n) * key_bytes);
+  }
+  if (op == AK_OP_SORT_SEGMENTED) {  // device-wide split of segments above the shared capacity
+    L.split_big = off;
+    off += align256(size_t(split_big_cap(n, key_bytes, vb)) * 32);
+    L.split_tcount = off;
+    off += align256(size_t(split_tile_cap(n, key_bytes, vb)) * RADIX * 4);
+    L.split_buckets = off;
+    off += align256(size_t(split_bucket_cap(n, key_bytes, vb)) * 16);
   }
   L.total = off;
   return L;
@@ -248,6 +258,12 @@ static ak_status run_seg(int op, void *keys, const int64_t *off, int64_t nseg, i
   c.hdr = reinterpret_cast<DevHeader *>(t + L.hdr);
   c.path_tag = merge ? AK_PATH_MERGE : AK_PATH_BLOCK;
   c.merge = merge;
+  if (op == AK_OP_SORT_SEGMENTED) {
+    c.split_state = t + L.split_state;
+    c.split_big = t + L.split_big;
+    c.split_tcount = reinterpret_cast<uint32_t *>(t + L.split_tcount);
+    c.split_buckets = t + L.split_buckets;
+  }
   c.stream = stream;
   return seg_dispatch(ki.bytes, c) == cudaSuccess ? AK_OK : AK_ERR_CUDA;
 }

@@ -108,6 +108,10 @@ constexpr int tile_keys(int key_bytes, int val_bytes, int cfg) {
 // 64-bit look-back words (n > 2^30) are built for configurations 0 and 3.
 constexpr int effective_cfg(int cfg, bool status_wide) { return status_wide && cfg != CFG_WS ? 0 : cfg; }
 
+// Keys of one segment the shared-memory sort takes (a multiple of 32): 80 KB
+// of keys, values and 16-bit positions, so two CTAs fit an SM.
+constexpr int seg_cap(int key_bytes, int val_bytes) { return (81920 / (key_bytes + val_bytes + 2)) / 32 * 32; }
+
 // One segmented sort (or a single segment when off == NULL) on device buffers.
 struct SegCall {
   void *keys, *vals;       // in place; vals NULL for keys only
@@ -123,8 +127,35 @@ struct SegCall {
   const uint32_t *gate;    // if set, run only when *gate == gate_want
   uint32_t gate_want;
   int merge;               // off == NULL: sort tiles of the shared-memory capacity, then merge them
+  // device-wide split of segments above the shared capacity (segsplit.cuh);
+  // all NULL: one CTA sorts such a segment through global memory by itself
+  void *split_state;       // SplitState, zeroed
+  void *split_big;         // BigSeg[split_big_cap]
+  uint32_t *split_tcount;  // RADIX counters per split tile
+  void *split_buckets;     // BucketItem[split_bucket_cap]
   cudaStream_t stream;
 };
+// Split workspace of a segmented sort of n keys (key_bytes + val_bytes wide):
+// big segments hold more than the shared capacity each; every one of them
+// gets at most 4 len / CAP non-empty buckets (buckets average more than CAP / 4).
+constexpr int64_t split_big_cap(int64_t n, int key_bytes, int val_bytes) {
+  return n / (seg_cap(key_bytes, val_bytes) + 1) + 1;
+}
+constexpr int64_t split_bucket_cap(int64_t n, int key_bytes, int val_bytes) {
+  return 4 * (n / seg_cap(key_bytes, val_bytes)) + 256;
+}
+// Split tiles: SPLIT_BLOCK threads x up to 8 keys, about 32 KB of keys and values.
+constexpr int SPLIT_BLOCK = 512;
+constexpr int SPLIT_TILE_BYTES = 32768;
+constexpr int split_items(int key_bytes, int val_bytes) {
+  return SPLIT_TILE_BYTES / (SPLIT_BLOCK * (key_bytes + val_bytes)) < 1   ? 1
+         : SPLIT_TILE_BYTES / (SPLIT_BLOCK * (key_bytes + val_bytes)) > 8 ? 8
+                                                                          : SPLIT_TILE_BYTES / (SPLIT_BLOCK * (key_bytes + val_bytes));
+}
+constexpr int split_tile(int key_bytes, int val_bytes) { return SPLIT_BLOCK * split_items(key_bytes, val_bytes); }
+constexpr int64_t split_tile_cap(int64_t n, int key_bytes, int val_bytes) {
+  return n / split_tile(key_bytes, val_bytes) + split_big_cap(n, key_bytes, val_bytes) + 1;
+}
 
 // Learned-CDF path: model, sample and finish regions of the workspace.
 struct LearnedCall {
@@ -153,9 +184,6 @@ cudaError_t learned_launch_u64_sint(const RadixCall &c, const LearnedCall &lc);
 cudaError_t learned_launch_u64_float(const RadixCall &c, const LearnedCall &lc);
 size_t learned_model_bytes();
 size_t learned_partials_bytes();
-// Keys of one segment the shared-memory sort takes (a multiple of 32): 80 KB
-// of keys, values and 16-bit positions, so two CTAs fit an SM.
-constexpr int seg_cap(int key_bytes, int val_bytes) { return (81920 / (key_bytes + val_bytes + 2)) / 32 * 32; }
 cudaError_t seg_launch_u16_uint(const SegCall &c);
 cudaError_t seg_launch_u16_sint(const SegCall &c);
 cudaError_t seg_launch_u32_uint(const SegCall &c);

@@ -511,7 +511,8 @@ __global__ void __launch_bounds__(WS_BLOCK, 2) onesweep_ws_pass(PassArgs<U, V> a
     prev_tile = tile;
     prev_n = tile_n;
   }
-  if (!aborted && prev_tile >= 0) {
+  if (!aborted && prev_tile >= 0) {  // (uniform: every compute thread left the loop at the same point)
+    named_sync(1, WS_NC);  // the last tile's scatter is complete in every warp
     if (mbar_wait_bounded(bar_lb + ((j - 1) & 1u), ((j - 1) >> 1) & 1u, a.timeout_ns)) {
       write_out(j - 1, prev_n);
     } else {

@@ -8,6 +8,7 @@
 #include "merge.cuh"
 #include "radix_launch.cuh"
 #include "segsort.cuh"
+#include "segsplit.cuh"
 
 namespace ak {
 
@@ -42,13 +43,40 @@ cudaError_t seg_run(const SegCall &c) {
   a.alt_v = reinterpret_cast<V *>(c.alt_v);
   a.flip = c.descending ? U(~U(0)) : U(0);
   a.seg_base = 0;
-  if (c.off && c.nseg > 0) {
+  const int sms = device_sm_count();
+  const bool split = c.off && c.nseg > 0 && c.split_state;
+  if (split) {  // long segments cut into buckets by all CTAs first (segsplit.cuh)
+    constexpr int SI = split_items(sizeof(U), HAS_V ? sizeof(V) : 0);
+    constexpr int64_t T = SPLIT_BLOCK * SI;
+    using SL = SplitSmem<U, V, HAS_V, KIND, SI>;
+    auto st = reinterpret_cast<SplitState *>(c.split_state);
+    auto big = reinterpret_cast<BigSeg *>(c.split_big);
+    auto bk = reinterpret_cast<BucketItem *>(c.split_buckets);
+    const int64_t g = (c.nseg + 255) / 256;
+    split_classify_kernel<<<unsigned(g), 256, 0, c.stream>>>(c.off, c.nseg, c.n, CAP, c.order, big, st, c.gate,
+                                                             c.gate_want);
+    split_tiles_kernel<<<1, 1024, 0, c.stream>>>(big, st, T, c.gate, c.gate_want);
+    split_vary_kernel<U, KIND><<<unsigned(sms * 4), SPLIT_BLOCK, 0, c.stream>>>(a.keys, big, st, T, a.flip, c.gate,
+                                                                                c.gate_want);
+    split_count_kernel<U, KIND><<<unsigned(sms * 4), SPLIT_BLOCK, 0, c.stream>>>(a.keys, big, st, T, CAP, a.flip,
+                                                                                 c.split_tcount, c.gate, c.gate_want);
+    split_scan_kernel<<<unsigned(sms * 8), RADIX, 0, c.stream>>>(big, st, c.split_tcount, bk, c.gate, c.gate_want);
+    auto sk = split_scatter_kernel<U, V, HAS_V, KIND, SI>;
+    e = cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SL::BYTES));
+    if (e != cudaSuccess) return e;
+    const int64_t sres = int64_t(resident_ctas(sk, SPLIT_BLOCK, SL::BYTES)) * sms;
+    sk<<<unsigned(sres), SPLIT_BLOCK, SL::BYTES, c.stream>>>(a.keys, a.vals, a.alt_k, a.alt_v, big, st,
+                                                               c.split_tcount, CAP, a.flip, c.gate, c.gate_want);
+    a.split = st;
+    a.buckets = bk;
+  } else if (c.off && c.nseg > 0) {
     const int64_t g = (c.nseg + 255) / 256;
     classify_kernel<<<unsigned(g), 256, 0, c.stream>>>(c.off, c.nseg, c.n, CAP, c.order, c.counters, c.gate,
                                                        c.gate_want);
   }
-  const int64_t resident = int64_t(resident_ctas(kern, SEG_BLOCK, Lay::BYTES)) * device_sm_count();
-  const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(a.nseg, resident)));
+  const int64_t resident = int64_t(resident_ctas(kern, SEG_BLOCK, Lay::BYTES)) * sms;
+  // with the split the work items (buckets + short segments) are counted on the device
+  const unsigned grid = unsigned(std::max<int64_t>(1, split ? resident : std::min<int64_t>(a.nseg, resident)));
   kern<<<grid, SEG_BLOCK, Lay::BYTES, c.stream>>>(a);
   if (!c.off && c.merge && c.n > CAP) {
     // merge rounds: runs of CAP * 2^r, ping-pong between the keys and the workspace copy

@@ -30,6 +30,27 @@ namespace ak {
 constexpr int SUB_BITS = 12;  // at most 2^SUB_BITS sub-ranges per segment
 constexpr int SUB_MAX = 48;   // largest sub-range the insertion sort takes
 
+struct SplitState {  // zeroed by the caller
+  uint32_t nbig;     // big segments
+  uint32_t nsmall;   // short segments in the work list
+  uint32_t nbuck;    // bucket work items
+  uint32_t ntiles;   // split tiles over all big segments
+  uint32_t pad[4];
+};
+
+struct BigSeg {
+  int64_t lo, len;              // key range [lo, lo + len)
+  unsigned long long vary;      // OR of (radix key ^ radix key of keys[lo])
+  uint32_t tile0;               // first split tile
+  uint32_t pad;
+};
+
+struct BucketItem {
+  int64_t lo, len;  // [lo, lo + len) in the workspace copy; sorted into the keys
+};
+static_assert(sizeof(BigSeg) == 32 && sizeof(BucketItem) == 16, "workspace sizes of the split tables");
+
+
 struct SegArgsBase {
   const int64_t *off;     // nseg + 1 offsets (clamped to [0, n] on read); NULL: tiles of tile_len
   int64_t tile_len;       // off == NULL: segment s = [s * tile_len, (s + 1) * tile_len) within [0, n)
@@ -40,6 +61,10 @@ struct SegArgsBase {
   int path_tag;           // written to ak_info.path by block 0
   const uint32_t *gate;   // if set, run only when *gate == gate_want
   uint32_t gate_want;
+  // device-wide split (segsplit.cuh): work items are the buckets of the long
+  // segments (workspace copy -> keys), then the short segments of `order`
+  const SplitState *split;
+  const BucketItem *buckets;
 };
 
 template <typename U, typename V>
@@ -488,13 +513,33 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
   c.init(smem, a.flip);
   uint32_t *s_work = c.s_misc;
   if (blockIdx.x == 0 && c.tid == 0 && a.path_tag) a.hdr->info.path = a.path_tag;
+  int64_t nbuck = 0, nwork = a.nseg;
+  if (a.split) {
+    nbuck = a.split->nbuck;
+    nwork = nbuck + a.split->nsmall;
+  }
   while (true) {
     if (c.tid == 0) s_work[0] = atomicAdd(&a.hdr->work_counter[0], 1u);
     __syncthreads();
     const int64_t w = s_work[0];
     __syncthreads();
-    if (w >= a.nseg) break;
-    const int64_t s = a.order ? a.order[w] : w;
+    if (w >= nwork) break;
+    if (w < nbuck) {  // a bucket of a long segment: from the workspace copy into the keys
+      const BucketItem it = a.buckets[w];
+      const int64_t g = a.seg_base + it.lo;
+      const int64_t len = it.len;
+      U *sk = a.alt_k + g;
+      V *sv = HAS_V ? a.alt_v + g : nullptr;
+      if (len <= CAP) {
+        c.sort_small(sk, sv, a.keys + g, HAS_V ? a.vals + g : nullptr, int(len), sk, sv);
+      } else {  // keys too clustered for the split: back into place, then through global memory
+        c.copy(a.keys + g, HAS_V ? a.vals + g : nullptr, sk, sv, len);
+        __syncthreads();
+        c.sort_large(a.keys + g, HAS_V ? a.vals + g : nullptr, sk, sv, len);
+      }
+      continue;
+    }
+    const int64_t s = a.order ? a.order[w - nbuck] : w;
     const int64_t lo = a.off ? clamp_off(a.off[s], a.n) : s * a.tile_len;
     const int64_t hi0 = a.off ? clamp_off(a.off[s + 1], a.n) : ((lo + a.tile_len) < a.n ? lo + a.tile_len : a.n);
     const int64_t hi = hi0 < lo ? lo : hi0;

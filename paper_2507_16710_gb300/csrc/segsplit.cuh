@@ -33,38 +33,10 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.h"
+#include "segsort.cuh"
 
 namespace ak {
-
-constexpr int SPLIT_BLOCK = 512;
-constexpr int SPLIT_TILE_BYTES = 32768;  // keys + values of one split tile
-
-// items per thread of a split tile (tile = SPLIT_BLOCK x items, about 32 KB)
-constexpr int split_items(int key_bytes, int val_bytes) {
-  return SPLIT_TILE_BYTES / (SPLIT_BLOCK * (key_bytes + val_bytes)) < 1   ? 1
-         : SPLIT_TILE_BYTES / (SPLIT_BLOCK * (key_bytes + val_bytes)) > 8 ? 8
-                                                                          : SPLIT_TILE_BYTES / (SPLIT_BLOCK * (key_bytes + val_bytes));
-}
-constexpr int split_tile(int key_bytes, int val_bytes) { return SPLIT_BLOCK * split_items(key_bytes, val_bytes); }
-
-struct SplitState {  // zeroed by the caller
-  uint32_t nbig;     // big segments
-  uint32_t nsmall;   // short segments in the work list
-  uint32_t nbuck;    // bucket work items
-  uint32_t ntiles;   // split tiles over all big segments
-  uint32_t pad[4];
-};
-
-struct BigSeg {
-  int64_t lo, len;              // key range [lo, lo + len)
-  unsigned long long vary;      // OR of (radix key ^ radix key of keys[lo])
-  uint32_t tile0;               // first split tile
-  uint32_t pad;
-};
-
-struct BucketItem {
-  int64_t lo, len;  // [lo, lo + len) in the workspace copy; sorted into the keys
-};
 
 // Bits of the split digit of a big segment and its shift.
 __device__ __forceinline__ void split_digit_of(const BigSeg &b, int64_t cap, int &shift, uint32_t &mask) {
@@ -232,7 +204,7 @@ struct SplitSmem {
 };
 
 template <typename U, typename V, bool HAS_V, int KIND, int ITEMS>
-__global__ void __launch_bounds__(SPLIT_BLOCK) split_scatter_kernel(const U *keys, const V *vals, U *alt_k, V *alt_v,
+__global__ void __launch_bounds__(SPLIT_BLOCK, 2) split_scatter_kernel(const U *keys, const V *vals, U *alt_k, V *alt_v,
                                                                     const BigSeg *big, const SplitState *st,
                                                                     const uint32_t *tcount, int64_t cap, U flip,
                                                                     const uint32_t *gate, uint32_t gate_want) {
