@@ -482,7 +482,7 @@ static ak_status run_radix(int op, const void *k_in, void *k_final, const void *
   c.n = n;
   c.kind = ki.kind;
   c.descending = order == AK_DESCENDING;
-  c.tile_config = (o.tile_config >= 1 && o.tile_config <= AK_TILE_CONFIGS) ? o.tile_config - 1 : 0;
+  c.tile_config = (o.tile_config >= 1 && o.tile_config <= AK_TILE_CONFIGS) ? o.tile_config - 1 : CFG_DEFAULT;
   c.hdr = reinterpret_cast<DevHeader *>(t + L.hdr);
   c.counts = reinterpret_cast<unsigned long long *>(t + L.counts);
   c.plan = reinterpret_cast<RadixPlan *>(t + L.plan);

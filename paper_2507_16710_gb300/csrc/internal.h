@@ -65,6 +65,8 @@ constexpr int CFG_BLOCK[4] = {512, 384, 512, 512};
 constexpr int CFG_BYTES[4] = {32768, 24576, 32768, 0};
 constexpr bool CFG_PERSIST[4] = {true, true, false, true};
 constexpr int CFG_WS = 3;
+// Configuration of tile_config 0 (the default) and of the learned path's passes.
+constexpr int CFG_DEFAULT = 0;
 
 constexpr int WS_BLOCK = 512;       // threads of the look-back-warp pass
 constexpr int WS_NCW = 15;          // its compute warps (the last warp looks back)
@@ -139,11 +141,15 @@ struct SegCall {
 // big segments hold more than the shared capacity each; every one of them
 // gets at most 4 len / CAP non-empty buckets (buckets average more than CAP / 4).
 constexpr int64_t split_big_cap(int64_t n, int key_bytes, int val_bytes) {
-  return n / (seg_cap(key_bytes, val_bytes) + 1) + 1;
+  return n / (int64_t(seg_cap(key_bytes, val_bytes)) + 1) + 1;
 }
 constexpr int64_t split_bucket_cap(int64_t n, int key_bytes, int val_bytes) {
   return 4 * (n / seg_cap(key_bytes, val_bytes)) + 256;
 }
+// Segments above SPLIT_MIN_CAPS times the shared capacity are split across all
+// CTAs before the per-CTA sort (segsplit.cuh); shorter ones above the capacity
+// are taken by one CTA through global memory, overlapped with other work.
+constexpr int SPLIT_MIN_CAPS = 8;
 // Split tiles: SPLIT_BLOCK threads x up to 8 keys, about 32 KB of keys and values.
 constexpr int SPLIT_BLOCK = 512;
 constexpr int SPLIT_TILE_BYTES = 32768;

@@ -92,15 +92,16 @@ template <> inline cudaError_t seg_launch_kind<uint64_t, KIND_FLOAT>(const SegCa
 // place of the model evaluation.
 template <typename U, typename V, bool HAS_V, int KIND, typename S, int DIGIT = DIGIT_LEARNED>
 cudaError_t lm_passes(const RadixCall &c, const LearnedCall &lc) {
-  constexpr int CFG = 0;
-  constexpr int BLOCK = CFG_BLOCK[CFG];
-  constexpr int ITEMS = tile_items(sizeof(U), HAS_V ? sizeof(V) : 0, CFG);
-  constexpr bool PERSIST = CFG_PERSIST[CFG];
-  using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
-  auto kern = onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, PERSIST, DIGIT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::BYTES));
+  constexpr int CFG = CFG_DEFAULT;
+  using P = PassKernel<U, V, HAS_V, KIND, S, CFG, DIGIT>;
+  constexpr int BLOCK = P::BLOCK;
+  constexpr bool PERSIST = P::PERSIST;
+  constexpr int TILE = P::TILE;
+  constexpr size_t BYTES = P::BYTES;
+  auto kern = P::kernel();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(BYTES));
   if (e != cudaSuccess) return e;
-  const int64_t tiles = (c.n + L::TILE - 1) / L::TILE;
+  const int64_t tiles = (c.n + TILE - 1) / TILE;
   PassArgs<U, V> a{};
   a.k_in = reinterpret_cast<const U *>(c.k_in);
   a.k_final = reinterpret_cast<U *>(c.k_final);
@@ -139,14 +140,14 @@ cudaError_t lm_passes(const RadixCall &c, const LearnedCall &lc) {
   }
   lm_plan_kernel<<<1, 1024, 0, c.stream>>>(lc.bucket_counts, c.n, lc.model, c.plan, c.hdr, lc.seg_off, lc.seg_capacity);
   const int passes = int((lc.bucket_bits + RADIX_BITS - 1) / RADIX_BITS);
-  const int64_t wave = int64_t(resident_ctas(kern, BLOCK, L::BYTES)) * device_sm_count();
+  const int64_t wave = int64_t(resident_ctas(kern, BLOCK, BYTES)) * device_sm_count();
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, PERSIST ? wave : tiles)));
   a.prefetch_ahead = PERSIST ? 0 : wave;
   for (int p = 0; p < passes; ++p) {
     a.pass = p;
     a.status_cur = c.status[p & 1];
     a.status_next = (p + 1 < passes) ? c.status[(p + 1) & 1] : nullptr;
-    kern<<<grid, BLOCK, L::BYTES, c.stream>>>(a);
+    kern<<<grid, BLOCK, BYTES, c.stream>>>(a);
   }
   {
     const int64_t want = (c.n + 1023) / 1024;

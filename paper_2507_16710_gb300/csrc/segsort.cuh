@@ -31,11 +31,12 @@ constexpr int SUB_BITS = 12;  // at most 2^SUB_BITS sub-ranges per segment
 constexpr int SUB_MAX = 48;   // largest sub-range the insertion sort takes
 
 struct SplitState {  // zeroed by the caller
-  uint32_t nbig;     // big segments
-  uint32_t nsmall;   // short segments in the work list
-  uint32_t nbuck;    // bucket work items
+  uint32_t nbig;     // big segments (split across CTAs)
+  uint32_t nlong;    // segments above the shared capacity, sorted by one CTA (front of the work list)
+  uint32_t nshort;   // segments within the shared capacity (back of the work list)
+  uint32_t nbuck;    // bucket work items of the big segments
   uint32_t ntiles;   // split tiles over all big segments
-  uint32_t pad[4];
+  uint32_t pad[3];
 };
 
 struct BigSeg {
@@ -513,10 +514,15 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
   c.init(smem, a.flip);
   uint32_t *s_work = c.s_misc;
   if (blockIdx.x == 0 && c.tid == 0 && a.path_tag) a.hdr->info.path = a.path_tag;
-  int64_t nbuck = 0, nwork = a.nseg;
+  // with the split, work items are: the long segments (one CTA each, through
+  // global memory), the buckets of the big ones, the short segments -- longest
+  // work first
+  int64_t nlong = 0, nbuck = 0, nshort = 0, nwork = a.nseg;
   if (a.split) {
+    nlong = a.split->nlong;
     nbuck = a.split->nbuck;
-    nwork = nbuck + a.split->nsmall;
+    nshort = a.split->nshort;
+    nwork = nlong + nbuck + nshort;
   }
   while (true) {
     if (c.tid == 0) s_work[0] = atomicAdd(&a.hdr->work_counter[0], 1u);
@@ -524,8 +530,8 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
     const int64_t w = s_work[0];
     __syncthreads();
     if (w >= nwork) break;
-    if (w < nbuck) {  // a bucket of a long segment: from the workspace copy into the keys
-      const BucketItem it = a.buckets[w];
+    if (w >= nlong && w < nlong + nbuck) {  // a bucket of a big segment: from the workspace copy into the keys
+      const BucketItem it = a.buckets[w - nlong];
       const int64_t g = a.seg_base + it.lo;
       const int64_t len = it.len;
       U *sk = a.alt_k + g;
@@ -539,7 +545,10 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
       }
       continue;
     }
-    const int64_t s = a.order ? a.order[w - nbuck] : w;
+    const int64_t s = !a.order ? w
+                      : !a.split  ? a.order[w]
+                      : w < nlong ? a.order[w]
+                                  : a.order[a.nseg - nshort + (w - nlong - nbuck)];
     const int64_t lo = a.off ? clamp_off(a.off[s], a.n) : s * a.tile_len;
     const int64_t hi0 = a.off ? clamp_off(a.off[s + 1], a.n) : ((lo + a.tile_len) < a.n ? lo + a.tile_len : a.n);
     const int64_t hi = hi0 < lo ? lo : hi0;

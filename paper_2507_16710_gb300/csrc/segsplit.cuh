@@ -1,13 +1,16 @@
 // segsplit.cuh -- device-wide split of the long segments of a segmented sort.
 //
 // A segment longer than the shared-memory capacity CAP cannot be sorted by one
-// CTA in shared memory, and one CTA working through it alone (a 567K-key
-// segment of a lognormal batch) would outlast the rest of the batch.  Before
-// the per-CTA sort runs, every such segment is cut into buckets by one stable
-// MSD pass that all CTAs share, tile by tile:
+// CTA in shared memory; one CTA takes it through global memory (an MSD pass,
+// then its buckets in shared memory), which for a segment many times CAP long
+// (a 567K-key segment of a lognormal batch) would outlast the rest of the
+// batch.  Before the per-CTA sort runs, every segment above SPLIT_MIN_CAPS x CAP
+// keys is cut into buckets by one stable MSD pass that all CTAs share, tile by
+// tile:
 //
-//   split_classify_kernel  segments up to CAP (and above one key) go to the
-//                          work list as they are; longer ones to the big list
+//   split_classify_kernel  segments above SPLIT_MIN_CAPS x CAP keys go to the
+//                          big list; the others (above one key) to the work
+//                          list as they are
 //   split_tiles_kernel     first tile of every big segment (exclusive scan of
 //                          ceil(len / T)), total tile count
 //   split_vary_kernel      per big segment, the OR of (radix key ^ radix key
@@ -59,9 +62,12 @@ __device__ __forceinline__ uint32_t split_find(const BigSeg *big, uint32_t nbig,
   return lo;
 }
 
+// Segments above `split_min` keys go to the big list; the others (above one
+// key) to the work list, those above `cap` (sorted by one CTA through global
+// memory, the longest work) from its front, the rest from its back.
 static __global__ void split_classify_kernel(const int64_t *off, int64_t nseg, int64_t n, int64_t cap,
-                                             uint32_t *order, BigSeg *big, SplitState *st, const uint32_t *gate,
-                                             uint32_t gate_want) {
+                                             int64_t split_min, uint32_t *order, BigSeg *big, SplitState *st,
+                                             const uint32_t *gate, uint32_t gate_want) {
   if (gate && *gate != gate_want) return;
   const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
@@ -69,13 +75,16 @@ static __global__ void split_classify_kernel(const int64_t *off, int64_t nseg, i
   lo = lo < 0 ? 0 : (lo > n ? n : lo);
   hi = hi < 0 ? 0 : (hi > n ? n : hi);
   const int64_t len = hi - lo;
-  if (len > cap) {
+  if (len > split_min) {
     const uint32_t b = atomicAdd(&st->nbig, 1u);
     big[b].lo = lo;
     big[b].len = len;
     big[b].vary = 0;
-  } else if (len > 1) {
+  } else if (len > cap) {
     order[atomicAdd(&st->nsmall, 1u)] = uint32_t(s);
+    atomicAdd(&st->nlong, 1u);
+  } else if (len > 1) {
+    order[nseg - 1 - atomicAdd(&st->nshort, 1u)] = uint32_t(s);
   }
 }
 

@@ -90,3 +90,27 @@ def test_first_adam_step_is_signed_lr():
     g = np.array([3.0, -2.0, 1e-3])
     p, _, _ = L.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
     assert np.allclose(p, [-0.01, 0.01, -0.01])
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    """With the same gradient every step, bias correction makes m-hat = g and
+    v-hat = g^2 at every step t, so each step moves -lr * sign(g): after 5
+    steps p = -5 lr sign(g).  A wrong power of beta in the correction of any
+    step after the first breaks this."""
+    g = np.array([3.0, -2.0, 1e-3, -7.5])
+    p, m1, m2 = np.zeros(4), np.zeros(4), np.zeros(4)
+    for step in range(1, 6):
+        p, m1, m2 = L.adam_step(p, g, m1, m2, step, lr=0.01, eps=0.0)
+        assert np.allclose(p, -0.01 * step * np.sign(g), rtol=0, atol=1e-15), step
+
+
+def test_adam_second_step_by_hand():
+    """g1 = 1 then g2 = -1 (scalar, lr = 0.01, eps = 0): after step 1, m1 = 0.1,
+    m2 = 0.001, p = -lr.  Step 2: m1 = 0.9 * 0.1 - 0.1 = -0.01, m-hat =
+    -0.01 / (1 - 0.81) = -1/19; m2 = 0.999 * 0.001 + 0.001 = 0.001999, v-hat =
+    0.001999 / (1 - 0.998001) = 1; p = -lr + lr / 19 = -lr * 18 / 19."""
+    p, m1, m2 = L.adam_step(np.zeros(1), np.array([1.0]), np.zeros(1), np.zeros(1), 1, lr=0.01, eps=0.0)
+    assert np.allclose(p, [-0.01]) and np.allclose(m1, [0.1]) and np.allclose(m2, [0.001])
+    p, m1, m2 = L.adam_step(p, np.array([-1.0]), m1, m2, 2, lr=0.01, eps=0.0)
+    assert np.allclose(m1, [-0.01]) and np.allclose(m2, [0.001999])
+    assert np.allclose(p, [-0.01 * 18.0 / 19.0], rtol=1e-12)
