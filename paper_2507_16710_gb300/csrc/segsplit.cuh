@@ -81,8 +81,7 @@ static __global__ void split_classify_kernel(const int64_t *off, int64_t nseg, i
     big[b].len = len;
     big[b].vary = 0;
   } else if (len > cap) {
-    order[atomicAdd(&st->nsmall, 1u)] = uint32_t(s);
-    atomicAdd(&st->nlong, 1u);
+    order[atomicAdd(&st->nlong, 1u)] = uint32_t(s);
   } else if (len > 1) {
     order[nseg - 1 - atomicAdd(&st->nshort, 1u)] = uint32_t(s);
   }
