@@ -521,6 +521,21 @@ def run_ours(args):
             r["learned_over_plain"] = round(r["learned_GBps"] / r["plain_GBps"], 3)
             lvp[name] = r
         extra["learned_vs_plain"] = lvp
+        # the MLP residual on a heavy-tailed distribution that the 64 knots underfit
+        # (Pareto, alpha 1.5): piecewise-linear CDF alone vs trained residual
+        par = (1.0 - synth.u01_f64(44, n)) ** (-1.0 / 1.5)
+        mlp = {}
+        for label, steps in (("pl_only", -1), ("mlp_16_steps", 0), ("mlp_64_steps", 64)):
+            gbs, ms, info, ok = time_sort(torch, ak, dev, stream, flush2, par, ak.AK_F64,
+                                          {"path": ak.AK_PATH_LEARNED, "train_steps": steps}, "sort",
+                                          warmup=args.warmup, steps=min(args.steps, 5))
+            if not ok:
+                raise RuntimeError(f"output check failed: pareto {label}")
+            mlp[label] = {"GBps": round(gbs, 2), "ms": round(ms, 3), "max_bucket": info["max_bucket"],
+                          "buckets": info["buckets"], "path": PATH_NAMES.get(info["path"]),
+                          "loss_before": info["loss_before"], "loss_after": info["loss_after"]}
+        extra["mlp_residual_pareto"] = mlp
+        del par
         temp = None
 
 

@@ -43,10 +43,14 @@ extern "C" {
 typedef struct CUstream_st *ak_stream_t; /* same handle as cudaStream_t */
 
 /* Key element types: the paper's FFI list (Sec. IV: int16, int32, int64,
- * float, double) with unsigned variants; __int128 is not supported. */
+ * float, double) with unsigned variants, and the 16-bit floats IEEE binary16
+ * (AK_F16) and bfloat16 (AK_BF16, the upper half of a binary32), ordered like
+ * the other floats (-0.0 before +0.0, every NaN after +Inf and tied); __int128
+ * is not supported.  ak_accumulate does not take the 16-bit floats. */
 typedef enum ak_dtype {
     AK_U16 = 0, AK_I16 = 1, AK_U32 = 2, AK_I32 = 3,
-    AK_U64 = 4, AK_I64 = 5, AK_F32 = 6, AK_F64 = 7
+    AK_U64 = 4, AK_I64 = 5, AK_F32 = 6, AK_F64 = 7,
+    AK_F16 = 8, AK_BF16 = 9
 } ak_dtype;
 
 typedef enum ak_order { AK_ASCENDING = 0, AK_DESCENDING = 1 } ak_order;

@@ -6,7 +6,7 @@ Julia isless order.  Python here only marshals arguments: the compiled library
 ``lib/libak_sort.so`` (built by ``_build.build()``) does all the work.
 """
 from ._lib import (  # noqa: F401
-    AK_ASCENDING, AK_DESCENDING, AK_F32, AK_F64, AK_I16, AK_I32, AK_I64, AK_OP_SORT,
+    AK_ASCENDING, AK_BF16, AK_DESCENDING, AK_F16, AK_F32, AK_F64, AK_I16, AK_I32, AK_I64, AK_OP_SORT,
     AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED, AK_OP_SORTPERM, AK_PATH_AUTO, AK_PATH_BLOCK,
     AK_PATH_LEARNED, AK_PATH_MERGE, AK_PATH_RADIX, AK_TILE_CONFIGS, AK_U16, AK_U32, AK_U64, EXPORTED, LIB_PATH,
     AK_DEBUG_SKIP_FIRST_TILE, AK_MAX_PASSES,

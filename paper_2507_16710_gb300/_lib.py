@@ -17,7 +17,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("AK_SORT_LIB") or os.path.join(_HERE, "lib", "libak_sort.so")
 
-AK_U16, AK_I16, AK_U32, AK_I32, AK_U64, AK_I64, AK_F32, AK_F64 = range(8)
+AK_U16, AK_I16, AK_U32, AK_I32, AK_U64, AK_I64, AK_F32, AK_F64, AK_F16, AK_BF16 = range(10)
 AK_ASCENDING, AK_DESCENDING = 0, 1
 AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED = range(4)
 AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK, AK_PATH_MERGE = range(5)
@@ -114,7 +114,7 @@ def load() -> ctypes.CDLL:
 
 _TORCH_DTYPE = {
     torch.int16: AK_I16, torch.int32: AK_I32, torch.int64: AK_I64,
-    torch.float32: AK_F32, torch.float64: AK_F64,
+    torch.float32: AK_F32, torch.float64: AK_F64, torch.float16: AK_F16, torch.bfloat16: AK_BF16,
 }
 for _name, _code in (("uint16", AK_U16), ("uint32", AK_U32), ("uint64", AK_U64)):
     if hasattr(torch, _name):

@@ -51,6 +51,8 @@ static bool key_info(int kd, KeyInfo *ki) {
     case AK_I64: *ki = {8, KIND_SINT}; return true;
     case AK_F32: *ki = {4, KIND_FLOAT}; return true;
     case AK_F64: *ki = {8, KIND_FLOAT}; return true;
+    case AK_F16: *ki = {2, KIND_FLOAT}; return true;
+    case AK_BF16: *ki = {2, KIND_BF16}; return true;
   }
   return false;
 }
@@ -123,7 +125,11 @@ static void apply_tuning(int op, int kd, int64_t n, int val_bytes, ak_options &o
 
 static cudaError_t radix_dispatch(int key_bytes, const RadixCall &c) {
   switch (key_bytes) {
-    case 2: return c.kind == KIND_SINT ? radix_launch_u16_sint(c) : radix_launch_u16_uint(c);
+    case 2:
+      return c.kind == KIND_BF16    ? radix_launch_u16_bf16(c)
+             : c.kind == KIND_FLOAT ? radix_launch_u16_float(c)
+             : c.kind == KIND_SINT  ? radix_launch_u16_sint(c)
+                                    : radix_launch_u16_uint(c);
     case 4:
       return c.kind == KIND_FLOAT  ? radix_launch_u32_float(c)
              : c.kind == KIND_SINT ? radix_launch_u32_sint(c)
@@ -137,7 +143,11 @@ static cudaError_t radix_dispatch(int key_bytes, const RadixCall &c) {
 
 static cudaError_t seg_dispatch(int key_bytes, const SegCall &c) {
   switch (key_bytes) {
-    case 2: return c.kind == KIND_SINT ? seg_launch_u16_sint(c) : seg_launch_u16_uint(c);
+    case 2:
+      return c.kind == KIND_BF16    ? seg_launch_u16_bf16(c)
+             : c.kind == KIND_FLOAT ? seg_launch_u16_float(c)
+             : c.kind == KIND_SINT  ? seg_launch_u16_sint(c)
+                                    : seg_launch_u16_uint(c);
     case 4:
       return c.kind == KIND_FLOAT  ? seg_launch_u32_float(c)
              : c.kind == KIND_SINT ? seg_launch_u32_sint(c)
@@ -344,7 +354,11 @@ int learned_auto_bucket_bits(int op, int64_t n, int key_bytes, int val_bytes) {
 
 static cudaError_t learned_dispatch(int key_bytes, int kind, const RadixCall &c, const LearnedCall &lc) {
   switch (key_bytes) {
-    case 2: return kind == KIND_SINT ? learned_launch_u16_sint(c, lc) : learned_launch_u16_uint(c, lc);
+    case 2:
+      return kind == KIND_BF16    ? learned_launch_u16_bf16(c, lc)
+             : kind == KIND_FLOAT ? learned_launch_u16_float(c, lc)
+             : kind == KIND_SINT  ? learned_launch_u16_sint(c, lc)
+                                  : learned_launch_u16_uint(c, lc);
     case 4:
       return kind == KIND_FLOAT  ? learned_launch_u32_float(c, lc)
              : kind == KIND_SINT ? learned_launch_u32_sint(c, lc)

@@ -19,7 +19,9 @@ constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAX_PASSES = 8;
 
-enum KeyKind : int { KIND_UINT = 0, KIND_SINT = 1, KIND_FLOAT = 2 };
+// KIND_FLOAT: IEEE binary16/32/64 by the key width; KIND_BF16: bfloat16 (the
+// upper half of a binary32: 8 exponent bits), 16-bit keys only.
+enum KeyKind : int { KIND_UINT = 0, KIND_SINT = 1, KIND_FLOAT = 2, KIND_BF16 = 3 };
 
 // ----------------------------------------------------------------- key transform
 // Julia isless on the raw bits of a key, as an unsigned integer order:
@@ -35,14 +37,21 @@ template <> struct FloatBits<uint16_t> { static constexpr uint16_t EXP = 0x7C00u
 template <> struct FloatBits<uint32_t> { static constexpr uint32_t EXP = 0x7F800000u; };
 template <> struct FloatBits<uint64_t> { static constexpr uint64_t EXP = 0x7FF0000000000000ull; };
 
+// Exponent field of a float kind (all ones: infinity, above it: NaN).
+template <int KIND, typename U>
+__host__ __device__ constexpr U float_exp() {
+  return KIND == KIND_BF16 ? U(0x7F80u) : FloatBits<U>::EXP;
+}
+constexpr bool is_float_kind(int kind) { return kind == KIND_FLOAT || kind == KIND_BF16; }
+
 template <typename U>
 __device__ __forceinline__ U radix_key(U u, int kind, U flip) {
   constexpr U SIGN = U(U(1) << (8 * sizeof(U) - 1));
   U r;
-  if (kind == KIND_FLOAT) {
+  if (is_float_kind(kind)) {
     const U mag = U(u & U(~SIGN));
     r = (u & SIGN) ? U(~u) : U(u ^ SIGN);
-    if (mag > FloatBits<U>::EXP) r = U(~U(0));
+    if (mag > (kind == KIND_BF16 ? float_exp<KIND_BF16, U>() : FloatBits<U>::EXP)) r = U(~U(0));
   } else if (kind == KIND_SINT) {
     r = U(u ^ SIGN);
   } else {
@@ -55,12 +64,12 @@ __device__ __forceinline__ U radix_key(U u, int kind, U flip) {
 template <int KIND, typename U>
 __device__ __forceinline__ U radix_key_t(U u, U flip) {
   constexpr U SIGN = U(U(1) << (8 * sizeof(U) - 1));
-  if constexpr (KIND == KIND_FLOAT) {
+  if constexpr (KIND == KIND_FLOAT || KIND == KIND_BF16) {
     // negative -> ~u, non-negative -> u ^ SIGN: xor with (arithmetic sign mask | SIGN)
     using S = typename std::make_signed<U>::type;
     const U neg = U(S(u) >> (8 * sizeof(U) - 1));
     U r = U(u ^ (neg | SIGN));
-    r = (U(u & U(~SIGN)) > FloatBits<U>::EXP) ? U(~U(0)) : r;
+    r = (U(u & U(~SIGN)) > float_exp<KIND, U>()) ? U(~U(0)) : r;
     return U(r ^ flip);
   } else if constexpr (KIND == KIND_SINT) {
     return U(u ^ SIGN ^ flip);
@@ -168,6 +177,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     if ((++spins & 15u) == 0 && globaltimer_ns() - t0 > timeout_ns) return false;
   }
   return true;
+}
+
+// Named barriers: a subset of the CTA's warps synchronises (bar.sync) or only
+// signals its arrival (bar.arrive); `nthreads` counts every participant.
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(uint32_t id, uint32_t nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // ------------------------------------------------------------------ warp utils

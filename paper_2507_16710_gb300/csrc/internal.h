@@ -46,6 +46,8 @@ struct RadixCall {
 // One entry point per key word width and key kind (unsigned/signed/float).
 cudaError_t radix_launch_u16_uint(const RadixCall &c);
 cudaError_t radix_launch_u16_sint(const RadixCall &c);
+cudaError_t radix_launch_u16_float(const RadixCall &c);
+cudaError_t radix_launch_u16_bf16(const RadixCall &c);
 cudaError_t radix_launch_u32_uint(const RadixCall &c);
 cudaError_t radix_launch_u32_sint(const RadixCall &c);
 cudaError_t radix_launch_u32_float(const RadixCall &c);
@@ -182,6 +184,8 @@ struct LearnedCall {
 };
 cudaError_t learned_launch_u16_uint(const RadixCall &c, const LearnedCall &lc);
 cudaError_t learned_launch_u16_sint(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u16_float(const RadixCall &c, const LearnedCall &lc);
+cudaError_t learned_launch_u16_bf16(const RadixCall &c, const LearnedCall &lc);
 cudaError_t learned_launch_u32_uint(const RadixCall &c, const LearnedCall &lc);
 cudaError_t learned_launch_u32_sint(const RadixCall &c, const LearnedCall &lc);
 cudaError_t learned_launch_u32_float(const RadixCall &c, const LearnedCall &lc);
@@ -192,6 +196,8 @@ size_t learned_model_bytes();
 size_t learned_partials_bytes();
 cudaError_t seg_launch_u16_uint(const SegCall &c);
 cudaError_t seg_launch_u16_sint(const SegCall &c);
+cudaError_t seg_launch_u16_float(const SegCall &c);
+cudaError_t seg_launch_u16_bf16(const SegCall &c);
 cudaError_t seg_launch_u32_uint(const SegCall &c);
 cudaError_t seg_launch_u32_sint(const SegCall &c);
 cudaError_t seg_launch_u32_float(const SegCall &c);

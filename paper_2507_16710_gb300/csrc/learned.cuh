@@ -228,9 +228,9 @@ __global__ void lm_sample_kernel(const U *keys, int64_t n, U flip, uint32_t m, u
     const U r = radix_key_t<KIND>(k, flip);
     sample_r[j] = (unsigned long long)r;
     bool nonfinite = false;  // NaN and infinities stay out of the range (x-hat clamps them)
-    if (KIND == KIND_FLOAT) {
+    if (KIND == KIND_FLOAT || KIND == KIND_BF16) {
       constexpr U SIGN = U(U(1) << (8 * sizeof(U) - 1));
-      nonfinite = U(k & U(~SIGN)) >= FloatBits<U>::EXP;
+      nonfinite = U(k & U(~SIGN)) >= float_exp<KIND, U>();
     }
     if (!nonfinite) {
       lo_n = max(lo_n, ~(unsigned long long)r);

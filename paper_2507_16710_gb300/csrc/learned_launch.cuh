@@ -67,6 +67,8 @@ template <typename U, int KIND>
 cudaError_t radix_launch_kind(const RadixCall &c);
 template <> inline cudaError_t radix_launch_kind<uint16_t, KIND_UINT>(const RadixCall &c) { return radix_launch_u16_uint(c); }
 template <> inline cudaError_t radix_launch_kind<uint16_t, KIND_SINT>(const RadixCall &c) { return radix_launch_u16_sint(c); }
+template <> inline cudaError_t radix_launch_kind<uint16_t, KIND_FLOAT>(const RadixCall &c) { return radix_launch_u16_float(c); }
+template <> inline cudaError_t radix_launch_kind<uint16_t, KIND_BF16>(const RadixCall &c) { return radix_launch_u16_bf16(c); }
 template <> inline cudaError_t radix_launch_kind<uint32_t, KIND_UINT>(const RadixCall &c) { return radix_launch_u32_uint(c); }
 template <> inline cudaError_t radix_launch_kind<uint32_t, KIND_SINT>(const RadixCall &c) { return radix_launch_u32_sint(c); }
 template <> inline cudaError_t radix_launch_kind<uint32_t, KIND_FLOAT>(const RadixCall &c) { return radix_launch_u32_float(c); }
@@ -78,6 +80,8 @@ template <typename U, int KIND>
 cudaError_t seg_launch_kind(const SegCall &c);
 template <> inline cudaError_t seg_launch_kind<uint16_t, KIND_UINT>(const SegCall &c) { return seg_launch_u16_uint(c); }
 template <> inline cudaError_t seg_launch_kind<uint16_t, KIND_SINT>(const SegCall &c) { return seg_launch_u16_sint(c); }
+template <> inline cudaError_t seg_launch_kind<uint16_t, KIND_FLOAT>(const SegCall &c) { return seg_launch_u16_float(c); }
+template <> inline cudaError_t seg_launch_kind<uint16_t, KIND_BF16>(const SegCall &c) { return seg_launch_u16_bf16(c); }
 template <> inline cudaError_t seg_launch_kind<uint32_t, KIND_UINT>(const SegCall &c) { return seg_launch_u32_uint(c); }
 template <> inline cudaError_t seg_launch_kind<uint32_t, KIND_SINT>(const SegCall &c) { return seg_launch_u32_sint(c); }
 template <> inline cudaError_t seg_launch_kind<uint32_t, KIND_FLOAT>(const SegCall &c) { return seg_launch_u32_float(c); }

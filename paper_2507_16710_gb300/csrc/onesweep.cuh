@@ -202,7 +202,9 @@ struct PassSmem {
   static constexpr size_t OFF_BAR = (OFF_SCR + (RADIX / 32) * 4 + 15) / 16 * 16;               // u64
   static constexpr size_t OFF_TILE = OFF_BAR + 8;                                            // i64: next tile
   static constexpr size_t OFF_FLAG = OFF_TILE + 8;                                           // u32
-  static constexpr size_t OFF_DIG = (OFF_FLAG + 4 + 15) / 16 * 16;  // u8[TILE]: digit of each output slot
+  static constexpr size_t OFF_LBC = (OFF_FLAG + 4 + 15) / 16 * 16;  // u32[RADIX]: tile digit counts (look-back)
+  static constexpr size_t OFF_LBS = OFF_LBC + RADIX * 4;             // u32[RADIX]: tile digit starts
+  static constexpr size_t OFF_DIG = OFF_LBS + RADIX * 4;  // u8[TILE]: digit of each output slot
   static constexpr size_t BYTES = OFF_DIG + size_t(TILE);
   static_assert(TILE < 65536, "warp bases are u16");
   static_assert(NW % 2 == 0, "two 16-bit counters per word");
@@ -214,6 +216,9 @@ struct PassSmem {
 #define AK_LOOKBACK_WINDOW 8
 #endif
 constexpr int LOOKBACK_WINDOW = AK_LOOKBACK_WINDOW;  // predecessor words probed per round trip
+#ifndef AK_LB_UPPER
+#define AK_LB_UPPER 1
+#endif
 
 // One digit pass.  Tile ids come from an atomic counter, so every predecessor
 // of a tile is held by a CTA that already runs (forward progress of the
@@ -260,6 +265,10 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   long long *s_next = reinterpret_cast<long long *>(smem + L::OFF_TILE);
   uint32_t *s_flag = reinterpret_cast<uint32_t *>(smem + L::OFF_FLAG);
   uint8_t *s_dig = smem + L::OFF_DIG;
+  uint32_t *s_lbc = reinterpret_cast<uint32_t *>(smem + L::OFF_LBC);
+  uint32_t *s_lbs = reinterpret_cast<uint32_t *>(smem + L::OFF_LBS);
+  // 512-thread CTAs: the upper 256 threads do the look-back while the lower 256 scatter
+  constexpr bool UPPER_LB = AK_LB_UPPER && BLOCK == 2 * RADIX;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (a.gate && *a.gate != a.gate_want) return;
 
@@ -408,6 +417,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           my_cnt += (w & 0xFFFFu) + (w >> 16);
         }
         st_relaxed(&st[tile * RADIX + tid], (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt));
+        if (UPPER_LB) s_lbc[tid] = my_cnt;
         inc = warp_inclusive_scan(my_cnt);
         if (lane == 31) s_scr[warp] = inc;
       }
@@ -431,24 +441,27 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           run = hi + (w >> 16);
           hrow[v] = (lo & 0xFFFFu) | (hi << 16);
         }
+        if (UPPER_LB) s_lbs[tid] = start;
       }
-      __syncthreads();  // B: warp bases ready
 
-      // ---- scatter into the output buffer in digit order
+      // ---- scatter into the output buffer in digit order (this thread's items)
+      auto scatter = [&]() {
 #pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t d = dr[i] & 511u;
-        if (FULL || d < RADIX) {
-          const int idx = wbase + i * 32 + lane;
-          const uint32_t pos = uint32_t(whist[d * H2 + warp]) + (dr[i] >> 9);
-          ok[pos] = sk[idx];
-          if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
-          s_dig[pos] = uint8_t(d);
+        for (int i = 0; i < ITEMS; ++i) {
+          const uint32_t d = dr[i] & 511u;
+          if (FULL || d < RADIX) {
+            const int idx = wbase + i * 32 + lane;
+            const uint32_t pos = uint32_t(whist[d * H2 + warp]) + (dr[i] >> 9);
+            ok[pos] = sk[idx];
+            if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
+            s_dig[pos] = uint8_t(d);
+          }
         }
-      }
-
-      // ---- decoupled look-back over a window of predecessors per probe
-      if (tid < RADIX) {
+      };
+      // ---- decoupled look-back of digit d (count cnt) over a window of
+      // predecessors per probe; publishes the inclusive count, returns the
+      // exclusive prefix
+      auto lookback = [&](int d, uint32_t cnt) -> unsigned long long {
         unsigned long long excl = 0;
         if (tile > 0) {
           int64_t j = tile - 1;
@@ -457,7 +470,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           for (;;) {
             S lb[LOOKBACK_WINDOW];  // lb[k]: status word of predecessor j - k
 #pragma unroll
-            for (int k = 0; k < LOOKBACK_WINDOW; ++k) lb[k] = (j - k >= 0) ? ld_relaxed(&st[(j - k) * RADIX + tid]) : S(0);
+            for (int k = 0; k < LOOKBACK_WINDOW; ++k) lb[k] = (j - k >= 0) ? ld_relaxed(&st[(j - k) * RADIX + d]) : S(0);
             int used = 0;
             bool done = false, stop = false;
 #pragma unroll
@@ -488,9 +501,33 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
               }
             }
           }
-          st_relaxed(&st[tile * RADIX + tid], (S(FLAG_INC) << StatusWord<S>::SHIFT) | S(excl + my_cnt));
+          st_relaxed(&st[tile * RADIX + d], (S(FLAG_INC) << StatusWord<S>::SHIFT) | S(excl + cnt));
         }
-        s_delta[tid] = Delta((long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start);
+        return excl;
+      };
+
+      if constexpr (UPPER_LB) {
+        // the upper half looks back (one digit per thread) while the lower
+        // half scatters its items; then the upper half scatters its own
+        if (tid < RADIX) {
+          __threadfence_block();   // warp bases and digit starts ready for the upper half
+          named_arrive(2, BLOCK);
+          named_sync(1, RADIX);    // ... and for the rest of the lower half
+          scatter();
+        } else {
+          const int d = tid - RADIX;
+          const unsigned long long excl = lookback(d, s_lbc[d]);
+          named_sync(2, BLOCK);
+          s_delta[d] = Delta((long long)(a.plan->bin_off[a.pass][d] + excl) - (long long)s_lbs[d]);
+          scatter();
+        }
+      } else {
+        __syncthreads();  // B: warp bases ready
+        scatter();
+        if (tid < RADIX) {
+          const unsigned long long excl = lookback(tid, my_cnt);
+          s_delta[tid] = Delta((long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start);
+        }
       }
       if (PERSIST && tid == CLAIMER) {
         *s_next = (long long)next_tile;

@@ -74,10 +74,6 @@ struct WsSmem {
                 "shared-memory arrays aligned to their element size (bulk copies: 16 bytes)");
 };
 
-__device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }

@@ -129,13 +129,15 @@ ak_status ss_dispatch(const void *v, int64_t n, const void *x, int64_t m, int kd
     case AK_U64: return ss_launch<uint64_t, KIND_UINT, LAST>(v, n, x, m, desc, out, st);
     case AK_I64: return ss_launch<uint64_t, KIND_SINT, LAST>(v, n, x, m, desc, out, st);
     case AK_F64: return ss_launch<uint64_t, KIND_FLOAT, LAST>(v, n, x, m, desc, out, st);
+    case AK_F16: return ss_launch<uint16_t, KIND_FLOAT, LAST>(v, n, x, m, desc, out, st);
+    case AK_BF16: return ss_launch<uint16_t, KIND_BF16, LAST>(v, n, x, m, desc, out, st);
   }
   return AK_ERR_INVALID_ARG;
 }
 
 int ss_key_bytes(int kd) {
   switch (kd) {
-    case AK_U16: case AK_I16: return 2;
+    case AK_U16: case AK_I16: case AK_F16: case AK_BF16: return 2;
     case AK_U32: case AK_I32: case AK_F32: return 4;
     case AK_U64: case AK_I64: case AK_F64: return 8;
   }

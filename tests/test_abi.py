@@ -133,7 +133,7 @@ def test_searchsorted_host_checks(lib):
         assert f(None, 0, None, 0, ak.AK_F64, 0, None, None) == 0
         assert f(v, -1, x, 5, ak.AK_F64, 0, out, None) == 1            # negative n
         assert f(v, 10, x, -5, ak.AK_F64, 0, out, None) == 1           # negative m
-        assert f(v, 10, x, 5, 8, 0, out, None) == 1                    # bad dtype
+        assert f(v, 10, x, 5, 10, 0, out, None) == 1                   # bad dtype
         assert f(v, 10, x, 5, ak.AK_F64, 2, out, None) == 1            # bad order
         assert f(v, 10, None, 5, ak.AK_F64, 0, out, None) == 1         # NULL queries
         assert f(v, 10, x, 5, ak.AK_F64, 0, None, None) == 1           # NULL output
@@ -151,12 +151,15 @@ def test_accumulate_host_checks(lib):
     tiles = (1 << 20) // 8192  # 32 KB tiles of float32
     assert out.value >= tiles * (4 + 8 + 8) and out.value % 256 == 0
     assert lib.ak_accumulate_temp_bytes(-1, ak.AK_F32, ctypes.byref(out)) == 1
-    assert lib.ak_accumulate_temp_bytes(10, 8, ctypes.byref(out)) == 1
+    assert lib.ak_accumulate_temp_bytes(10, 10, ctypes.byref(out)) == 1
+    for kd in (ak.AK_F16, ak.AK_BF16):  # valid key types the scan does not take
+        assert lib.ak_accumulate_temp_bytes(10, kd, ctypes.byref(out)) == 2
     x, y, t = ctypes.c_void_p(1 << 16), ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 24)
     f = lib.ak_accumulate
     assert f(None, None, 0, ak.AK_I32, 0, 1, None, None, 0, None, None) == 0        # n = 0: nothing to do
     assert f(x, y, -1, ak.AK_I32, 0, 1, None, t, 1 << 20, None, None) == 1          # negative n
-    assert f(x, y, 10, 8, 0, 1, None, t, 1 << 20, None, None) == 1                  # bad dtype
+    assert f(x, y, 10, 10, 0, 1, None, t, 1 << 20, None, None) == 1                 # bad dtype
+    assert f(x, y, 10, ak.AK_F16, 0, 1, None, t, 1 << 20, None, None) == 2          # unsupported
     assert f(x, y, 10, ak.AK_I32, 3, 1, None, t, 1 << 20, None, None) == 1          # bad operator
     assert f(x, y, 10, ak.AK_I32, 0, 2, None, t, 1 << 20, None, None) == 1          # bad inclusive flag
     assert f(None, y, 10, ak.AK_I32, 0, 1, None, t, 1 << 20, None, None) == 1       # NULL input

@@ -125,22 +125,26 @@ def test_nan_and_signed_zero_with_learned_buckets(ak):
 
 
 def test_mlp_residual_gain_over_piecewise_linear(ak):
-    """What the trained network adds: on the same sample, the training loss of
-    PL + MLP is below that of the piecewise-linear CDF alone (the model at step
-    0), and the bucket occupancy is no worse."""
-    n = 1 << 22
-    keys = synth.dist_f64(n, "lognormal", seed=12)
+    """What the trained network adds: on a heavy-tailed distribution (Pareto,
+    alpha = 1.5, whose density the 64 piecewise-linear knots underfit), the
+    learned path with the MLP residual trained for 64 steps puts strictly fewer
+    keys in its largest bucket than the piecewise-linear CDF alone, with a
+    lower training loss; both sorts stay exact."""
+    n = 1 << 24
+    keys = (1.0 - synth.u01_f64(44, n)) ** (-1.0 / 1.5)
     res = {}
-    for steps in (-1, 0):
+    for steps in (-1, 64):
         opts = _learned(ak, train_steps=steps)
         t, _ = to_dev(keys)
         temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64, options=opts), t.device)
         ak.ak_sort(t, temp=temp, options=opts)
         res[steps] = ak.ak_last_info(temp)
-        assert_bits_equal(to_host(t, np.float64), np.sort(keys), "lognormal sort")
-    trained = res[0]
-    assert trained["loss_after"] < trained["loss_before"], trained
-    assert trained["max_bucket"] <= 2 * res[-1]["max_bucket"], (trained, res[-1])
+        assert res[steps]["path"] == ak.AK_PATH_LEARNED, res[steps]
+        assert_bits_equal(to_host(t, np.float64), np.sort(keys), "pareto sort")
+    pl, mlp = res[-1], res[64]
+    assert mlp["loss_after"] < mlp["loss_before"], mlp
+    assert mlp["max_bucket"] < pl["max_bucket"], (mlp, pl)
+    assert mlp["max_bucket"] < 0.75 * pl["max_bucket"], (mlp["max_bucket"], pl["max_bucket"])
 
 
 def test_auto_takes_learned_for_large_64bit_keys(ak):
