@@ -202,9 +202,7 @@ struct PassSmem {
   static constexpr size_t OFF_BAR = (OFF_SCR + (RADIX / 32) * 4 + 15) / 16 * 16;               // u64
   static constexpr size_t OFF_TILE = OFF_BAR + 8;                                            // i64: next tile
   static constexpr size_t OFF_FLAG = OFF_TILE + 8;                                           // u32
-  static constexpr size_t OFF_LBC = (OFF_FLAG + 4 + 15) / 16 * 16;  // u32[RADIX]: tile digit counts (look-back)
-  static constexpr size_t OFF_LBS = OFF_LBC + RADIX * 4;             // u32[RADIX]: tile digit starts
-  static constexpr size_t OFF_DIG = OFF_LBS + RADIX * 4;  // u8[TILE]: digit of each output slot
+  static constexpr size_t OFF_DIG = (OFF_FLAG + 4 + 15) / 16 * 16;  // u8[TILE]: digit of each output slot
   static constexpr size_t BYTES = OFF_DIG + size_t(TILE);
   static_assert(TILE < 65536, "warp bases are u16");
   static_assert(NW % 2 == 0, "two 16-bit counters per word");
@@ -216,9 +214,7 @@ struct PassSmem {
 #define AK_LOOKBACK_WINDOW 8
 #endif
 constexpr int LOOKBACK_WINDOW = AK_LOOKBACK_WINDOW;  // predecessor words probed per round trip
-#ifndef AK_LB_UPPER
-#define AK_LB_UPPER 1
-#endif
+
 
 // One digit pass.  Tile ids come from an atomic counter, so every predecessor
 // of a tile is held by a CTA that already runs (forward progress of the
@@ -265,10 +261,6 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   long long *s_next = reinterpret_cast<long long *>(smem + L::OFF_TILE);
   uint32_t *s_flag = reinterpret_cast<uint32_t *>(smem + L::OFF_FLAG);
   uint8_t *s_dig = smem + L::OFF_DIG;
-  uint32_t *s_lbc = reinterpret_cast<uint32_t *>(smem + L::OFF_LBC);
-  uint32_t *s_lbs = reinterpret_cast<uint32_t *>(smem + L::OFF_LBS);
-  // 512-thread CTAs: the upper 256 threads do the look-back while the lower 256 scatter
-  constexpr bool UPPER_LB = AK_LB_UPPER && BLOCK == 2 * RADIX;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (a.gate && *a.gate != a.gate_want) return;
 
@@ -417,7 +409,6 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           my_cnt += (w & 0xFFFFu) + (w >> 16);
         }
         st_relaxed(&st[tile * RADIX + tid], (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt));
-        if (UPPER_LB) s_lbc[tid] = my_cnt;
         inc = warp_inclusive_scan(my_cnt);
         if (lane == 31) s_scr[warp] = inc;
       }
@@ -441,7 +432,6 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           run = hi + (w >> 16);
           hrow[v] = (lo & 0xFFFFu) | (hi << 16);
         }
-        if (UPPER_LB) s_lbs[tid] = start;
       }
 
       // ---- scatter into the output buffer in digit order (this thread's items)
@@ -506,28 +496,11 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
         return excl;
       };
 
-      if constexpr (UPPER_LB) {
-        // the upper half looks back (one digit per thread) while the lower
-        // half scatters its items; then the upper half scatters its own
-        if (tid < RADIX) {
-          __threadfence_block();   // warp bases and digit starts ready for the upper half
-          named_arrive(2, BLOCK);
-          named_sync(1, RADIX);    // ... and for the rest of the lower half
-          scatter();
-        } else {
-          const int d = tid - RADIX;
-          const unsigned long long excl = lookback(d, s_lbc[d]);
-          named_sync(2, BLOCK);
-          s_delta[d] = Delta((long long)(a.plan->bin_off[a.pass][d] + excl) - (long long)s_lbs[d]);
-          scatter();
-        }
-      } else {
-        __syncthreads();  // B: warp bases ready
-        scatter();
-        if (tid < RADIX) {
-          const unsigned long long excl = lookback(tid, my_cnt);
-          s_delta[tid] = Delta((long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start);
-        }
+      __syncthreads();  // B: warp bases ready
+      scatter();
+      if (tid < RADIX) {
+        const unsigned long long excl = lookback(tid, my_cnt);
+        s_delta[tid] = Delta((long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start);
       }
       if (PERSIST && tid == CLAIMER) {
         *s_next = (long long)next_tile;

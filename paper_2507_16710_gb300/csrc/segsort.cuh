@@ -375,50 +375,121 @@ struct SegCta {
 
   // Sort gk/gv[0, len) (global) into dk/dv (global, may alias gk/gv), len <= CAP;
   // tk/tv: len elements of global scratch other than dk/dv (may alias gk/gv).
+  // Six CTA barriers; the caller separates consecutive calls by a barrier.
   __device__ void sort_small(const U *gk, const V *gv, U *dk, V *dv, int len, U *tk, V *tv) {
+    // radix-key arithmetic in 32 bits for keys of 32 bits or less
+    using R = typename std::conditional<(sizeof(U) <= 4), uint32_t, unsigned long long>::type;
     U *ak = buf_k(0);
     V *av = buf_v(0);
-    copy(ak, av, gk, gv, len);
-    __syncthreads();
-    U mn, mx;
-    unsigned long long vary;
-    key_range(ak, len, mn, mx, vary);
+    // 1. load into shared memory with the range of the radix keys: min, max and
+    //    OR of (r ^ r of the first key), reduced per warp, then by every warp
+    //    over the warp partials
+    R *scr = reinterpret_cast<R *>(s_cnt);  // 3 x NW partials
+    const R r0 = R(rk(gk[0]));
+    R lo = R(~R(0)), hi = 0, vary = 0;
+    for (int i = tid; i < len; i += BLOCK) {
+      const U k = gk[i];
+      ak[i] = k;
+      if (HAS_V) av[i] = gv[i];
+      const R r = R(rk(k));
+      lo = r < lo ? r : lo;
+      hi = r > hi ? r : hi;
+      vary |= r ^ r0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      vary |= __shfl_xor_sync(0xffffffffu, vary, o);
+      lo = l2 < lo ? l2 : lo;
+      hi = h2 > hi ? h2 : hi;
+    }
+    if (lane == 0) {
+      scr[warp] = lo;
+      scr[NW + warp] = hi;
+      scr[2 * NW + warp] = vary;
+    }
+    __syncthreads();  // [1] keys staged, warp partials written
+    lo = lane < NW ? scr[lane] : R(~R(0));
+    hi = lane < NW ? scr[NW + lane] : R(0);
+    vary = lane < NW ? scr[2 * NW + lane] : R(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      vary |= __shfl_xor_sync(0xffffffffu, vary, o);
+      lo = l2 < lo ? l2 : lo;
+      hi = h2 > hi ? h2 : hi;
+    }
     if (vary == 0) {  // every key equivalent: stable order is the input order
-      if (dk != gk) {
-        copy(dk, dv, ak, av, len);
-        __syncthreads();
-      }
+      if (dk != gk) copy(dk, dv, ak, av, len);
       return;
     }
-    // sub-ranges of width 2^sh over [mn, mx]: about two keys each when spread evenly
-    const unsigned long long span = (unsigned long long)(U(mx - mn));
-    const int span_bits = 64 - __clzll((long long)span);
+    // 2. sub-ranges of width 2^sh over [lo, hi]: about two keys each when the
+    //    keys are spread evenly; counts in the (zero) mask words
+    const R span = R(hi - lo);
+    const int span_bits = sizeof(R) == 4 ? 32 - __clz(uint32_t(span)) : 64 - __clzll((long long)span);
     int want = (32 - __clz(uint32_t(len - 1))) - 1;
     want = want < 1 ? 1 : (want > SUB_BITS ? SUB_BITS : want);
     const int sh = span_bits > want ? span_bits - want : 0;
     const int nsub = int(span >> sh) + 1;
-    uint32_t *sub = wmask;  // mask words are zero outside a ranking step
-    for (int i = tid; i < len; i += BLOCK) atomicAdd(&sub[(unsigned long long)(U(rk(ak[i]) - mn)) >> sh], 1u);
-    __syncthreads();
-    const uint32_t biggest = scan_counts(sub, nsub);
-    if (biggest > uint32_t(SUB_MAX)) {  // clustered keys: LSD over the varying bits
+    uint32_t *sub = wmask;
+    for (int i = tid; i < len; i += BLOCK) atomicAdd(&sub[R(R(rk(ak[i])) - lo) >> sh], 1u);
+    __syncthreads();  // [2] counts complete
+    // 3. exclusive scan of the counts and the largest count: per-thread runs of
+    //    counters, warp scans, every warp combines the warp totals itself
+    uint32_t *scr32 = s_cnt + 8 * NW;  // words of their own, past the range partials
+    const int per = (nsub + BLOCK - 1) / BLOCK;
+    const int b0 = tid * per, b1 = (b0 + per) < nsub ? (b0 + per) : nsub;
+    uint32_t sum = 0, big = 0;
+    for (int i = b0; i < b1; ++i) {
+      const uint32_t c = sub[i];
+      sum += c;
+      big = c > big ? c : big;
+    }
+    const uint32_t winc = warp_inclusive_scan(sum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t b2 = __shfl_xor_sync(0xffffffffu, big, o);
+      big = b2 > big ? b2 : big;
+    }
+    if (lane == 31) scr32[warp] = winc;
+    if (lane == 0) scr32[NW + warp] = big;
+    __syncthreads();  // [3] warp totals
+    {
+      const uint32_t t = lane < NW ? scr32[lane] : 0u;
+      const uint32_t tinc = warp_inclusive_scan(t);
+      const uint32_t wbase = __shfl_sync(0xffffffffu, tinc - t, warp);
+      big = lane < NW ? scr32[NW + lane] : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t b2 = __shfl_xor_sync(0xffffffffu, big, o);
+        big = b2 > big ? b2 : big;
+      }
+      uint32_t run = wbase + winc - sum;
+      for (int i = b0; i < b1; ++i) {
+        const uint32_t c = sub[i];
+        sub[i] = run;
+        run += c;
+      }
+    }
+    __syncthreads();  // [4] offsets in place
+    if (big > uint32_t(SUB_MAX)) {  // clustered keys: LSD over the varying bits
       for (int i = tid; i < nsub; i += BLOCK) sub[i] = 0u;
       copy(tk, tv, ak, av, len);  // buffer A stages the chunks of the passes
       __syncthreads();
-      const int lo = __ffsll((long long)vary) - 1;
-      const int hi = 63 - __clzll((long long)vary);
-      lsd_global(tk, tv, dk, dv, len, lo, hi, dk, dv);
+      const int vlo = __ffsll((long long)vary) - 1;
+      const int vhi = 63 - __clzll((long long)vary);
+      lsd_global(tk, tv, dk, dv, len, vlo, vhi, dk, dv);
       return;
     }
-    // input positions by sub-range (any order inside a sub-range) ...
+    // 4. input positions by sub-range (any order inside a sub-range) ...
     uint16_t *pos = reinterpret_cast<uint16_t *>(buf_k(1));
     for (int i = tid; i < len; i += BLOCK) {
-      const uint32_t slot = atomicAdd(&sub[(unsigned long long)(U(rk(ak[i]) - mn)) >> sh], 1u);
+      const uint32_t slot = atomicAdd(&sub[R(R(rk(ak[i])) - lo) >> sh], 1u);
       pos[slot] = uint16_t(i);
     }
-    __syncthreads();
-    // ... then each sub-range in (radix key, input position) order; sub[s] now
-    // holds the end of sub-range s
+    __syncthreads();  // [5]
+    // 5. ... then each sub-range in (radix key, input position) order; sub[s]
+    //    now holds the end of sub-range s
     for (int s_ = tid; s_ < nsub; s_ += BLOCK) {
       const int b = s_ ? int(sub[s_ - 1]) : 0, e = int(sub[s_]);
       for (int p = b + 1; p < e; ++p) {
@@ -435,14 +506,14 @@ struct SegCta {
         pos[q + 1] = x;
       }
     }
-    __syncthreads();
+    __syncthreads();  // [6]
+    // 6. gather out; the counters go back to zero for the next segment
     for (int i = tid; i < nsub; i += BLOCK) sub[i] = 0u;
     for (int j = tid; j < len; j += BLOCK) {
       const int x = pos[j];
       dk[j] = ak[x];
       if (HAS_V) dv[j] = av[x];
     }
-    __syncthreads();
   }
 
   // Chunked LSD through global memory over bits [lo, hi]: src -> alternating
@@ -488,6 +559,7 @@ struct SegCta {
       if (bl <= CAP) {
         sort_small(ak + bs, HAS_V ? av + bs : nullptr, gk + bs, HAS_V ? gv + bs : nullptr, int(bl), ak + bs,
                    HAS_V ? av + bs : nullptr);
+        __syncthreads();  // the next bucket reuses the shared buffers
       } else {
         // still too large: chunked LSD over the bits below the top digit
         const unsigned long long bv = vary_bits(ak + bs, bl);
@@ -524,11 +596,12 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
     nshort = a.split->nshort;
     nwork = nlong + nbuck + nshort;
   }
+  uint32_t par = 0;  // work slot: the next pop writes the other one, so one barrier per pop
   while (true) {
-    if (c.tid == 0) s_work[0] = atomicAdd(&a.hdr->work_counter[0], 1u);
-    __syncthreads();
-    const int64_t w = s_work[0];
-    __syncthreads();
+    if (c.tid == 0) s_work[par] = atomicAdd(&a.hdr->work_counter[0], 1u);
+    __syncthreads();  // also: the previous item's shared buffers are free
+    const int64_t w = s_work[par];
+    par ^= 1u;
     if (w >= nwork) break;
     if (w >= nlong && w < nlong + nbuck) {  // a bucket of a big segment: from the workspace copy into the keys
       const BucketItem it = a.buckets[w - nlong];
