@@ -66,7 +66,8 @@ typedef enum ak_status {
 } ak_status;
 
 typedef enum ak_op {
-    AK_OP_SORT = 0, AK_OP_SORTPERM = 1, AK_OP_SORT_PAIRS = 2, AK_OP_SORT_SEGMENTED = 3
+    AK_OP_SORT = 0, AK_OP_SORTPERM = 1, AK_OP_SORT_PAIRS = 2, AK_OP_SORT_SEGMENTED = 3,
+    AK_OP_SORTPERM_LOWMEM = 4
 } ak_op;
 
 typedef enum ak_path {
@@ -163,6 +164,19 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order,
  */
 ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
                       void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt);
+
+/*
+ * ak_sortperm with less temporary memory (Sec. II-B "sortperm_lowmem"): the
+ * same permutation, bit for bit, from a workspace that holds no copy of the
+ * keys (ak_sort_temp_bytes with AK_OP_SORTPERM_LOWMEM: about n * 4 bytes plus
+ * per-tile counters, where ak_sortperm needs 2 n * key bytes more).  Every
+ * digit pass moves only the indices and reads each key through its index from
+ * d_keys, so the passes after the first gather keys from anywhere in d_keys
+ * (slower than ak_sortperm).  Always the radix path; tile_config 4 runs as 1.
+ * Arguments, errors and limits as ak_sortperm.
+ */
+ak_status ak_sortperm_lowmem(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
+                             void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt);
 
 /*
  * In-place stable key-value sort (Sec. II-B "merge_sort_by_key"): keys and the

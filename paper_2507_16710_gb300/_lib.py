@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("AK_SORT_LIB") or os.path.join(_HERE, "lib", "libak_so
 
 AK_U16, AK_I16, AK_U32, AK_I32, AK_U64, AK_I64, AK_F32, AK_F64, AK_F16, AK_BF16 = range(10)
 AK_ASCENDING, AK_DESCENDING = 0, 1
-AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED = range(4)
+AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED, AK_OP_SORTPERM_LOWMEM = range(5)
 AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK, AK_PATH_MERGE = range(5)
 AK_TILE_CONFIGS = 4
 AK_DEBUG_SKIP_FIRST_TILE = 1
@@ -34,7 +34,7 @@ EXPORTED = (
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
     "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
     "ak_segment_capacity", "ak_autotune_temp_bytes", "ak_searchsortedfirst", "ak_searchsortedlast",
-    "ak_accumulate", "ak_accumulate_temp_bytes",
+    "ak_accumulate", "ak_accumulate_temp_bytes", "ak_sortperm_lowmem",
 )
 
 
@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
                 "ak_sort_temp_bytes": ([i32, i64, i32, i32, i64, opt, ctypes.POINTER(sz)], i32),
                 "ak_sort": ([p, i64, i32, i32, p, sz, p, opt], i32),
                 "ak_sortperm": ([p, p, i64, i32, i32, p, sz, p, opt], i32),
+                "ak_sortperm_lowmem": ([p, p, i64, i32, i32, p, sz, p, opt], i32),
                 "ak_sort_pairs": ([p, p, i32, i64, i32, i32, p, sz, p, opt], i32),
                 "ak_sort_segmented": ([p, p, i64, i64, i32, i32, p, sz, p, opt], i32),
                 "ak_status_check": ([p, p], i32),
@@ -220,6 +221,23 @@ def ak_sortperm(keys: torch.Tensor, order="ascending", *, perm=None, temp=None, 
     _check(load().ak_sortperm(keys.data_ptr(), perm.data_ptr(), n, kd, order_code(order),
                               temp.data_ptr(), temp.numel(), _stream_ptr(stream), _opts(options)),
            "ak_sortperm")
+    return perm
+
+
+def ak_sortperm_lowmem(keys: torch.Tensor, order="ascending", *, perm=None, temp=None, stream=None,
+                       options=None, unsigned: bool = False) -> torch.Tensor:
+    """ak_sortperm's permutation from a workspace without key copies (indices
+    only; keys are read through them)."""
+    _contig_cuda(keys, "keys")
+    kd = dtype_code(keys, unsigned)
+    n = keys.numel()
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device=keys.device)
+    _contig_cuda(perm, "perm")
+    temp = _temp_for(temp, AK_OP_SORTPERM_LOWMEM, n, kd, keys.device, options=options)
+    _check(load().ak_sortperm_lowmem(keys.data_ptr(), perm.data_ptr(), n, kd, order_code(order),
+                                     temp.data_ptr(), temp.numel(), _stream_ptr(stream), _opts(options)),
+           "ak_sortperm_lowmem")
     return perm
 
 

@@ -81,11 +81,16 @@ static RadixLayout radix_layout(int op, int64_t n, int key_bytes, int val_bytes,
   off += align256(size_t(tiles) * RADIX * sw);
   L.status1 = off;
   off += align256(size_t(tiles) * RADIX * sw);
-  L.k_alt0 = off;
-  off += align256(size_t(n) * key_bytes);
+  if (op != AK_OP_SORTPERM_LOWMEM) {  // the low-memory sortperm keeps no key copy
+    L.k_alt0 = off;
+    off += align256(size_t(n) * key_bytes);
+  }
   if (op == AK_OP_SORTPERM) {
     L.k_alt1 = off;
     off += align256(size_t(n) * key_bytes);
+    L.v_alt = off;
+    off += align256(size_t(n) * 4);
+  } else if (op == AK_OP_SORTPERM_LOWMEM) {
     L.v_alt = off;
     off += align256(size_t(n) * 4);
   } else if (op == AK_OP_SORT_PAIRS) {
@@ -220,7 +225,7 @@ static int choose_path(int op, int64_t n, int key_bytes, int vb, const ak_option
 }
 
 static int value_bytes(int op, int val_bytes) {
-  return (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
+  return (op == AK_OP_SORTPERM || op == AK_OP_SORTPERM_LOWMEM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
 }
 
 struct LearnedLayout;
@@ -229,6 +234,7 @@ static size_t learned_total(int op, int64_t n, int key_bytes, int val_bytes, con
 static size_t temp_for(int op, int64_t n, int key_bytes, int val_bytes, int64_t nseg, const ak_options &o) {
   const int vb = value_bytes(op, val_bytes);
   if (op == AK_OP_SORT_SEGMENTED) return seg_layout(op, n, nseg, key_bytes, 0).total;
+  if (op == AK_OP_SORTPERM_LOWMEM) return radix_layout(op, n, key_bytes, 4, min_tile_keys(key_bytes, 4)).total;
   const int path = choose_path(op, n, key_bytes, vb, o);
   if (path == AK_PATH_BLOCK || path == AK_PATH_MERGE) return seg_layout(op, n, 1, key_bytes, vb).total;
   if (path == AK_PATH_LEARNED) return learned_total(op, n, key_bytes, val_bytes, o);
@@ -478,25 +484,28 @@ static ak_status run_radix(int op, const void *k_in, void *k_final, const void *
                            size_t temp_bytes, cudaStream_t stream, const ak_options &o) {
   // Look-back arrays are sized for the smallest tile of any configuration, so
   // every configuration the launcher may pick fits.
-  const int vb = (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
+  const int vb = value_bytes(op, val_bytes);
   const RadixLayout L = radix_layout(op, n, ki.bytes, val_bytes, min_tile_keys(ki.bytes, vb));
   if (d_temp == nullptr || temp_bytes < L.total) return AK_ERR_WORKSPACE_TOO_SMALL;
   uint8_t *t = static_cast<uint8_t *>(d_temp);
   if (cudaMemsetAsync(t, 0, L.plan, stream) != cudaSuccess) return AK_ERR_CUDA;
   RadixCall c{};
-  c.mode = (op == AK_OP_SORTPERM) ? MODE_PERM : MODE_INPLACE;
+  const bool lowmem = op == AK_OP_SORTPERM_LOWMEM;
+  c.mode = (op == AK_OP_SORTPERM || lowmem) ? MODE_PERM : MODE_INPLACE;
+  c.gather = lowmem ? 1 : 0;
   c.k_in = k_in;
   c.k_final = k_final;
-  c.k_alt0 = t + L.k_alt0;
+  c.k_alt0 = lowmem ? nullptr : t + L.k_alt0;
   c.k_alt1 = (op == AK_OP_SORTPERM) ? t + L.k_alt1 : nullptr;
   c.v_in = v_in;
   c.v_final = v_final;
   c.v_alt = L.v_alt ? t + L.v_alt : nullptr;
-  c.val_bytes = (op == AK_OP_SORTPERM) ? 4 : (op == AK_OP_SORT_PAIRS ? val_bytes : 0);
+  c.val_bytes = vb;
   c.n = n;
   c.kind = ki.kind;
   c.descending = order == AK_DESCENDING;
   c.tile_config = (o.tile_config >= 1 && o.tile_config <= AK_TILE_CONFIGS) ? o.tile_config - 1 : CFG_DEFAULT;
+  if (lowmem && c.tile_config == CFG_WS) c.tile_config = 0;
   c.hdr = reinterpret_cast<DevHeader *>(t + L.hdr);
   c.counts = reinterpret_cast<unsigned long long *>(t + L.counts);
   c.plan = reinterpret_cast<RadixPlan *>(t + L.plan);
@@ -542,13 +551,13 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
                              const ak_options *opt, size_t *bytes) {
   KeyInfo ki;
   if (!bytes || n < 0 || !key_info(kd, &ki)) return AK_ERR_INVALID_ARG;
-  if (op < AK_OP_SORT || op > AK_OP_SORT_SEGMENTED) return AK_ERR_INVALID_ARG;
+  if (op < AK_OP_SORT || op > AK_OP_SORTPERM_LOWMEM) return AK_ERR_INVALID_ARG;
   if (op == AK_OP_SORT_PAIRS && val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8)
     return AK_ERR_INVALID_ARG;
   if (op == AK_OP_SORT_SEGMENTED && nseg < 0) return AK_ERR_INVALID_ARG;
   ak_options o;
   if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
-  if (op != AK_OP_SORT_SEGMENTED) apply_tuning(op, kd, n, val_bytes, o);
+  if (op != AK_OP_SORT_SEGMENTED && op != AK_OP_SORTPERM_LOWMEM) apply_tuning(op, kd, n, val_bytes, o);
   *bytes = temp_for(op, n, ki.bytes, val_bytes, nseg, o);
   return AK_OK;
 }
@@ -590,6 +599,19 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
   if (path == AK_PATH_LEARNED)
     return run_learned(AK_OP_SORTPERM, nullptr, d_keys, d_perm, 4, n, ki, order, d_temp, temp_bytes, st, o);
   return run_radix(AK_OP_SORTPERM, d_keys, nullptr, nullptr, d_perm, 4, n, ki, order, d_temp, temp_bytes, st, o);
+}
+
+ak_status ak_sortperm_lowmem(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
+                             void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt) {
+  KeyInfo ki;
+  ak_options o;
+  if (n < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
+  if (n == 0) return AK_OK;
+  if (n > int64_t(0xFFFFFFFFll)) return AK_ERR_INDEX_OVERFLOW;
+  if (!d_keys || !d_perm || !aligned(d_keys, ki.bytes) || !aligned(d_perm, 4)) return AK_ERR_INVALID_ARG;
+  if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
+  return run_radix(AK_OP_SORTPERM_LOWMEM, d_keys, nullptr, nullptr, d_perm, 4, n, ki, order, d_temp, temp_bytes,
+                   reinterpret_cast<cudaStream_t>(stream), o);
 }
 
 ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak_dtype kd, ak_order order,

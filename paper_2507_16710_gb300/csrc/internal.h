@@ -38,6 +38,7 @@ struct RadixCall {
   void **pass_events;      // optional profiling events (2 per pass)
   const uint32_t *gate;    // if set, every kernel runs only when *gate == gate_want
   uint32_t gate_want;
+  int gather;              // MODE_PERM with keys read through the index (no key copies)
   cudaStream_t stream;
 };
 

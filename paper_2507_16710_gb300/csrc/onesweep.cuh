@@ -78,7 +78,9 @@ struct PassArgs {
 // Digit of a key in a pass: a radix digit, a byte of the learned bucket id
 // evaluated from the key, or a byte of the value (a bucket id computed once and
 // carried along as the value).
-enum DigitSource : int { DIGIT_RADIX = 0, DIGIT_LEARNED = 1, DIGIT_VALUE = 2 };
+// DIGIT_GATHER (the low-memory sortperm): the index is the only data that
+// moves; each pass reads a key through its index from the caller's keys.
+enum DigitSource : int { DIGIT_RADIX = 0, DIGIT_LEARNED = 1, DIGIT_VALUE = 2, DIGIT_GATHER = 3 };
 
 // ------------------------------------------------------------------ histogram
 template <typename U, int BLOCK>
@@ -245,6 +247,8 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   constexpr int H2 = 2 * L::HSTRIDE;  // u16 slots per digit row
   static_assert(BLOCK >= RADIX, "one digit per thread in the scan and look-back");
   static_assert(DIGIT != DIGIT_VALUE || HAS_V, "a value-carried digit needs the value stream");
+  static_assert(DIGIT != DIGIT_GATHER || HAS_V, "gathered keys need the index stream");
+  constexpr bool GATHER = DIGIT == DIGIT_GATHER;  // keys are read through the index, never moved
   extern __shared__ __align__(128) uint8_t smem[];
   U *sk = reinterpret_cast<U *>(smem);
   V *sv = reinterpret_cast<V *>(smem + L::KEYS);
@@ -297,10 +301,12 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
     else vsrc = vbuf(q - 1);
   }
   const bool load_v = HAS_V && !gen_index;
-  const bool aligned = ((reinterpret_cast<uintptr_t>(ksrc) & 15) == 0) &&
+  const bool load_k = !GATHER;  // the stage holds the tile's keys (gathered keys are read in the ranking)
+  if (GATHER) write_keys = false;
+  const bool aligned = (!load_k || ((reinterpret_cast<uintptr_t>(ksrc) & 15) == 0)) &&
                        (!load_v || ((reinterpret_cast<uintptr_t>(vsrc) & 15) == 0));
   const int64_t full_tiles = a.n / TILE;  // tiles that need no bounds checks
-  auto is_bulk = [&](int64_t t) { return aligned && t < full_tiles; };
+  auto is_bulk = [&](int64_t t) { return aligned && t < full_tiles && (load_k || load_v); };
   uint32_t phase = 0;     // thread 0: parity of the next completion of bar
   bool pending = false;   // thread 0: a bulk copy is in flight
   auto claim = [&]() -> int64_t {
@@ -310,15 +316,15 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   constexpr int CLAIMER = BLOCK - 1;  // claims the next tile; not a look-back thread when BLOCK > RADIX
   auto issue = [&](int64_t t) {  // thread 0 only; the stage buffer must be free
     if (t < a.num_tiles && is_bulk(t)) {
-      mbar_expect_tx(bar, uint32_t(L::KEYS + (load_v ? L::VALS : 0)));
-      bulk_g2s(sk, ksrc + t * TILE, uint32_t(L::KEYS), bar);
+      mbar_expect_tx(bar, uint32_t((load_k ? L::KEYS : 0) + (load_v ? L::VALS : 0)));
+      if (load_k) bulk_g2s(sk, ksrc + t * TILE, uint32_t(L::KEYS), bar);
       if (load_v) bulk_g2s(sv, vsrc + t * TILE, uint32_t(L::VALS), bar);
       pending = true;
     }
   };
   auto prefetch_l2 = [&](int64_t t) {  // thread 0 only
     if (t < full_tiles && aligned) {
-      bulk_prefetch_l2(ksrc + t * TILE, uint32_t(L::KEYS));
+      if (load_k) bulk_prefetch_l2(ksrc + t * TILE, uint32_t(L::KEYS));
       if (load_v) bulk_prefetch_l2(vsrc + t * TILE, uint32_t(L::VALS));
     }
   };
@@ -362,7 +368,8 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
     const int64_t base = tile * TILE;
     const int tile_n = int((a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE));
     if (!is_bulk(tile)) {  // ragged last tile or unaligned source: plain loads
-      for (int i = tid; i < tile_n; i += BLOCK) sk[i] = ksrc[base + i];
+      if (load_k)
+        for (int i = tid; i < tile_n; i += BLOCK) sk[i] = ksrc[base + i];
       if (load_v)
         for (int i = tid; i < tile_n; i += BLOCK) sv[i] = vsrc[base + i];
       __syncthreads();
@@ -378,6 +385,10 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
         const int idx = wbase + i * 32 + lane;
         if constexpr (DIGIT == DIGIT_VALUE)
           dr[i] = (FULL || idx < tile_n) ? ((uint32_t(sv[idx]) >> shift) & uint32_t(RADIX - 1)) : uint32_t(RADIX);
+        else if constexpr (GATHER)  // the key of this item's index, from the caller's keys
+          dr[i] = (FULL || idx < tile_n)
+                      ? pass_digit<DIGIT_RADIX, KIND>(a, a.k_in[gen_index ? base + idx : int64_t(sv[idx])], shift)
+                      : uint32_t(RADIX);
         else
           dr[i] = (FULL || idx < tile_n) ? pass_digit<DIGIT, KIND>(a, sk[idx], shift) : uint32_t(RADIX);
       }
@@ -442,7 +453,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           if (FULL || d < RADIX) {
             const int idx = wbase + i * 32 + lane;
             const uint32_t pos = uint32_t(whist[d * H2 + warp]) + (dr[i] >> 9);
-            ok[pos] = sk[idx];
+            if (!GATHER) ok[pos] = sk[idx];
             if (HAS_V) ov[pos] = gen_index ? V(base + idx) : sv[idx];
             s_dig[pos] = uint8_t(d);
           }
@@ -524,7 +535,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
 #pragma unroll
           for (int r = 0; r < WB; ++r) {
             const int i = (r0 + r) * BLOCK + tid;
-            k[r] = ok[i];
+            k[r] = GATHER ? U(0) : ok[i];
             dst[r] = (long long)s_delta[s_dig[i]] + i;
           }
 #pragma unroll
@@ -535,7 +546,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
         }
       } else {
         for (int i = tid; i < tile_n; i += BLOCK) {
-          const U k = ok[i];
+          const U k = GATHER ? U(0) : ok[i];
           const long long dst = (long long)s_delta[s_dig[i]] + i;
           if (write_keys) kdst[dst] = k;
           if (HAS_V) vdst[dst] = ov[i];

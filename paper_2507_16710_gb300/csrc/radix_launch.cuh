@@ -55,9 +55,9 @@ struct PassKernel {
                 "tile shape");
 };
 
-template <typename U, typename V, bool HAS_V, int KIND, typename S, int CFG>
+template <typename U, typename V, bool HAS_V, int KIND, typename S, int CFG, int DIGIT = DIGIT_RADIX>
 cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
-  using P = PassKernel<U, V, HAS_V, KIND, S, CFG>;
+  using P = PassKernel<U, V, HAS_V, KIND, S, CFG, DIGIT>;
   constexpr int BLOCK = P::BLOCK;
   constexpr bool PERSIST = P::PERSIST;
   constexpr int TILE = P::TILE;
@@ -119,6 +119,16 @@ cudaError_t run_status(const RadixCall &c) {
   a.debug_skip = (c.debug_flags & AK_DEBUG_SKIP_FIRST_TILE) ? 1 : 0;
   a.gate = c.gate;
   a.gate_want = c.gate_want;
+  if constexpr (HAS_V && std::is_same<V, uint32_t>::value) {
+    if (c.gather) {  // low-memory sortperm: the shared-memory-staged configurations only
+      if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, 0, DIGIT_GATHER>(c, a);
+      switch (c.tile_config) {
+        case 1: return run_passes<U, V, HAS_V, KIND, uint32_t, 1, DIGIT_GATHER>(c, a);
+        case 2: return run_passes<U, V, HAS_V, KIND, uint32_t, 2, DIGIT_GATHER>(c, a);
+        default: return run_passes<U, V, HAS_V, KIND, uint32_t, 0, DIGIT_GATHER>(c, a);
+      }
+    }
+  }
   if (c.status_wide) {  // 64-bit look-back words: configurations 0 and 3
     if (c.tile_config == CFG_WS) return run_passes<U, V, HAS_V, KIND, unsigned long long, CFG_WS>(c, a);
     return run_passes<U, V, HAS_V, KIND, unsigned long long, 0>(c, a);

@@ -236,3 +236,15 @@ def test_binding_refuses_host_tensors_and_mismatches(lib):
     assert ak.accumulate_temp_bytes(0, ak.AK_F64) >= 256
     with pytest.raises(ak.AkError):
         ak.accumulate_temp_bytes(-1, ak.AK_F64)
+
+
+def test_sortperm_lowmem_workspace_is_smaller(lib):
+    """The low-memory sortperm's workspace holds no key copy: at least 2 n x key
+    bytes below ak_sortperm's radix workspace, about n x 4 bytes in all."""
+    import paper_2507_16710_gb300 as ak
+    n = 1 << 24
+    for kd, kb in ((ak.AK_I64, 8), (ak.AK_F32, 4), (ak.AK_U16, 2), (ak.AK_BF16, 2)):
+        full = ak.temp_bytes(ak.AK_OP_SORTPERM, n, kd, options={"path": ak.AK_PATH_RADIX})
+        low = ak.temp_bytes(ak.AK_OP_SORTPERM_LOWMEM, n, kd)
+        assert low + 2 * n * kb <= full, (kd, low, full)
+        assert low < n * 4 + (n // 1000) * 1024 + (1 << 20), (kd, low)

@@ -246,3 +246,35 @@ def test_full_size_268M(ak, which):
         assert_bits_equal(to_host(t, keys.dtype), keys[perm.astype(np.int64)], "full-size sort")
         del t
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("desc", [False, True])
+def test_sortperm_lowmem_matches_oracle(ak, dtype, desc):
+    """ak_sortperm_lowmem (Sec. II-B sortperm_lowmem): the permutation of
+    ak_sortperm from a workspace without key copies, keys read through the
+    index in every pass."""
+    for n in (1, 2, 3841, 6145, 100_003):
+        keys = synth.random_keys(n, dtype, seed=9000 + n, mode="dups" if n % 2 else "bits")
+        want = oracle_perm(keys, desc).astype(np.uint32)
+        t, u = to_dev(keys)
+        p = ak.ak_sortperm_lowmem(t, "descending" if desc else "ascending", unsigned=u)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(p, np.uint32), want), (np.dtype(dtype), n, desc)
+        assert_bits_equal(to_host(t, keys.dtype), keys, "lowmem keeps the keys")
+
+
+def test_sortperm_lowmem_configs_unaligned_and_many_tiles(ak):
+    keys = synth.random_keys(3_000_001, np.float64, seed=9100, mode="bits")
+    want = oracle_perm(keys, False, threads=8).astype(np.uint32)
+    for cfg in (0, 1, 2, 3, 4):
+        t, _ = to_dev(keys)
+        p = ak.ak_sortperm_lowmem(t, options={"tile_config": cfg})
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(p, np.uint32), want), cfg
+    base = synth.random_keys(200_001, np.int32, seed=9101, mode="bits")
+    t, _ = to_dev(base)
+    p = ak.ak_sortperm_lowmem(t[1:])  # keys off 16-byte alignment
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(p, np.uint32), oracle_perm(base[1:], False).astype(np.uint32))
+

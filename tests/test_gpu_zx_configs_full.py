@@ -186,6 +186,10 @@ def test_wide_lookback_words_above_2_30(ak):
     p = ak.ak_sortperm(t, options=rad, unsigned=u)
     torch.cuda.synchronize()
     perm = to_host(p, np.uint32)
+    del p
+    check_perm_properties(keys, perm, descending=False)
+    p = ak.ak_sortperm_lowmem(t, unsigned=u)  # the gather passes with 64-bit look-back words
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(p, np.uint32), perm), "lowmem sortperm differs from sortperm"
     del p, t
     torch.cuda.empty_cache()
-    check_perm_properties(keys, perm, descending=False)
