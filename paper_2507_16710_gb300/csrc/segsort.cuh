@@ -263,6 +263,7 @@ struct SegCta {
   // staged through buffer A so that every warp stores digit runs.  If
   // `buckets`, s_bst/s_bcnt receive the digit starts/counts.
   __device__ void pass_global(const U *sk, const V *sv, U *dk, V *dv, int64_t len, int shift, bool buckets) {
+    for (int i = tid; i < NW * HROW; i += BLOCK) wmask[i] = 0u;  // ranking state (sort_small leaves counters)
     digit_offsets(sk, len, shift);
     if (buckets && tid < RADIX) {
       s_bst[tid] = s_run[tid];
@@ -375,7 +376,7 @@ struct SegCta {
 
   // Sort gk/gv[0, len) (global) into dk/dv (global, may alias gk/gv), len <= CAP;
   // tk/tv: len elements of global scratch other than dk/dv (may alias gk/gv).
-  // Six CTA barriers; the caller separates consecutive calls by a barrier.
+  // Five CTA barriers; the caller separates consecutive calls by a barrier.
   __device__ void sort_small(const U *gk, const V *gv, U *dk, V *dv, int len, U *tk, V *tv) {
     // radix-key arithmetic in 32 bits for keys of 32 bits or less
     using R = typename std::conditional<(sizeof(U) <= 4), uint32_t, unsigned long long>::type;
@@ -385,6 +386,8 @@ struct SegCta {
     //    OR of (r ^ r of the first key), reduced per warp, then by every warp
     //    over the warp partials
     R *scr = reinterpret_cast<R *>(s_cnt);  // 3 x NW partials
+    uint32_t *sub = wmask;                   // sub-range counters, cleared here for this segment
+    for (int i = tid; i < (1 << SUB_BITS); i += BLOCK) sub[i] = 0u;
     const R r0 = R(rk(gk[0]));
     R lo = R(~R(0)), hi = 0, vary = 0;
     for (int i = tid; i < len; i += BLOCK) {
@@ -431,7 +434,6 @@ struct SegCta {
     want = want < 1 ? 1 : (want > SUB_BITS ? SUB_BITS : want);
     const int sh = span_bits > want ? span_bits - want : 0;
     const int nsub = int(span >> sh) + 1;
-    uint32_t *sub = wmask;
     for (int i = tid; i < len; i += BLOCK) atomicAdd(&sub[R(R(rk(ak[i])) - lo) >> sh], 1u);
     __syncthreads();  // [2] counts complete
     // 3. exclusive scan of the counts and the largest count: per-thread runs of
@@ -487,32 +489,26 @@ struct SegCta {
       const uint32_t slot = atomicAdd(&sub[R(R(rk(ak[i])) - lo) >> sh], 1u);
       pos[slot] = uint16_t(i);
     }
-    __syncthreads();  // [5]
-    // 5. ... then each sub-range in (radix key, input position) order; sub[s]
-    //    now holds the end of sub-range s
-    for (int s_ = tid; s_ < nsub; s_ += BLOCK) {
-      const int b = s_ ? int(sub[s_ - 1]) : 0, e = int(sub[s_]);
-      for (int p = b + 1; p < e; ++p) {
-        const uint16_t x = pos[p];
-        const U rx = rk(ak[x]);
-        int q = p - 1;
-        while (q >= b) {
-          const uint16_t y = pos[q];
-          const U ry = rk(ak[y]);
-          if (ry < rx || (ry == rx && y < x)) break;
-          pos[q + 1] = y;
-          --q;
-        }
-        pos[q + 1] = x;
-      }
-    }
-    __syncthreads();  // [6]
-    // 6. gather out; the counters go back to zero for the next segment
-    for (int i = tid; i < nsub; i += BLOCK) sub[i] = 0u;
+    __syncthreads();  // [5] sub[s] now holds the end of sub-range s
+    // 5. ... then every key finds its place in its sub-range by counting the
+    //    keys there that come before it in (radix key, input position) order
+    //    (independent loads: no chain of dependent moves), and goes straight to
+    //    its output slot.  The counters stay as they are: the next segment
+    //    clears them, and pass_global clears them before it ranks.
     for (int j = tid; j < len; j += BLOCK) {
       const int x = pos[j];
-      dk[j] = ak[x];
-      if (HAS_V) dv[j] = av[x];
+      const U kx = ak[x];
+      const R rx = R(rk(kx));
+      const uint32_t s_ = uint32_t(R(rx - lo) >> sh);
+      const int b = s_ ? int(sub[s_ - 1]) : 0, e = int(sub[s_]);
+      int rank = 0;
+      for (int i = b; i < e; ++i) {
+        const int y = pos[i];
+        const R ry = R(rk(ak[y]));
+        rank += (ry < rx || (ry == rx && y < x)) ? 1 : 0;
+      }
+      dk[b + rank] = kx;
+      if (HAS_V) dv[b + rank] = av[x];
     }
   }
 
