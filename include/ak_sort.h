@@ -81,8 +81,9 @@ typedef enum ak_path {
 
 /* Optional tuning knobs.  Pass NULL for defaults; zero fields mean "default".
  * A field outside its documented range (unknown path, tile configuration or
- * debug flag, bucket_bits not 0 or 8..16, train_steps below -1, a nonzero
- * reserved word) makes the call return AK_ERR_INVALID_ARG with nothing
+ * debug flag, bucket_bits not 0 or 8..16, train_steps below -1, digit_bits not 0
+ * or 8, split_caps outside -1..1024, a nonzero reserved word) makes the call
+ * return AK_ERR_INVALID_ARG with nothing
  * enqueued; the options are checked before the n = 0 early return, so an
  * empty call with malformed options is refused too. */
 typedef struct ak_options {
@@ -104,7 +105,15 @@ typedef struct ak_options {
     void **pass_events;    /* optional: 2*AK_MAX_PASSES cudaEvent_t created by the caller;
                               the radix path records [2p] before and [2p+1] after the
                               launch of digit pass p on the call's stream (profiling) */
-    int32_t reserved[4];   /* must be zero */
+    int32_t digit_bits;    /* radix digit width: 0 = default = 8, the only width built
+                              (an 11-bit digit pass is not), so any other value is refused */
+    int32_t split_caps;    /* ak_sort_segmented: segments longer than split_caps times the
+                              shared-memory capacity (ak_segment_capacity) are cut into
+                              buckets by all CTAs together before the per-CTA sort; shorter
+                              ones above the capacity are sorted by one CTA through global
+                              memory.  0 = autotuned choice, else 8; -1 = never split;
+                              else 1..1024 */
+    int32_t reserved[2];   /* must be zero */
 } ak_options;
 
 #define AK_MAX_PASSES 8
@@ -362,8 +371,23 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
                       size_t temp_bytes, ak_stream_t stream, ak_options *best);
 /* Workspace ak_autotune needs for this call shape (host only). */
 ak_status ak_autotune_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, size_t *bytes);
+
+/*
+ * Tunes ak_sort_segmented for the caller's batch: times the split threshold
+ * (split_caps 1, 2, 4, 8, 16 and never) on d_keys / d_offsets (restored from a
+ * copy before every timed call; the keys hold their input again on return) and
+ * caches the fastest under (dtype, ceil(log2 n), ceil(log2 nseg)); segmented
+ * calls with split_caps 0 take it.  d_temp: ak_autotune_segmented_temp_bytes
+ * bytes.  Synchronises `stream`.  `best` (optional) receives the choice.
+ */
+ak_status ak_autotune_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg, int64_t n, ak_dtype kd,
+                                ak_order order, void *d_temp, size_t temp_bytes, ak_stream_t stream,
+                                ak_options *best);
+ak_status ak_autotune_segmented_temp_bytes(int64_t n, int64_t nseg, ak_dtype kd, size_t *bytes);
 /* The cache as JSON lines {"op", "dtype", "log2n", "val_bytes", "path",
- * "tile_config", "ms", "bucket_bits"} (bucket_bits optional, 0 = automatic): save, load (merging; malformed lines are skipped), clear. */
+ * "tile_config", "ms", "bucket_bits", "split_caps"} (bucket_bits and split_caps
+ * optional, 0 = automatic; segmented entries have op 3 and ceil(log2 nseg) in
+ * val_bytes): save, load (merging; malformed lines are skipped), clear. */
 ak_status ak_autotune_save(const char *path);
 ak_status ak_autotune_load(const char *path);
 void ak_autotune_clear(void);

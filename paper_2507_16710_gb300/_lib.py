@@ -34,7 +34,8 @@ EXPORTED = (
     "ak_learned_loss_grad", "ak_learned_grad_temp_bytes", "ak_autotune", "ak_autotune_save",
     "ak_autotune_load", "ak_autotune_clear", "ak_version", "ak_sort_static_scratch",
     "ak_segment_capacity", "ak_autotune_temp_bytes", "ak_searchsortedfirst", "ak_searchsortedlast",
-    "ak_accumulate", "ak_accumulate_temp_bytes", "ak_sortperm_lowmem",
+    "ak_accumulate", "ak_accumulate_temp_bytes", "ak_sortperm_lowmem", "ak_autotune_segmented",
+    "ak_autotune_segmented_temp_bytes",
 )
 
 
@@ -49,7 +50,8 @@ class Options(ctypes.Structure):
                 ("bucket_bits", ctypes.c_int32), ("seed", ctypes.c_uint32),
                 ("timeout_ns", ctypes.c_uint64), ("train_steps", ctypes.c_int32),
                 ("debug_flags", ctypes.c_int32), ("pass_events", ctypes.c_void_p),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("digit_bits", ctypes.c_int32), ("split_caps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Info(ctypes.Structure):
@@ -100,6 +102,8 @@ def load() -> ctypes.CDLL:
                 "ak_sort_static_scratch": ([p, i64, i32, i32, p], i32),
                 "ak_segment_capacity": ([i32, i32], i64),
                 "ak_autotune_temp_bytes": ([i32, i64, i32, i32, ctypes.POINTER(sz)], i32),
+                "ak_autotune_segmented": ([p, p, i64, i64, i32, i32, p, sz, p, opt], i32),
+                "ak_autotune_segmented_temp_bytes": ([i64, i64, i32, ctypes.POINTER(sz)], i32),
                 "ak_searchsortedfirst": ([p, i64, p, i64, i32, i32, p, p], i32),
                 "ak_searchsortedlast": ([p, i64, p, i64, i32, i32, p, p], i32),
                 "ak_accumulate": ([p, p, i64, i32, i32, i32, p, p, sz, p, opt], i32),
@@ -421,6 +425,26 @@ def ak_autotune(op: int, keys: torch.Tensor, order="ascending", vals=None, perm=
                               vals.data_ptr() if vals is not None else None,
                               perm.data_ptr() if perm is not None else None, temp.data_ptr(),
                               temp.numel(), _stream_ptr(stream), ctypes.byref(best)), "ak_autotune")
+    return best
+
+
+def ak_autotune_segmented(keys: torch.Tensor, offsets: torch.Tensor, order="ascending", temp=None, stream=None,
+                          unsigned: bool = False) -> Options:
+    """Time the split thresholds of ak_sort_segmented on this batch and cache
+    the fastest; returns it (split_caps)."""
+    _contig_cuda(keys, "keys")
+    _contig_cuda(offsets, "offsets")
+    kd = dtype_code(keys, unsigned)
+    n, nseg = keys.numel(), offsets.numel() - 1
+    if temp is None:
+        out = ctypes.c_size_t(0)
+        _check(load().ak_autotune_segmented_temp_bytes(n, nseg, kd, ctypes.byref(out)),
+               "ak_autotune_segmented_temp_bytes")
+        temp = workspace(out.value, keys.device)
+    best = Options()
+    _check(load().ak_autotune_segmented(keys.data_ptr(), offsets.data_ptr(), nseg, n, kd, order_code(order),
+                                        temp.data_ptr(), temp.numel(), _stream_ptr(stream), ctypes.byref(best)),
+           "ak_autotune_segmented")
     return best
 
 

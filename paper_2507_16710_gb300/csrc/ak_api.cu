@@ -111,6 +111,8 @@ bool resolve_options(const ak_options *opt, ak_options *o) {
   if (o->bucket_bits != 0 && (o->bucket_bits < 8 || o->bucket_bits > 16)) return false;
   if (o->train_steps < -1) return false;
   if (o->debug_flags & ~(AK_DEBUG_SKIP_FIRST_TILE | AK_DEBUG_NO_PREFETCH)) return false;
+  if (o->digit_bits != 0 && o->digit_bits != RADIX_BITS) return false;
+  if (o->split_caps < -1 || o->split_caps > 1024) return false;
   for (int r : o->reserved)
     if (r != 0) return false;
   if (o->timeout_ns == 0) o->timeout_ns = 1000000000ull;
@@ -244,7 +246,7 @@ static size_t temp_for(int op, int64_t n, int key_bytes, int val_bytes, int64_t 
 // Segmented sort, or the one-launch block sort of a single segment (off NULL).
 static ak_status run_seg(int op, void *keys, const int64_t *off, int64_t nseg, int64_t n, const void *k_in,
                          void *vals, int val_bytes, const KeyInfo &ki, int order, void *d_temp, size_t temp_bytes,
-                         cudaStream_t stream, int merge = 0) {
+                         cudaStream_t stream, int merge = 0, int64_t split_min = 0) {
   const int vb = value_bytes(op, val_bytes);
   const SegLayout L = seg_layout(op, n, off ? nseg : 1, ki.bytes, vb);
   if (d_temp == nullptr || temp_bytes < L.total) return AK_ERR_WORKSPACE_TOO_SMALL;
@@ -275,6 +277,7 @@ static ak_status run_seg(int op, void *keys, const int64_t *off, int64_t nseg, i
   c.path_tag = merge ? AK_PATH_MERGE : AK_PATH_BLOCK;
   c.merge = merge;
   if (op == AK_OP_SORT_SEGMENTED) {
+    c.split_min = split_min;
     c.split_state = t + L.split_state;
     c.split_big = t + L.split_big;
     c.split_tcount = reinterpret_cast<uint32_t *>(t + L.split_tcount);
@@ -647,8 +650,11 @@ ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg
   if (n > int64_t(0xFFFFFFFFll) || nseg > int64_t(0xFFFFFFFFll)) return AK_ERR_UNSUPPORTED;
   if (!d_keys || !d_offsets || !aligned(d_keys, ki.bytes) || !aligned(d_offsets, 8)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
+  int caps = o.split_caps;
+  if (caps == 0 && !tune_lookup_segmented(kd, n, nseg, &caps)) caps = SPLIT_MIN_CAPS;
+  const int64_t cap = seg_cap(ki.bytes, 0);
   return run_seg(AK_OP_SORT_SEGMENTED, d_keys, d_offsets, nseg, n, nullptr, nullptr, 0, ki, order, d_temp,
-                 temp_bytes, reinterpret_cast<cudaStream_t>(stream));
+                 temp_bytes, reinterpret_cast<cudaStream_t>(stream), 0, caps < 0 ? -1 : int64_t(caps) * cap);
 }
 
 ak_status ak_status_check(const void *d_temp, ak_stream_t stream) {

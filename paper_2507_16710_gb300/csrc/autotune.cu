@@ -1,6 +1,7 @@
 // autotune.cu -- timed choice of path and tile configuration per call shape.
 //
-// ak_autotune runs every candidate (radix with each tile configuration, the
+// ak_autotune runs every candidate (radix with each tile configuration -- the
+// configurations differ in threads per CTA, keys per thread and persistence --, the
 // learned path with its own bucket count and with half and twice as many
 // buckets, the one-launch block path when n fits it, else the merge path up to
 // 2^26 keys) on the caller's
@@ -27,6 +28,7 @@ namespace {
 struct TuneEntry {
   int path, tile_config, bucket_bits;
   float ms;
+  int split_caps;  // segmented entries: split threshold in capacities (-1 = never)
 };
 using TuneKey = std::tuple<int, int, int, int>;  // op, dtype, log2 n, value bytes
 
@@ -45,16 +47,16 @@ ak_status load_file(const char *path) {
   if (!f) return AK_ERR_INVALID_ARG;
   char line[512];
   while (fgets(line, sizeof line, f)) {
-    int op, dt, lg, vb, pth, tc, bb = 0;
+    int op, dt, lg, vb, pth, tc, bb = 0, sc = 0;
     float ms;
-    // bucket_bits is optional (entries written before it existed mean "automatic")
+    // bucket_bits and split_caps are optional (absent: "automatic")
     const int got = sscanf(line,
                            " {\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
-                           "\"tile_config\": %d, \"ms\": %f, \"bucket_bits\": %d}",
-                           &op, &dt, &lg, &vb, &pth, &tc, &ms, &bb);
-    if ((got == 7 || got == 8) && pth >= AK_PATH_RADIX && pth <= AK_PATH_MERGE && tc >= 0 &&
-        tc <= AK_TILE_CONFIGS && (bb == 0 || (bb >= 8 && bb <= 16)))
-      g_cache[TuneKey(op, dt, lg, vb)] = TuneEntry{pth, tc, bb, ms};
+                           "\"tile_config\": %d, \"ms\": %f, \"bucket_bits\": %d, \"split_caps\": %d}",
+                           &op, &dt, &lg, &vb, &pth, &tc, &ms, &bb, &sc);
+    if ((got >= 7 && got <= 9) && pth >= AK_PATH_RADIX && pth <= AK_PATH_MERGE && tc >= 0 &&
+        tc <= AK_TILE_CONFIGS && (bb == 0 || (bb >= 8 && bb <= 16)) && sc >= -1 && sc <= 1024)
+      g_cache[TuneKey(op, dt, lg, vb)] = TuneEntry{pth, tc, bb, ms, sc};
   }
   fclose(f);
   return AK_OK;
@@ -80,17 +82,35 @@ bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *ti
   return true;
 }
 
+bool tune_lookup_segmented(int dtype, int64_t n, int64_t nseg, int *split_caps) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  load_env_once();
+  auto it = g_cache.find(TuneKey(AK_OP_SORT_SEGMENTED, dtype, log2_class(n), log2_class(nseg)));
+  if (it == g_cache.end() || it->second.split_caps == 0) return false;
+  *split_caps = it->second.split_caps;
+  return true;
+}
+
 }  // namespace ak
 
 using namespace ak;
+
+static int key_bytes_of(ak_dtype kd) {
+  switch (kd) {
+    case AK_U16: case AK_I16: case AK_F16: case AK_BF16: return 2;
+    case AK_U32: case AK_I32: case AK_F32: return 4;
+    case AK_U64: case AK_I64: case AK_F64: return 8;
+  }
+  return 0;
+}
 
 // Candidates of one call shape and the workspace ak_autotune needs for them:
 // the largest candidate's temporaries (256-byte aligned), then a copy of the inputs.
 static ak_status candidates(int op, int64_t n, ak_dtype kd, int val_bytes, std::vector<ak_options> *cands,
                             size_t *need, size_t *input_bytes) {
   if (op != AK_OP_SORT && op != AK_OP_SORTPERM && op != AK_OP_SORT_PAIRS) return AK_ERR_INVALID_ARG;
-  if (n <= 0 || int(kd) < int(AK_U16) || int(kd) > int(AK_F64)) return AK_ERR_INVALID_ARG;
-  const int kb = (kd <= AK_I16) ? 2 : (kd <= AK_I32 || kd == AK_F32) ? 4 : 8;
+  const int kb = key_bytes_of(kd);
+  if (n <= 0 || kb == 0) return AK_ERR_INVALID_ARG;
   const int vb = (op == AK_OP_SORT_PAIRS) ? val_bytes : 0;
   if (op == AK_OP_SORT_PAIRS && vb != 1 && vb != 2 && vb != 4 && vb != 8) return AK_ERR_INVALID_ARG;
   cands->clear();
@@ -152,7 +172,7 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
   (void)inb;
   if (!d_keys || !d_temp || (op == AK_OP_SORT_PAIRS && !d_vals) || (op == AK_OP_SORTPERM && !d_perm))
     return AK_ERR_INVALID_ARG;
-  const int kb = (kd <= AK_I16) ? 2 : (kd <= AK_I32 || kd == AK_F32) ? 4 : 8;
+  const int kb = key_bytes_of(kd);
   const int vb = (op == AK_OP_SORT_PAIRS) ? val_bytes : 0;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t kbytes = size_t(n) * kb, vbytes = size_t(n) * vb;
@@ -210,9 +230,85 @@ ak_status ak_autotune(int op, int64_t n, ak_dtype kd, int val_bytes, ak_order or
   {
     std::lock_guard<std::mutex> lock(g_mu);
     g_cache[TuneKey(op, int(kd), log2_class(n), vb)] = TuneEntry{best_o.path, best_o.tile_config, best_o.bucket_bits,
-                                                                 best_ms};
+                                                                 best_ms, 0};
   }
   if (best) *best = best_o;
+  return result;
+}
+
+static const int kSplitCands[] = {1, 2, 4, 8, 16, -1};
+
+ak_status ak_autotune_segmented_temp_bytes(int64_t n, int64_t nseg, ak_dtype kd, size_t *bytes) {
+  if (!bytes || n <= 0 || nseg <= 0 || key_bytes_of(kd) == 0) return AK_ERR_INVALID_ARG;
+  size_t need = 0;
+  const ak_status s = ak_sort_temp_bytes(AK_OP_SORT_SEGMENTED, n, kd, 0, nseg, nullptr, &need);
+  if (s != AK_OK) return s;
+  *bytes = ((need + 255) & ~size_t(255)) + size_t(n) * key_bytes_of(kd);
+  return AK_OK;
+}
+
+ak_status ak_autotune_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg, int64_t n, ak_dtype kd,
+                                ak_order order, void *d_temp, size_t temp_bytes, ak_stream_t stream,
+                                ak_options *best) {
+  size_t total = 0;
+  const ak_status ts = ak_autotune_segmented_temp_bytes(n, nseg, kd, &total);
+  if (ts != AK_OK) return ts;
+  if (!d_keys || !d_offsets || !d_temp) return AK_ERR_INVALID_ARG;
+  if (temp_bytes < total) return AK_ERR_WORKSPACE_TOO_SMALL;
+  const size_t kbytes = size_t(n) * key_bytes_of(kd);
+  const size_t need = total - kbytes;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t *copy_k = static_cast<uint8_t *>(d_temp) + need;
+  if (cudaMemcpyAsync(copy_k, d_keys, kbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return AK_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return AK_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return AK_ERR_CUDA;
+  }
+  ak_status result = AK_OK;
+  float best_ms = INFINITY;
+  int best_caps = 0;
+  for (int caps : kSplitCands) {
+    ak_options o{};
+    o.split_caps = caps;
+    float tot = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {  // one warm-up, three timed
+      if (cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaEventRecord(e0, st) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      const ak_status s = ak_sort_segmented(d_keys, d_offsets, nseg, n, kd, order, d_temp, need, stream, &o);
+      if (s != AK_OK || cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      if (ak_status_check(d_temp, stream) != AK_OK) ok = false;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;
+    }
+    if (ok && tot / 3.f < best_ms) {
+      best_ms = tot / 3.f;
+      best_caps = caps;
+    }
+  }
+  if (cudaMemcpyAsync(d_keys, copy_k, kbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) result = AK_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) result = AK_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!isfinite(best_ms)) return result == AK_OK ? AK_ERR_CUDA : result;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_cache[TuneKey(AK_OP_SORT_SEGMENTED, int(kd), log2_class(n), log2_class(nseg))] =
+        TuneEntry{AK_PATH_BLOCK, 0, 0, best_ms, best_caps};
+  }
+  if (best) {
+    *best = ak_options{};
+    best->split_caps = best_caps;
+  }
   return result;
 }
 
@@ -226,8 +322,9 @@ ak_status ak_autotune_save(const char *path) {
     std::tie(op, dt, lg, vb) = kv.first;
     fprintf(f,
             "{\"op\": %d, \"dtype\": %d, \"log2n\": %d, \"val_bytes\": %d, \"path\": %d, "
-            "\"tile_config\": %d, \"ms\": %.6f, \"bucket_bits\": %d}\n",
-            op, dt, lg, vb, kv.second.path, kv.second.tile_config, kv.second.ms, kv.second.bucket_bits);
+            "\"tile_config\": %d, \"ms\": %.6f, \"bucket_bits\": %d, \"split_caps\": %d}\n",
+            op, dt, lg, vb, kv.second.path, kv.second.tile_config, kv.second.ms, kv.second.bucket_bits,
+            kv.second.split_caps);
   }
   fclose(f);
   return AK_OK;

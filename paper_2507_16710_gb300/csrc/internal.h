@@ -138,6 +138,7 @@ struct SegCall {
   void *split_big;         // BigSeg[split_big_cap]
   uint32_t *split_tcount;  // RADIX counters per split tile
   void *split_buckets;     // BucketItem[split_bucket_cap]
+  int64_t split_min;       // split segments above this many keys; 0: SPLIT_MIN_CAPS x capacity; < 0: none
   cudaStream_t stream;
 };
 // Split workspace of a segmented sort of n keys (key_bytes + val_bytes wide):
@@ -214,6 +215,9 @@ bool resolve_options(const ak_options *opt, ak_options *o);
 
 // Autotune cache: the tuned path and tile configuration of a call shape.
 bool tune_lookup(int op, int dtype, int64_t n, int val_bytes, int *path, int *tile_config, int *bucket_bits);
+// Autotune cache of the segmented sort: the split threshold (in capacities,
+// -1 = never) of a batch shape.
+bool tune_lookup_segmented(int dtype, int64_t n, int64_t nseg, int *split_caps);
 // Bucket bits the learned path picks by itself for a call shape.
 int learned_auto_bucket_bits(int op, int64_t n, int key_bytes, int val_bytes);
 

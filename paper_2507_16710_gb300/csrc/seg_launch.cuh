@@ -53,8 +53,9 @@ cudaError_t seg_run(const SegCall &c) {
     auto big = reinterpret_cast<BigSeg *>(c.split_big);
     auto bk = reinterpret_cast<BucketItem *>(c.split_buckets);
     const int64_t g = (c.nseg + 255) / 256;
-    split_classify_kernel<<<unsigned(g), 256, 0, c.stream>>>(c.off, c.nseg, c.n, CAP, int64_t(SPLIT_MIN_CAPS) * CAP,
-                                                             c.order, big, st, c.gate, c.gate_want);
+    const int64_t split_min = c.split_min > 0 ? c.split_min : (c.split_min < 0 ? INT64_MAX : int64_t(SPLIT_MIN_CAPS) * CAP);
+    split_classify_kernel<<<unsigned(g), 256, 0, c.stream>>>(c.off, c.nseg, c.n, CAP, split_min, c.order, big, st,
+                                                             c.gate, c.gate_want);
     split_tiles_kernel<<<1, 1024, 0, c.stream>>>(big, st, T, c.gate, c.gate_want);
     split_vary_kernel<U, KIND><<<unsigned(sms * 4), SPLIT_BLOCK, 0, c.stream>>>(a.keys, big, st, T, a.flip, c.gate,
                                                                                 c.gate_want);

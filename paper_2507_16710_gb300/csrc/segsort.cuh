@@ -2,15 +2,19 @@
 // persistent launch (and the one-launch small-n sort, a single segment).
 //
 // classify_kernel  builds the work order: segments above the shared-memory
-//                  capacity first (they take longest), then the rest
-// segsort_kernel   persistent CTAs pop segments from a device work counter.
+//                  capacity first (they take longest), then the rest (with
+//                  the device-wide split of segsplit.cuh, its classifier
+//                  builds the order instead)
+// segsort_kernel   persistent CTAs pop work items from a device work counter.
 //   * L <= CAP: the segment is loaded into shared memory and its radix-key
-//     range [rmin, rmax] found.  One counting pass spreads the keys over up to
-//     2^SUB_BITS sub-ranges of equal width ((r - rmin) >> sh, monotone in r);
-//     each sub-range (a handful of keys when the keys are spread smoothly) is
-//     insertion-sorted on (radix key, input position), which keeps the sort
-//     stable; only 16-bit input positions move in shared memory and the result
-//     is gathered out once.  When a sub-range holds more than SUB_MAX keys
+//     range [rmin, rmax] found in the same pass.  One counting pass spreads
+//     the keys over up to 2^SUB_BITS sub-ranges of equal width
+//     ((r - rmin) >> sh, monotone in r; a key or two each when the keys are
+//     spread smoothly); 16-bit input positions are scattered by sub-range;
+//     then every key counts the keys of its own sub-range that come before it
+//     in (radix key, input position) order -- which keeps the sort stable --
+//     and is written straight to its output slot.  When a sub-range holds more
+//     than SUB_MAX keys
 //     (clustered keys), the segment instead takes stable LSD passes over only
 //     the radix bits that vary inside it (OR of r ^ r0), through a global
 //     workspace copy, chunk by chunk with warp ranks.
@@ -28,7 +32,11 @@
 namespace ak {
 
 constexpr int SUB_BITS = 12;  // at most 2^SUB_BITS sub-ranges per segment
-constexpr int SUB_MAX = 48;   // largest sub-range the insertion sort takes
+constexpr int SUB_MAX = 48;   // largest sub-range a segment sorts by counting (else LSD passes)
+// sub-ranges per segment about len / 2^AK_SUB_SLACK (at most 2^SUB_BITS)
+#ifndef AK_SUB_SLACK
+#define AK_SUB_SLACK 1
+#endif
 
 struct SplitState {  // zeroed by the caller
   uint32_t nbig;     // big segments (split across CTAs)
@@ -430,7 +438,7 @@ struct SegCta {
     //    keys are spread evenly; counts in the (zero) mask words
     const R span = R(hi - lo);
     const int span_bits = sizeof(R) == 4 ? 32 - __clz(uint32_t(span)) : 64 - __clzll((long long)span);
-    int want = (32 - __clz(uint32_t(len - 1))) - 1;
+    int want = (32 - __clz(uint32_t(len - 1))) - AK_SUB_SLACK;
     want = want < 1 ? 1 : (want > SUB_BITS ? SUB_BITS : want);
     const int sh = span_bits > want ? span_bits - want : 0;
     const int nsub = int(span >> sh) + 1;

@@ -74,20 +74,22 @@ def test_options_out_of_range_are_refused(lib):
         return lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 1 << 20, ak.AK_F64, 0, 0, ctypes.byref(o), ctypes.byref(out))
 
     for good in ({}, {"path": ak.AK_PATH_MERGE}, {"tile_config": 3}, {"tile_config": 4}, {"bucket_bits": 8}, {"bucket_bits": 16},
-                 {"train_steps": -1}, {"debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE | 2}, {"timeout_ns": 5}):
+                 {"train_steps": -1}, {"debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE | 2}, {"timeout_ns": 5},
+                 {"digit_bits": 8}, {"split_caps": -1}, {"split_caps": 1}, {"split_caps": 1024}):
         assert query(**good) == 0, good
     for bad in ({"path": 5}, {"path": -1}, {"tile_config": 5}, {"bucket_bits": 7}, {"bucket_bits": 17},
-                {"train_steps": -2}, {"debug_flags": 4}):
+                {"train_steps": -2}, {"debug_flags": 4}, {"digit_bits": 11}, {"digit_bits": 4},
+                {"split_caps": -2}, {"split_caps": 1025}):
         assert query(**bad) == 1, bad
     o = ak.Options()
-    o.reserved[2] = 1
+    o.reserved[1] = 1
     assert lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 10, ak.AK_U32, 0, 0, ctypes.byref(o), ctypes.byref(out)) == 1
     # malformed options are refused even by the n = 0 no-op of every entry point (no pointer touched)
     assert lib.ak_sort(None, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
     assert lib.ak_sortperm(None, None, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
     assert lib.ak_sort_pairs(None, None, 4, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
     assert lib.ak_sort_segmented(None, None, 0, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 1
-    o.reserved[2] = 0
+    o.reserved[1] = 0
     assert lib.ak_sort(None, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 0
     assert lib.ak_sort_segmented(None, None, 0, 0, ak.AK_U32, 0, None, 0, None, ctypes.byref(o)) == 0
 
@@ -214,6 +216,23 @@ def test_autotune_cache_roundtrip_and_auto_sizing(lib, tmp_path):
     rows = [json.loads(x) for x in out.read_text().splitlines()]
     assert len(rows) == 1 and rows[0]["bucket_bits"] == 9
     lib.ak_autotune_clear()
+    # segmented entries carry the split threshold (op 3, log2 nseg in val_bytes);
+    # thresholds outside -1..1024 are skipped
+    src.write_text(
+        json.dumps({"op": 3, "dtype": ak.AK_U32, "log2n": 28, "val_bytes": 16, "path": ak.AK_PATH_BLOCK,
+                    "tile_config": 0, "ms": 3.5, "bucket_bits": 0, "split_caps": 2}) + "\n" +
+        json.dumps({"op": 3, "dtype": ak.AK_U32, "log2n": 27, "val_bytes": 16, "path": ak.AK_PATH_BLOCK,
+                    "tile_config": 0, "ms": 3.5, "bucket_bits": 0, "split_caps": 5000}) + "\n")
+    ak.ak_autotune_load(str(src))
+    ak.ak_autotune_save(str(out))
+    rows = [json.loads(x) for x in out.read_text().splitlines()]
+    assert len(rows) == 1 and rows[0]["split_caps"] == 2 and rows[0]["op"] == 3
+    lib.ak_autotune_clear()
+    # the segmented tuner's workspace: the sort's workspace plus a copy of the keys
+    got = ctypes.c_size_t(0)
+    assert lib.ak_autotune_segmented_temp_bytes(1 << 20, 100, ak.AK_U32, ctypes.byref(got)) == 0
+    assert got.value >= ak.temp_bytes(ak.AK_OP_SORT_SEGMENTED, 1 << 20, ak.AK_U32, nseg=100) + 4 * (1 << 20)
+    assert lib.ak_autotune_segmented_temp_bytes(1 << 20, 0, ak.AK_U32, ctypes.byref(got)) == 1
 
 
 def test_binding_refuses_host_tensors_and_mismatches(lib):

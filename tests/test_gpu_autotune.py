@@ -48,3 +48,36 @@ def test_autotune_then_auto_call(ak, op):
         assert np.array_equal(vals.cpu().numpy(), p.astype(np.int32))
     assert ak.ak_last_info(temp)["path"] in (best.path, ak.AK_PATH_RADIX)
     ak.ak_autotune_clear()
+
+
+def test_autotune_segmented_picks_a_split_threshold_and_stays_exact(ak):
+    """The segmented tuner times the split thresholds on a lognormal batch,
+    restores the keys, caches its choice; the next default call takes it and
+    every segment is sorted."""
+    ak.ak_autotune_clear()
+    off = synth.lognormal_segments(4096, seed=20)
+    n = int(off[-1])
+    keys = synth.uniform_u32(n, seed=21)
+    t, u = to_dev(keys)
+    o = torch.from_numpy(off).cuda()
+    best = ak.ak_autotune_segmented(t, o, unsigned=u)
+    assert best.split_caps in (1, 2, 4, 8, 16, -1)
+    assert_bits_equal(to_host(t, np.uint32), keys, "inputs restored")
+    ak.ak_sort_segmented(t, o, unsigned=u)
+    torch.cuda.synchronize()
+    seg = np.repeat(np.arange(off.size - 1, dtype=np.uint64), np.diff(off))
+    want = np.sort((seg << np.uint64(32)) | keys.astype(np.uint64)).astype(np.uint32)
+    assert_bits_equal(to_host(t, np.uint32), want, "tuned segmented sort")
+    ak.ak_autotune_clear()
+
+
+@pytest.mark.parametrize("caps", [1, 2, 16, -1])
+def test_every_split_threshold_is_exact(ak, caps):
+    off = synth.lognormal_segments(1024, seed=23, median=8192.0)
+    n = int(off[-1])
+    keys = synth.random_keys(n, np.float32, seed=24, mode="bits")
+    t, u = to_dev(keys)
+    ak.ak_sort_segmented(t, torch.from_numpy(off).cuda(), options={"split_caps": caps}, unsigned=u)
+    torch.cuda.synchronize()
+    want = oracle.sort_segmented(keys, off)
+    assert_bits_equal(to_host(t, np.float32), want, f"split_caps {caps}")
