@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted", "accumulate"],
                     help="c2 (default): the headline line; the others print their own lines")
     ap.add_argument("--segments", type=int, default=65536, help="c4: number of segments")
+    ap.add_argument("--tile-config", type=int, default=0, help="c2: digit-pass tile configuration (0 = default)")
     return ap.parse_args()
 
 
@@ -383,7 +384,7 @@ def run_ours(args):
         pristine = torch.from_numpy(host).to(dev)
         arrays.append({"pristine": pristine, "work": torch.empty_like(pristine), "kd": kd, "w": w})
     perm = torch.empty(n, dtype=torch.int32, device=dev)
-    tb = max(ak.temp_bytes(op, n, kd, options={"path": ak.AK_PATH_RADIX})
+    tb = max(ak.temp_bytes(op, n, kd, options={"path": ak.AK_PATH_RADIX, "tile_config": args.tile_config})
              for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM) for kd in (ak.AK_I64, ak.AK_F32))
     temp = ak.workspace(tb, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -397,11 +398,13 @@ def run_ours(args):
     ev_arr = (ctypes.c_void_p * len(pass_ev))(*[e.cuda_event for e in pass_ev])
     opts = ak.Options()
     opts.path = ak.AK_PATH_RADIX  # the plain radix path: the digit-pass kernel is the roofline's subject
+    opts.tile_config = args.tile_config
     opts.pass_events = ctypes.cast(ev_arr, ctypes.c_void_p)
     calls = [("sortperm", 0), ("sort", 0), ("sortperm", 1), ("sort", 1)]
 
     radix_opts = ak.Options()
     radix_opts.path = ak.AK_PATH_RADIX
+    radix_opts.tile_config = args.tile_config
 
     def call(op, a, with_events):
         o = ctypes.byref(opts) if with_events else ctypes.byref(radix_opts)

@@ -10,10 +10,13 @@
 // HBM bound: n * w bytes read and n * w written.  Design for GB300:
 //  * persistent CTAs (resident count) take 32 KB tiles from an atomic counter,
 //    in increasing order, so a tile only ever waits on tiles already held by
-//    running CTAs -- forward progress needs no co-residency;
-//  * each thread loads 64 contiguous bytes (four 16-byte vector loads when the
-//    tile is whole and the pointers 16-byte aligned) and scans them in
-//    registers; the CTA scans the 512 thread totals with warp shuffles;
+//    running CTAs -- forward progress needs no co-residency; a CTA claims its
+//    next tile as soon as the current one's aggregate is published and loads
+//    it into registers while warp 0 looks back;
+//  * each thread loads 64 contiguous bytes (32 for 16-bit keys: four or two
+//    16-byte vector loads when the tile is whole and the pointers 16-byte
+//    aligned) and scans them in registers; the CTA scans the 512 thread
+//    totals with warp shuffles;
 //  * the tile publishes its aggregate, then warp 0 looks back over up to 32
 //    predecessors at a time, stops at the nearest inclusive prefix and
 //    publishes its own inclusive prefix;
@@ -40,8 +43,10 @@
 namespace ak {
 
 constexpr int SCAN_BLOCK = 512;
-constexpr int SCAN_VEC_PER_THREAD = 4;  // 16-byte vectors: 64 bytes per thread
-constexpr int SCAN_TILE_BYTES = SCAN_BLOCK * SCAN_VEC_PER_THREAD * 16;
+// 16-byte vectors per thread: 64 bytes (32 bytes for 16-bit keys, whose values
+// each take a register)
+constexpr int scan_vecs(int key_bytes) { return key_bytes == 2 ? 2 : 4; }
+constexpr int scan_tile(int key_bytes) { return SCAN_BLOCK * scan_vecs(key_bytes) * 16 / key_bytes; }
 constexpr uint32_t SCAN_FLAG_AGG = 1, SCAN_FLAG_INC = 2;
 
 // ----------------------------------------------------------------- operators
@@ -231,33 +236,29 @@ template <typename T, int OP>
 __global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_kernel(ScanArgs a) {
   using Op = ScanOp<T, OP>;
   constexpr int PER_VEC = 16 / int(sizeof(T));
-  constexpr int ITEMS = SCAN_VEC_PER_THREAD * PER_VEC;
+  constexpr int VECS = scan_vecs(int(sizeof(T)));
+  constexpr int ITEMS = VECS * PER_VEC;
   constexpr int TILE = SCAN_BLOCK * ITEMS;
   __shared__ T s_warp[SCAN_BLOCK / 32];
   __shared__ T s_prefix;
   __shared__ int64_t s_tile;
   const int tid = threadIdx.x;
   // x and out may be the same array (in place): each thread reads its own run
-  // before the CTA barriers and writes it after them
+  // before the CTA barriers and writes it after them; the next tile's run is
+  // read before this tile's run is written, and the two never overlap
   const T *x = static_cast<const T *>(a.x);
   T *out = static_cast<T *>(a.out);
   const T init = from_bits64<T>(a.init_bits);
-  for (;;) {
-    if (tid == 0) s_tile = int64_t(atomicAdd(&a.hdr->tile_counter[0], 1u)) + (a.debug_skip ? 1 : 0);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= a.num_tiles) break;
+  // this thread's run of a tile into registers (identity past the end of the array)
+  auto load_run = [&](int64_t tile, T (&v)[ITEMS]) {
     const int64_t base = tile * TILE;
     const int64_t tile_n = (a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE);
-    const int64_t first = base + int64_t(tid) * ITEMS;  // this thread's run of ITEMS
+    const int64_t first = base + int64_t(tid) * ITEMS;
     const int64_t end = base + tile_n;
-    const bool vec = a.aligned16 && tile_n == TILE;
-    // 1. load the run (identity past the end of the array)
-    T v[ITEMS];
-    if (vec) {
+    if (a.aligned16 && tile_n == TILE) {
       const uint4 *src = reinterpret_cast<const uint4 *>(x + first);
 #pragma unroll
-      for (int r = 0; r < SCAN_VEC_PER_THREAD; ++r) {
+      for (int r = 0; r < VECS; ++r) {
         const uint4 q = src[r];
 #pragma unroll
         for (int k = 0; k < PER_VEC; ++k) v[r * PER_VEC + k] = reinterpret_cast<const T *>(&q)[k];
@@ -266,21 +267,47 @@ __global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_kernel(ScanArgs a) {
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) v[k] = first + k < end ? x[first + k] : Op::identity();
     }
-    // 2. running prefix of the run, then the CTA scan of the run totals
+  };
+  if (tid == 0) s_tile = int64_t(atomicAdd(&a.hdr->tile_counter[0], 1u)) + (a.debug_skip ? 1 : 0);
+  __syncthreads();
+  int64_t tile = s_tile;
+  T v[ITEMS];
+  if (tile < a.num_tiles) load_run(tile, v);
+  while (tile < a.num_tiles) {
+    const int64_t base = tile * TILE;
+    const int64_t tile_n = (a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE);
+    const int64_t first = base + int64_t(tid) * ITEMS;  // this thread's run of ITEMS
+    const int64_t end = base + tile_n;
+    const bool vec = a.aligned16 && tile_n == TILE;
+    // 1. running prefix of the run, then the CTA scan of the run totals
 #pragma unroll
     for (int k = 1; k < ITEMS; ++k) v[k] = Op::apply(v[k - 1], v[k]);
     T agg;
     const T run_ex = cta_exclusive<T, OP>(v[ITEMS - 1], s_warp, &agg);
-    // 3. publish the aggregate, look back, publish the inclusive prefix
+    // 2. publish the aggregate and claim the next tile (its loads then fly
+    //    while warp 0 looks back)
+    if (tid == 0) {
+      if (tile > 0) {
+        st_relaxed(&a.agg_bits[tile], to_bits64(agg));
+        st_release_flag(&a.flags[tile], SCAN_FLAG_AGG);
+      }
+      s_tile = int64_t(atomicAdd(&a.hdr->tile_counter[0], 1u)) + (a.debug_skip ? 1 : 0);
+    }
+    __syncthreads();
+    const int64_t next = s_tile;
+    // whole, aligned next tile: its run is loaded now as raw 16-byte vectors
+    // (unpacked after this tile is written); otherwise it is loaded then
+    uint4 nq[VECS];
+    const bool next_vec = next < a.num_tiles && a.aligned16 && (a.n - next * TILE) >= int64_t(TILE);
+    if (next_vec) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(x + next * TILE + int64_t(tid) * ITEMS);
+#pragma unroll
+      for (int r = 0; r < VECS; ++r) nq[r] = src[r];
+    }
+    // 3. look back, publish the inclusive prefix
     if (tid < 32) {
       T excl = Op::identity();
-      if (tile > 0) {
-        if (tid == 0) {
-          st_relaxed(&a.agg_bits[tile], to_bits64(agg));
-          st_release_flag(&a.flags[tile], SCAN_FLAG_AGG);
-        }
-        excl = scan_look_back<T, OP>(a, tile);
-      }
+      if (tile > 0) excl = scan_look_back<T, OP>(a, tile);
       if (tid == 0) {
         st_relaxed(&a.inc_bits[tile], to_bits64(Op::apply(excl, agg)));
         st_release_flag(&a.flags[tile], SCAN_FLAG_INC);
@@ -302,7 +329,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_kernel(ScanArgs a) {
     if (vec) {
       uint4 *dst = reinterpret_cast<uint4 *>(out + first);
 #pragma unroll
-      for (int r = 0; r < SCAN_VEC_PER_THREAD; ++r) {
+      for (int r = 0; r < VECS; ++r) {
         uint4 q;
 #pragma unroll
         for (int k = 0; k < PER_VEC; ++k) reinterpret_cast<T *>(&q)[k] = o[r * PER_VEC + k];
@@ -313,6 +340,15 @@ __global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_kernel(ScanArgs a) {
       for (int k = 0; k < ITEMS; ++k)
         if (first + k < end) out[first + k] = o[k];
     }
+    if (next_vec) {
+#pragma unroll
+      for (int r = 0; r < VECS; ++r)
+#pragma unroll
+        for (int k = 0; k < PER_VEC; ++k) v[r * PER_VEC + k] = reinterpret_cast<const T *>(&nq[r])[k];
+    } else if (next < a.num_tiles) {
+      load_run(next, v);
+    }
+    tile = next;
     __syncthreads();  // s_tile, s_prefix and s_warp are rewritten by the next tile
   }
 }
@@ -331,7 +367,7 @@ struct ScanLayout {
 
 ScanLayout scan_layout(int64_t n, int key_bytes) {
   ScanLayout L;
-  const int64_t tile = SCAN_TILE_BYTES / key_bytes;
+  const int64_t tile = scan_tile(key_bytes);
   L.tiles = (n + tile - 1) / tile;
   size_t off = scan_align256(sizeof(DevHeader));
   L.flags = off;

@@ -89,7 +89,8 @@ def test_parity_all_dtypes(ak, dtype, op, inclusive):
 def test_sizes_alignment_and_in_place(ak, dtype):
     """n = 1, a run, a tile -1/+0/+1, 40 tiles + 3; pointers off 16-byte
     alignment (scalar loads); the in-place form."""
-    tile = TILE_BYTES // np.dtype(dtype).itemsize
+    w = np.dtype(dtype).itemsize
+    tile = (TILE_BYTES // 2 if w == 2 else TILE_BYTES) // w  # 16-bit keys: 32-byte runs per thread
     for n in (1, 2, 31, tile - 1, tile, tile + 1, 40 * tile + 3):
         x = _keys(dtype, n, 112 + n, "add")
         for offset in (0, 1):
