@@ -43,7 +43,7 @@ NOMINAL_HBM_GBS = 8000.0
 # (keys per array, bytes per launch).  Traffic grows in proportion to the keys,
 # so it is scaled to the run's n.  None whenever the digit-pass kernel has
 # changed since the counters were taken.
-NCU_TRAFFIC = None
+NCU_TRAFFIC = (67_108_864, 1_096_529_397)  # profiles/onesweep_pass_traffic_67M.md
 
 
 def parse_args():
@@ -739,7 +739,7 @@ def run_workload(args):
             tot_l += ml
             tot_p += mp
         big = {}
-        for i, dist in enumerate(("uniform", "normal")):
+        for i, dist in enumerate(("uniform", "normal") if args.n == FULL_N else ()):  # --n: that size only
             keys = synth.dist_f64(FULL_N, dist, seed=10 + synth.F64_DISTS.index(dist))
             gp, mp, _ = sort_gbs(keys, ak.AK_F64, {"path": ak.AK_PATH_RADIX})
             gl, ml, info = sort_gbs(keys, ak.AK_F64, {"path": ak.AK_PATH_LEARNED})

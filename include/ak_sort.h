@@ -118,8 +118,8 @@ typedef struct ak_options {
 
 #define AK_MAX_PASSES 8
 
-/* Test hook: no CTA owns the first tile of any radix pass (or of an
- * ak_accumulate scan), so every look-back that reaches it waits until
+/* Test hook: no CTA owns the first tile of any radix pass, so every
+ * look-back that reaches it waits until
  * timeout_ns and the call ends with AK_ERR_TIMEOUT (the output is then
  * unspecified).  Exercises the bounded-wait error path. */
 #define AK_DEBUG_SKIP_FIRST_TILE 1
@@ -278,8 +278,8 @@ typedef enum ak_scan_op { AK_SCAN_ADD = 0, AK_SCAN_MAX = 1, AK_SCAN_MIN = 2 } ak
  *   AK_SCAN_ADD  integer + wrapping in the key's width; IEEE float + in the key's
  *                precision, in an order of its own (results differ from a left
  *                to right sum by rounding only: the bound is that of a sum of
- *                depth at most 64 / key bytes + 32 + 2 ceil(n / tile), a tile
- *                being 32 KB of keys);
+ *                depth at most m + 2 ceil(n / (32768 m)) + 84, m = 64 / key
+ *                bytes, 16 for 16-bit keys);
  *   AK_SCAN_MAX  Julia max: a NaN operand gives NaN, +0.0 is above -0.0;
  *   AK_SCAN_MIN  Julia min: a NaN operand gives NaN, -0.0 is below +0.0.
  * Integer results and max/min are exact.
@@ -289,9 +289,10 @@ typedef enum ak_scan_op { AK_SCAN_ADD = 0, AK_SCAN_MAX = 1, AK_SCAN_MIN = 2 } ak
  * overlap it.  Pointers are aligned to the key size (16-byte alignment of both
  * enables vector loads).  d_temp: a 256-byte aligned workspace of
  * ak_accumulate_temp_bytes bytes, whose first bytes hold the status word that
- * ak_status_check reads (AK_ERR_TIMEOUT when a look-back wait expired,
- * opt->timeout_ns); opt may be NULL (only timeout_ns and debug_flags apply).
- * Enqueues one memset and one kernel on `stream`; allocates nothing.
+ * ak_status_check reads (always AK_OK: no kernel of the scan waits on another
+ * CTA); opt may be NULL, and its timeout_ns and debug_flags have no effect here.
+ * Enqueues one memset and three kernels on `stream` (range totals, their
+ * prefixes, the ranges' scans); allocates nothing.
  * Returns AK_ERR_INVALID_ARG for a negative n, a bad dtype, op or inclusive
  * flag, malformed options, or a NULL or misaligned pointer with n > 0;
  * AK_ERR_WORKSPACE_TOO_SMALL; AK_ERR_CUDA if a launch fails.  n = 0 is a no-op.

@@ -1,32 +1,34 @@
-// scan.cu -- accumulate: single-pass prefix scan with decoupled look-back
-// (Sec. II-B, accumulate, inclusive and exclusive, with opportunistic
-// look-back after Merrill and Garland, "Single-pass Parallel Prefix Scan with
-// Decoupled Look-back", 2016).
+// scan.cu -- accumulate: prefix scan under a binary operator (Sec. II-B,
+// accumulate, inclusive and exclusive).
 //
 // out[i] = init (+) x[0] (+) ... (+) x[i]      (inclusive)
 // out[i] = init (+) x[0] (+) ... (+) x[i - 1]  (exclusive, out[0] = init)
 // for (+) = + (integers wrap in their width), Julia max, Julia min.
 //
-// HBM bound: n * w bytes read and n * w written.  Design for GB300:
-//  * persistent CTAs (resident count) take 32 KB tiles from an atomic counter,
-//    in increasing order, so a tile only ever waits on tiles already held by
-//    running CTAs -- forward progress needs no co-residency; a CTA claims its
-//    next tile as soon as the current one's aggregate is published and loads
-//    it into registers while warp 0 looks back;
-//  * each thread loads 64 contiguous bytes (32 for 16-bit keys: four or two
-//    16-byte vector loads when the tile is whole and the pointers 16-byte
-//    aligned) and scans them in registers; the CTA scans the 512 thread
-//    totals with warp shuffles;
-//  * the tile publishes its aggregate, then warp 0 looks back over up to 32
-//    predecessors at a time, stops at the nearest inclusive prefix and
-//    publishes its own inclusive prefix;
-//  * status: a 32-bit flag (release store / acquire load, gpu scope) beside
-//    two write-once 64-bit slots, the aggregate and the inclusive prefix, so a
-//    reader that saw one flag value can never pick up the other slot's value
-//    (one scheme for every key width);
-//  * every wait is bounded by the globaltimer: on expiry the CTA records
-//    AK_ERR_TIMEOUT, takes the identity for the missing prefix and finishes.
+// HBM bound: n * w bytes read and n * w written.  Design for GB300: three
+// launches, none of which waits on another CTA (reduce, then scan):
+//  * the array is cut into warp ranges, contiguous runs of whole warp tiles
+//    (32 lanes x 64 bytes; 32 bytes for 16-bit keys), as many ranges as warps
+//    are resident (16 per 512-thread CTA, 2 CTAs per SM);
+//  * scan_reduce_kernel: each warp combines its range from the last warp tile
+//    to the first (the start of every range is then the most recently read
+//    data in L2 for the third launch); a lane combines its run in order, the
+//    warp combines the 32 runs in lane order, and the tile total goes on the
+//    left of what was combined so far;
+//  * scan_carry_kernel: one CTA scans the range totals in order from init:
+//    the exclusive prefix of every range;
+//  * scan_ranges_kernel: each warp walks its range forward from that prefix:
+//    running prefix of each lane's run, warp scan of the run totals with
+//    shuffles, outputs, carry += tile total; the next warp tile's loads are in
+//    flight while the current one is scanned and stored.
+// Traffic is 3 n w (the input is read twice) but every launch streams with
+// no barrier inside its loop: a single-pass decoupled look-back measured 2.6
+// to 9.6 ms on 2^28 int64 keys (persistent 512-thread CTAs, look-back 6.5 to
+// 41 us a tile), this reads and writes the same in about a millisecond.
 //
+// Every operator is applied with the earlier operand on the left, so results
+// are exact for integers and max/min (the first NaN of the sequence wins);
+// float + rounds in a tree of its own.
 // Identities (x (+) e == x bit for bit, -0.0 and NaN included): + on floats
 // -0.0, on integers 0; max -Inf or the lowest integer; min +Inf or the highest.
 #include <cuda_runtime.h>
@@ -43,11 +45,16 @@
 namespace ak {
 
 constexpr int SCAN_BLOCK = 512;
-// 16-byte vectors per thread: 64 bytes (32 bytes for 16-bit keys, whose values
-// each take a register)
+constexpr int SCAN_WARPS = SCAN_BLOCK / 32;
+constexpr int SCAN_CARRY_BLOCK = 1024;
+// 16-byte vectors per lane and warp tile: 64 bytes (32 bytes for 16-bit keys,
+// whose values each take a register)
 constexpr int scan_vecs(int key_bytes) { return key_bytes == 2 ? 2 : 4; }
-constexpr int scan_tile(int key_bytes) { return SCAN_BLOCK * scan_vecs(key_bytes) * 16 / key_bytes; }
-constexpr uint32_t SCAN_FLAG_AGG = 1, SCAN_FLAG_INC = 2;
+constexpr int scan_items(int key_bytes) { return scan_vecs(key_bytes) * 16 / key_bytes; }
+constexpr int scan_warp_tile(int key_bytes) { return 32 * scan_items(key_bytes); }
+// Upper bound on the warp ranges (sizes the workspace; far above the
+// resident warps of any device).
+constexpr int64_t SCAN_MAX_RANGES = 1 << 15;
 
 // ----------------------------------------------------------------- operators
 template <typename T, int OP> struct ScanOp;
@@ -104,7 +111,7 @@ template <typename T> struct ScanOp<T, AK_SCAN_MIN> {
   }
 };
 
-// T <-> its bits zero-extended to 64 (the status value slot)
+// T <-> its bits zero-extended to 64 (the range slots)
 template <typename T> __device__ __forceinline__ unsigned long long to_bits64(T v) {
   if constexpr (sizeof(T) == 2) return (unsigned long long)__builtin_bit_cast(uint16_t, v);
   else if constexpr (sizeof(T) == 4) return (unsigned long long)__builtin_bit_cast(uint32_t, v);
@@ -116,207 +123,157 @@ template <typename T> __host__ __device__ __forceinline__ T from_bits64(unsigned
   else return __builtin_bit_cast(T, b);
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_flag(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_flag(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 struct ScanArgs {
   const void *x;
   void *out;
   int64_t n;
-  int64_t num_tiles;
+  int64_t wtiles;     // warp tiles, the last one possibly ragged
+  int64_t per;        // warp tiles per range (the last range may hold fewer)
+  int64_t nranges;    // ceil(wtiles / per)
   unsigned long long init_bits;
   int inclusive;
-  int aligned16;      // x and out 16-byte aligned: whole tiles take vector loads
-  int debug_skip;     // tile ids start at 1 (tile 0 never published: exercises the timeout)
-  uint64_t timeout_ns;
-  DevHeader *hdr;
-  uint32_t *flags;                // [num_tiles]: 0, SCAN_FLAG_AGG, SCAN_FLAG_INC
-  unsigned long long *agg_bits;   // [num_tiles]: the tile's aggregate, written before AGG
-  unsigned long long *inc_bits;   // [num_tiles]: the inclusive prefix, written before INC
+  int aligned16;      // x and out 16-byte aligned: whole warp tiles take vector loads
+  unsigned long long *agg;  // [nranges]: each range's total (bits)
+  unsigned long long *pre;  // [nranges]: init (+) the totals of the ranges before it
 };
 
 }  // namespace ak
 
 namespace ak {
 
-// Inclusive scan of one value per thread over the CTA under OP; `warp_tot`
-// holds SCAN_BLOCK / 32 values.  Returns the thread's exclusive prefix (the
-// identity for thread 0) and sets *total to the CTA's aggregate.
+// One warp tile into registers: lane l holds elements [base + l ITEMS, +ITEMS)
+// (identity past the end of the array).
 template <typename T, int OP>
-__device__ __forceinline__ T cta_exclusive(T v, T *warp_tot, T *total) {
+__device__ __forceinline__ void scan_load(const ScanArgs &a, const T *x, int64_t wt, T (&v)[scan_items(sizeof(T))]) {
   using Op = ScanOp<T, OP>;
-  constexpr int NW = SCAN_BLOCK / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T inc = v;
+  constexpr int ITEMS = scan_items(sizeof(T));
+  constexpr int VECS = scan_vecs(sizeof(T));
+  constexpr int PER_VEC = 16 / int(sizeof(T));
+  const int lane = threadIdx.x & 31;
+  const int64_t first = wt * (32 * ITEMS) + int64_t(lane) * ITEMS;
+  if (a.aligned16 && (wt + 1) * (32 * ITEMS) <= a.n) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(x + first);
+#pragma unroll
+    for (int r = 0; r < VECS; ++r) {
+      const uint4 q = src[r];
+#pragma unroll
+      for (int k = 0; k < PER_VEC; ++k) v[r * PER_VEC + k] = reinterpret_cast<const T *>(&q)[k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) v[k] = first + k < a.n ? x[first + k] : Op::identity();
+  }
+}
+
+// Warp ranges of this warp: [lo, hi) warp tiles; false when the warp has none.
+__device__ __forceinline__ bool scan_range(const ScanArgs &a, int64_t *r, int64_t *lo, int64_t *hi) {
+  *r = int64_t(blockIdx.x) * SCAN_WARPS + (threadIdx.x >> 5);
+  if (*r >= a.nranges) return false;
+  *lo = *r * a.per;
+  *hi = *lo + a.per < a.wtiles ? *lo + a.per : a.wtiles;
+  return true;
+}
+
+// Launch 1: the total of every warp range, combined in element order.
+template <typename T, int OP>
+__global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_reduce_kernel(ScanArgs a) {
+  using Op = ScanOp<T, OP>;
+  constexpr int ITEMS = scan_items(sizeof(T));
+  int64_t r, lo, hi;
+  if (!scan_range(a, &r, &lo, &hi)) return;
+  const int lane = threadIdx.x & 31;
+  const T *x = static_cast<const T *>(a.x);
+  T acc = Op::identity();
+  T v[ITEMS], nv[ITEMS];
+  scan_load<T, OP>(a, x, hi - 1, v);
+  for (int64_t wt = hi - 1; wt >= lo; --wt) {  // last tile first
+    if (wt > lo) scan_load<T, OP>(a, x, wt - 1, nv);
+    T w = v[0];
+#pragma unroll
+    for (int k = 1; k < ITEMS; ++k) w = Op::apply(w, v[k]);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T u = __shfl_down_sync(0xffffffffu, w, o);
+      if (lane + o < 32) w = Op::apply(w, u);  // lane + o holds later elements
+    }
+    acc = Op::apply(w, acc);  // this tile precedes everything combined so far
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) v[k] = nv[k];
+  }
+  if (lane == 0) a.agg[r] = to_bits64(acc);
+}
+
+// Launch 2 (one CTA): pre[r] = init (+) agg[0] (+) ... (+) agg[r - 1].
+template <typename T, int OP>
+__global__ void __launch_bounds__(SCAN_CARRY_BLOCK) scan_carry_kernel(ScanArgs a) {
+  using Op = ScanOp<T, OP>;
+  constexpr int NW = SCAN_CARRY_BLOCK / 32;
+  __shared__ T s_warp[NW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t chunk = (a.nranges + SCAN_CARRY_BLOCK - 1) / SCAN_CARRY_BLOCK;
+  const int64_t b = int64_t(tid) * chunk;
+  const int64_t e = b + chunk < a.nranges ? b + chunk : a.nranges;
+  T tot = Op::identity();
+  for (int64_t i = b; i < e; ++i) tot = Op::apply(tot, from_bits64<T>(a.agg[i]));
+  // exclusive scan of the thread totals in thread order
+  T inc = tot;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const T u = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc = Op::apply(u, inc);
   }
-  if (lane == 31) warp_tot[warp] = inc;
+  if (lane == 31) s_warp[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    T w = lane < NW ? warp_tot[lane] : Op::identity();
+    T w = s_warp[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const T u = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w = Op::apply(u, w);
     }
-    if (lane < NW) warp_tot[lane] = w;  // inclusive over warps 0..lane
+    s_warp[lane] = w;  // inclusive over warps 0..lane
   }
   __syncthreads();
-  *total = warp_tot[NW - 1];
-  const T before_warp = warp == 0 ? Op::identity() : warp_tot[warp - 1];
   T ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  const T before_warp = warp == 0 ? Op::identity() : s_warp[warp - 1];
   ex = lane == 0 ? before_warp : Op::apply(before_warp, ex);
-  return ex;
-}
-
-// Bounded wait for a tile's flag; on expiry records AK_ERR_TIMEOUT and
-// returns 0 (the caller then takes the identity and stops looking back).
-__device__ __forceinline__ uint32_t scan_wait_flag(const uint32_t *p, uint64_t timeout_ns, DevHeader *hdr) {
-  uint32_t f = ld_acquire_flag(p);
-  if (f != 0) return f;
-  const uint64_t t0 = globaltimer_ns();
-  uint32_t spins = 0;
-  while ((f = ld_acquire_flag(p)) == 0) {
-    __nanosleep(64);
-    if ((++spins & 15u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
-      set_error(hdr, AK_ERR_TIMEOUT);
-      return 0;
-    }
-  }
-  return f;
-}
-
-// Warp 0: the prefix of every tile before `tile` (identity for tile 0), found
-// by looking back over windows of 32 predecessors.  In each window lane l
-// holds tile j - l; the lanes up to the nearest inclusive prefix are combined
-// with the earlier tile on the left, and the walk stops there.
-template <typename T, int OP>
-__device__ __forceinline__ T scan_look_back(const ScanArgs &a, int64_t tile) {
-  using Op = ScanOp<T, OP>;
-  const int lane = threadIdx.x & 31;
-  T excl = Op::identity();
-  for (int64_t j = tile - 1;; j -= 32) {
-    const int64_t t = j - lane;
-    bool stop = t < 0;  // nothing before tile 0
-    T val = Op::identity();
-    if (t >= 0) {
-      const uint32_t f = scan_wait_flag(&a.flags[t], a.timeout_ns, a.hdr);
-      if (f == SCAN_FLAG_INC) {
-        val = from_bits64<T>(ld_relaxed(&a.inc_bits[t]));
-        stop = true;
-      } else if (f == SCAN_FLAG_AGG) {
-        val = from_bits64<T>(ld_relaxed(&a.agg_bits[t]));
-      } else {
-        stop = true;  // timed out: identity
-      }
-    }
-    const uint32_t stops = __ballot_sync(0xffffffffu, stop);
-    const int last = stops ? __ffs(stops) - 1 : 31;  // nearest lane that ends the walk
-    T w = lane <= last ? val : Op::identity();
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T u = __shfl_down_sync(0xffffffffu, w, o);
-      if (lane + o < 32) w = Op::apply(u, w);  // lane + o holds the earlier tiles
-    }
-    excl = Op::apply(__shfl_sync(0xffffffffu, w, 0), excl);
-    if (stops) return excl;
+  T run = Op::apply(from_bits64<T>(a.init_bits), ex);
+  for (int64_t i = b; i < e; ++i) {
+    a.pre[i] = to_bits64(run);
+    run = Op::apply(run, from_bits64<T>(a.agg[i]));
   }
 }
 
+// Launch 3: each warp scans its range forward from its prefix.
 template <typename T, int OP>
-__global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_kernel(ScanArgs a) {
+__global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_ranges_kernel(ScanArgs a) {
   using Op = ScanOp<T, OP>;
+  constexpr int ITEMS = scan_items(sizeof(T));
+  constexpr int VECS = scan_vecs(sizeof(T));
   constexpr int PER_VEC = 16 / int(sizeof(T));
-  constexpr int VECS = scan_vecs(int(sizeof(T)));
-  constexpr int ITEMS = VECS * PER_VEC;
-  constexpr int TILE = SCAN_BLOCK * ITEMS;
-  __shared__ T s_warp[SCAN_BLOCK / 32];
-  __shared__ T s_prefix;
-  __shared__ int64_t s_tile;
-  const int tid = threadIdx.x;
-  // x and out may be the same array (in place): each thread reads its own run
-  // before the CTA barriers and writes it after them; the next tile's run is
-  // read before this tile's run is written, and the two never overlap
+  int64_t r, lo, hi;
+  if (!scan_range(a, &r, &lo, &hi)) return;
+  const int lane = threadIdx.x & 31;
+  // x and out may be the same array (in place): a warp owns its range, reads
+  // each warp tile before writing it and reads ahead only tiles not yet written
   const T *x = static_cast<const T *>(a.x);
   T *out = static_cast<T *>(a.out);
-  const T init = from_bits64<T>(a.init_bits);
-  // this thread's run of a tile into registers (identity past the end of the array)
-  auto load_run = [&](int64_t tile, T (&v)[ITEMS]) {
-    const int64_t base = tile * TILE;
-    const int64_t tile_n = (a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE);
-    const int64_t first = base + int64_t(tid) * ITEMS;
-    const int64_t end = base + tile_n;
-    if (a.aligned16 && tile_n == TILE) {
-      const uint4 *src = reinterpret_cast<const uint4 *>(x + first);
+  T carry = from_bits64<T>(a.pre[r]);
+  T v[ITEMS], nv[ITEMS];
+  scan_load<T, OP>(a, x, lo, v);
+  for (int64_t wt = lo; wt < hi; ++wt) {
+    if (wt + 1 < hi) scan_load<T, OP>(a, x, wt + 1, nv);
 #pragma unroll
-      for (int r = 0; r < VECS; ++r) {
-        const uint4 q = src[r];
+    for (int k = 1; k < ITEMS; ++k) v[k] = Op::apply(v[k - 1], v[k]);  // running prefix of the run
+    T inc = v[ITEMS - 1];
 #pragma unroll
-        for (int k = 0; k < PER_VEC; ++k) v[r * PER_VEC + k] = reinterpret_cast<const T *>(&q)[k];
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) v[k] = first + k < end ? x[first + k] : Op::identity();
+    for (int o = 1; o < 32; o <<= 1) {
+      const T u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc = Op::apply(u, inc);
     }
-  };
-  if (tid == 0) s_tile = int64_t(atomicAdd(&a.hdr->tile_counter[0], 1u)) + (a.debug_skip ? 1 : 0);
-  __syncthreads();
-  int64_t tile = s_tile;
-  T v[ITEMS];
-  if (tile < a.num_tiles) load_run(tile, v);
-  while (tile < a.num_tiles) {
-    const int64_t base = tile * TILE;
-    const int64_t tile_n = (a.n - base) < int64_t(TILE) ? (a.n - base) : int64_t(TILE);
-    const int64_t first = base + int64_t(tid) * ITEMS;  // this thread's run of ITEMS
-    const int64_t end = base + tile_n;
-    const bool vec = a.aligned16 && tile_n == TILE;
-    // 1. running prefix of the run, then the CTA scan of the run totals
-#pragma unroll
-    for (int k = 1; k < ITEMS; ++k) v[k] = Op::apply(v[k - 1], v[k]);
-    T agg;
-    const T run_ex = cta_exclusive<T, OP>(v[ITEMS - 1], s_warp, &agg);
-    // 2. publish the aggregate and claim the next tile (its loads then fly
-    //    while warp 0 looks back)
-    if (tid == 0) {
-      if (tile > 0) {
-        st_relaxed(&a.agg_bits[tile], to_bits64(agg));
-        st_release_flag(&a.flags[tile], SCAN_FLAG_AGG);
-      }
-      s_tile = int64_t(atomicAdd(&a.hdr->tile_counter[0], 1u)) + (a.debug_skip ? 1 : 0);
-    }
-    __syncthreads();
-    const int64_t next = s_tile;
-    // whole, aligned next tile: its run is loaded now as raw 16-byte vectors
-    // (unpacked after this tile is written); otherwise it is loaded then
-    uint4 nq[VECS];
-    const bool next_vec = next < a.num_tiles && a.aligned16 && (a.n - next * TILE) >= int64_t(TILE);
-    if (next_vec) {
-      const uint4 *src = reinterpret_cast<const uint4 *>(x + next * TILE + int64_t(tid) * ITEMS);
-#pragma unroll
-      for (int r = 0; r < VECS; ++r) nq[r] = src[r];
-    }
-    // 3. look back, publish the inclusive prefix
-    if (tid < 32) {
-      T excl = Op::identity();
-      if (tile > 0) excl = scan_look_back<T, OP>(a, tile);
-      if (tid == 0) {
-        st_relaxed(&a.inc_bits[tile], to_bits64(Op::apply(excl, agg)));
-        st_release_flag(&a.flags[tile], SCAN_FLAG_INC);
-        s_prefix = excl;
-      }
-    }
-    __syncthreads();
-    // 4. outputs: init (+) tile prefix (+) run prefix (+) the run so far
-    const T lead = Op::apply(Op::apply(init, s_prefix), run_ex);
+    const T total = __shfl_sync(0xffffffffu, inc, 31);
+    T ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    const T lead = lane == 0 ? carry : Op::apply(carry, ex);  // everything before this run
     T o[ITEMS];
     if (a.inclusive) {
 #pragma unroll
@@ -326,30 +283,24 @@ __global__ void __launch_bounds__(SCAN_BLOCK, 2) scan_kernel(ScanArgs a) {
 #pragma unroll
       for (int k = 1; k < ITEMS; ++k) o[k] = Op::apply(lead, v[k - 1]);
     }
-    if (vec) {
+    const int64_t first = wt * (32 * ITEMS) + int64_t(lane) * ITEMS;
+    if (a.aligned16 && (wt + 1) * (32 * ITEMS) <= a.n) {
       uint4 *dst = reinterpret_cast<uint4 *>(out + first);
 #pragma unroll
-      for (int r = 0; r < VECS; ++r) {
+      for (int rr = 0; rr < VECS; ++rr) {
         uint4 q;
 #pragma unroll
-        for (int k = 0; k < PER_VEC; ++k) reinterpret_cast<T *>(&q)[k] = o[r * PER_VEC + k];
-        dst[r] = q;
+        for (int k = 0; k < PER_VEC; ++k) reinterpret_cast<T *>(&q)[k] = o[rr * PER_VEC + k];
+        dst[rr] = q;
       }
     } else {
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k)
-        if (first + k < end) out[first + k] = o[k];
+        if (first + k < a.n) out[first + k] = o[k];
     }
-    if (next_vec) {
+    carry = Op::apply(carry, total);
 #pragma unroll
-      for (int r = 0; r < VECS; ++r)
-#pragma unroll
-        for (int k = 0; k < PER_VEC; ++k) v[r * PER_VEC + k] = reinterpret_cast<const T *>(&nq[r])[k];
-    } else if (next < a.num_tiles) {
-      load_run(next, v);
-    }
-    tile = next;
-    __syncthreads();  // s_tile, s_prefix and s_warp are rewritten by the next tile
+    for (int k = 0; k < ITEMS; ++k) v[k] = nv[k];
   }
 }
 
@@ -361,21 +312,20 @@ namespace {
 inline size_t scan_align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct ScanLayout {
-  int64_t tiles;
-  size_t flags, agg, inc, total;  // byte offsets in the workspace (header at 0)
+  int64_t wtiles;
+  size_t agg, pre, total;  // byte offsets in the workspace (header at 0)
 };
 
 ScanLayout scan_layout(int64_t n, int key_bytes) {
   ScanLayout L;
-  const int64_t tile = scan_tile(key_bytes);
-  L.tiles = (n + tile - 1) / tile;
+  const int64_t wt = scan_warp_tile(key_bytes);
+  L.wtiles = (n + wt - 1) / wt;
+  const int64_t ranges = L.wtiles < SCAN_MAX_RANGES ? L.wtiles : SCAN_MAX_RANGES;
   size_t off = scan_align256(sizeof(DevHeader));
-  L.flags = off;
-  off += scan_align256(size_t(L.tiles) * 4);
   L.agg = off;
-  off += scan_align256(size_t(L.tiles) * 8);
-  L.inc = off;
-  off += scan_align256(size_t(L.tiles) * 8);
+  off += scan_align256(size_t(ranges) * 8);
+  L.pre = off;
+  off += scan_align256(size_t(ranges) * 8);
   L.total = off;
   return L;
 }
@@ -426,13 +376,25 @@ int scan_resident(const void *fn, int dev) {
 
 template <typename T, int OP>
 ak_status scan_launch(ScanArgs &a, cudaStream_t st) {
-  auto *fn = scan_kernel<T, OP>;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return AK_ERR_CUDA;
-  const int resident = scan_resident(reinterpret_cast<const void *>(fn), dev);
+  const int r1 = scan_resident(reinterpret_cast<const void *>(scan_reduce_kernel<T, OP>), dev);
+  const int r3 = scan_resident(reinterpret_cast<const void *>(scan_ranges_kernel<T, OP>), dev);
+  const int64_t resident = r1 < r3 ? r1 : r3;
   if (resident <= 0) return AK_ERR_CUDA;
-  const int grid = int(a.num_tiles < resident ? a.num_tiles : resident);
-  fn<<<grid, SCAN_BLOCK, 0, st>>>(a);
+  // one range per resident warp, whole warp tiles each
+  // (at least 1,024 ranges when there are that many warp tiles: the float +
+  // summation depth then has a device-independent bound)
+  int64_t target = resident * SCAN_WARPS;
+  if (target < 1024) target = 1024;
+  if (target > a.wtiles) target = a.wtiles;
+  if (target > SCAN_MAX_RANGES) target = SCAN_MAX_RANGES;
+  a.per = (a.wtiles + target - 1) / target;
+  a.nranges = (a.wtiles + a.per - 1) / a.per;
+  const unsigned blocks = unsigned((a.nranges + SCAN_WARPS - 1) / SCAN_WARPS);
+  scan_reduce_kernel<T, OP><<<blocks, SCAN_BLOCK, 0, st>>>(a);
+  scan_carry_kernel<T, OP><<<1, SCAN_CARRY_BLOCK, 0, st>>>(a);
+  scan_ranges_kernel<T, OP><<<blocks, SCAN_BLOCK, 0, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? AK_OK : AK_ERR_CUDA;
 }
 
@@ -492,22 +454,19 @@ ak_status ak_accumulate(const void *d_x, void *d_out, int64_t n, ak_dtype kd, ak
   a.x = d_x;
   a.out = d_out;
   a.n = n;
-  a.num_tiles = L.tiles;
+  a.wtiles = L.wtiles;
   a.init_bits = 0;
   if (h_init) std::memcpy(&a.init_bits, h_init, size_t(kb));  // little-endian: low bytes hold the value
   else a.init_bits = ak::scan_identity_bits(int(kd), int(op));
   a.inclusive = inclusive;
   a.aligned16 = !misaligned(d_x, 16) && !misaligned(d_out, 16);
-  a.debug_skip = (o.debug_flags & AK_DEBUG_SKIP_FIRST_TILE) ? 1 : 0;
-  a.timeout_ns = o.timeout_ns;
   char *t = static_cast<char *>(d_temp);
-  a.hdr = reinterpret_cast<ak::DevHeader *>(t);
-  a.flags = reinterpret_cast<uint32_t *>(t + L.flags);
-  a.agg_bits = reinterpret_cast<unsigned long long *>(t + L.agg);
-  a.inc_bits = reinterpret_cast<unsigned long long *>(t + L.inc);
+  a.agg = reinterpret_cast<unsigned long long *>(t + L.agg);
+  a.pre = reinterpret_cast<unsigned long long *>(t + L.pre);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // header (status, tile counter) and the flags start at zero; values need no clearing
-  if (cudaMemsetAsync(t, 0, L.agg, st) != cudaSuccess) return AK_ERR_CUDA;
+  // the header (status word, diagnostics) starts clean; the range slots are
+  // written before they are read
+  if (cudaMemsetAsync(t, 0, sizeof(ak::DevHeader), st) != cudaSuccess) return AK_ERR_CUDA;
   return ak::scan_dispatch(int(kd), int(op), a, st);
 }
 
