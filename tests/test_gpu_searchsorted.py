@@ -131,3 +131,58 @@ def test_full_size_sampled(ak):
     assert np.all(last >= first - 1)
     o = np.argsort(x, kind="stable")
     assert np.all(np.diff(first[o]) >= 0) and np.all(np.diff(last[o]) >= 0)
+
+
+TILE = 4096  # queries per CTA iteration; a tile in v's order takes the shared window
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("order", ["ascending", "descending"])
+@pytest.mark.parametrize("side", ["first", "last"])
+def test_sorted_query_tiles(ak, dtype, order, side):
+    """Queries in v's own order (duplicates, hits, specials): every tile is
+    answered through the shared-memory window; three whole tiles and a ragged
+    one."""
+    keys = np.concatenate([synth.random_keys(60_000, dtype, seed=181, mode="dups"),
+                           synth.random_keys(40_003 - synth.special_values(dtype).size, dtype, seed=182),
+                           synth.special_values(dtype)])
+    v = oracle.sort(keys, order)
+    x = oracle.sort(_queries(v, dtype, 183, 3 * TILE + 5 - synth.special_values(dtype).size), order)
+    assert x.size == 3 * TILE + 5
+    got = _search(ak, v, x, side, order)
+    np.testing.assert_array_equal(got, oracle.searchsorted(v, x, side, order))
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.float32, np.int64])
+def test_sorted_queries_tile_boundaries_and_windows(ak, dtype):
+    """m = one tile -1/+0/+1; dense tiles (the window holds the keys between a
+    tile's first and last answer) and sparse ones (queries spread over 2M keys:
+    the window is above 64 KB and the tile bisects in global memory between its
+    bounds)."""
+    v = oracle.sort(synth.random_keys(2_000_003, dtype, seed=184, mode="dups"))
+    for m in (TILE - 1, TILE, TILE + 1):
+        dense = oracle.sort(v[(synth.splitmix64(185 + m, m) % np.uint64(6_000)).astype(np.int64) + 1_000_000])
+        sparse = oracle.sort(_queries(v, dtype, 186 + m, m - synth.special_values(dtype).size))
+        for x in (dense, sparse):
+            for side in ("first", "last"):
+                got = _search(ak, v, x, side, "ascending")
+                np.testing.assert_array_equal(got, oracle.searchsorted(v, x, side), err_msg=f"m={m} {side}")
+
+
+def test_mixed_sorted_and_unsorted_tiles(ak):
+    """Tiles in order, out of order, in the reverse order and with one
+    descent at a tile's last slot, in one batch: each tile takes its own path
+    and every answer matches."""
+    v = oracle.sort(synth.random_keys(300_000, np.float64, seed=187, mode="dups"))
+    q = _queries(v, np.float64, 188, 4 * TILE - synth.special_values(np.float64).size)
+    a = oracle.sort(q[:TILE])
+    b = q[TILE: 2 * TILE]
+    c = oracle.sort(q[2 * TILE: 3 * TILE])[::-1]
+    d = oracle.sort(q[3 * TILE:])
+    d[-1], d[-2] = d[-2], d[-1]
+    x = np.ascontiguousarray(np.concatenate([a, b, c, d]))
+    for side in ("first", "last"):
+        for order in ("ascending", "descending"):
+            vv = oracle.sort(v, order)
+            got = _search(ak, vv, x, side, order)
+            np.testing.assert_array_equal(got, oracle.searchsorted(vv, x, side, order), err_msg=f"{side} {order}")
