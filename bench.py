@@ -15,7 +15,7 @@ are larger than L2 as well.  SM clocks are sampled with nvidia-smi during the
 timed steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-       python bench.py --workload c1|c3|c4|c5|searchsorted|accumulate   (their own lines)
+       python bench.py --workload c1|c3|c4|c5|searchsorted|accumulate|int128   (their own lines)
 Under torchrun every rank sorts its own replica of the workload on its own GPU
 (the sort has no exchange step on one node here: replicas, weak scaling).
 """
@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison of the headline")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted", "accumulate"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted", "accumulate", "int128"],
                     help="c2 (default): the headline line; the others print their own lines")
     ap.add_argument("--segments", type=int, default=65536, help="c4: number of segments")
     ap.add_argument("--tile-config", type=int, default=0, help="c2: digit-pass tile configuration (0 = default)")
@@ -803,6 +803,83 @@ def run_workload(args):
         run_searchsorted(args, torch, ak, synth, dev, stream, flush, peak)
     elif args.workload == "accumulate":
         run_accumulate(args, torch, ak, synth, dev, stream, flush, peak)
+    elif args.workload == "int128":
+        run_int128(args, torch, ak, synth, dev, stream, flush, peak)
+
+
+def _i128_order_ok(lo: np.ndarray, hi: np.ndarray) -> bool:
+    """Signed 128-bit keys (low, high words) in non-decreasing order."""
+    h = hi.view(np.int64)
+    return bool(np.all((h[1:] > h[:-1]) | ((h[1:] == h[:-1]) & (lo[1:] >= lo[:-1]))))
+
+
+def _i128_hash(lo: np.ndarray, hi: np.ndarray) -> int:
+    """Order-independent hash of a multiset of 128-bit keys."""
+    with np.errstate(over="ignore"):
+        z = lo ^ ((hi ^ (hi >> np.uint64(29))) * np.uint64(0xBF58476D1CE4E5B9))
+        z = (z ^ (z >> np.uint64(31))) * np.uint64(0x94D049BB133111EB)
+        z ^= z >> np.uint64(32)
+        return int(z.sum(dtype=np.uint64))
+
+
+def run_int128(args, torch, ak, synth, dev, stream, flush, peak):
+    """Int128 keys (the widest type of the paper's local-sort benchmarks):
+    268,435,456 signed 128-bit keys over all bit patterns (4 GiB), stable
+    ak_sort in place and ak_sortperm, through the radix path (16 digit
+    passes).  value = key bytes sorted per second over both calls."""
+    n = args.n
+    lo = synth.splitmix64(50, n)
+    hi = synth.splitmix64(51, n)
+    host = np.empty((n, 2), dtype=np.uint64)
+    host[:, 0], host[:, 1] = lo, hi
+    pristine = torch.from_numpy(host.view(np.int64)).to(dev)
+    work = torch.empty_like(pristine)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lib = ak.load()
+    tb = max(ak.temp_bytes(op, n, ak.AK_I128) for op in (ak.AK_OP_SORT, ak.AK_OP_SORTPERM))
+    temp = ak.workspace(tb, dev)
+    pass_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * ak.AK_MAX_PASSES)]
+    for e in pass_ev:
+        e.record(stream)
+    opts = ak.Options()
+    ev_arr = (ctypes.c_void_p * len(pass_ev))(*[e.cuda_event for e in pass_ev])
+    opts.pass_events = ctypes.cast(ev_arr, ctypes.c_void_p)
+    res, pass_ms, pass_bytes = {}, [], []
+    for op in ("sort", "sortperm"):
+        def call(op=op):
+            if op == "sort":
+                rc = lib.ak_sort(work.data_ptr(), n, ak.AK_I128, 0, temp.data_ptr(), temp.numel(), stream.cuda_stream,
+                                 ctypes.byref(opts))
+            else:
+                rc = lib.ak_sortperm(pristine.data_ptr(), perm.data_ptr(), n, ak.AK_I128, 0, temp.data_ptr(),
+                                     temp.numel(), stream.cuda_stream, ctypes.byref(opts))
+            if rc:
+                raise ak.AkError(rc, op)
+
+        ms = _timed(torch, stream, flush, lambda: work.copy_(pristine), call, args.warmup, args.steps)
+        npass = ak.ak_last_info(temp)["radix_passes"]
+        pb = onesweep_bytes(op, n, 16, 16)
+        for p in range(16):  # the last timed call's passes
+            pass_ms.append(pass_ev[2 * p].elapsed_time(pass_ev[2 * p + 1]))
+            pass_bytes.append(pb[p] if npass == 16 else 0)
+        res[op] = {"ms": round(ms, 3), "GBps": round(n * 16 / (ms / 1e3) / 1e9, 2), "digit_passes": npass}
+        if op == "sort":  # the last timed sort's output, before the sortperm timing restores the keys
+            out = work.cpu().numpy().view(np.uint64)
+            ok_sort = _i128_order_ok(out[:, 0], out[:, 1]) and _i128_hash(out[:, 0], out[:, 1]) == _i128_hash(lo, hi)
+            del out
+    p = perm.cpu().numpy().view(np.uint32).astype(np.int64)
+    ok_perm = bool(np.all(np.bincount(p, minlength=n) == 1)) and _i128_order_ok(lo[p], hi[p])
+    if not (ok_sort and ok_perm):
+        raise RuntimeError(f"int128 output check failed: sort {ok_sort} sortperm {ok_perm}")
+    total_ms = res["sort"]["ms"] + res["sortperm"]["ms"]
+    value = 2 * n * 16 / (total_ms / 1e3) / 1e9
+    achieved = sum(pass_bytes) / (sum(pass_ms) / 1e3) / 1e9
+    _line(args, f"{n:,} Int128 keys over all bit patterns (4 GiB), ak_sort + ak_sortperm ascending, radix path",
+          value, {"dtype": "i128", "results": res, "output_checked": True,
+                  "roofline": {"bound": "hbm", "kernel": "onesweep_pass<u128>", "achieved": round(achieved, 1),
+                               "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                               "launches": len(pass_ms)},
+                  "literal_2x_key_bytes_frac_of_measured": round(2 * value / peak, 4)})
 
 
 def run_accumulate(args, torch, ak, synth, dev, stream, flush, peak):

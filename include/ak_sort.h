@@ -45,12 +45,17 @@ typedef struct CUstream_st *ak_stream_t; /* same handle as cudaStream_t */
 /* Key element types: the paper's FFI list (Sec. IV: int16, int32, int64,
  * float, double) with unsigned variants, and the 16-bit floats IEEE binary16
  * (AK_F16) and bfloat16 (AK_BF16, the upper half of a binary32), ordered like
- * the other floats (-0.0 before +0.0, every NaN after +Inf and tied); __int128
- * is not supported.  ak_accumulate does not take the 16-bit floats. */
+ * the other floats (-0.0 before +0.0, every NaN after +Inf and tied), and the
+ * 128-bit integers (AK_I128, AK_U128: two's complement, little-endian, 16-byte
+ * aligned; the same layout as __int128 / unsigned __int128 on both host
+ * architectures).  ak_accumulate takes neither the 16-bit floats nor the
+ * 128-bit integers; 128-bit keys go through the radix path only: sort,
+ * sortperm, sortperm_lowmem, sort_pairs and the binary search (segmented sort,
+ * the learned, block and merge paths: AK_ERR_UNSUPPORTED). */
 typedef enum ak_dtype {
     AK_U16 = 0, AK_I16 = 1, AK_U32 = 2, AK_I32 = 3,
     AK_U64 = 4, AK_I64 = 5, AK_F32 = 6, AK_F64 = 7,
-    AK_F16 = 8, AK_BF16 = 9
+    AK_F16 = 8, AK_BF16 = 9, AK_I128 = 10, AK_U128 = 11
 } ak_dtype;
 
 typedef enum ak_order { AK_ASCENDING = 0, AK_DESCENDING = 1 } ak_order;
@@ -116,7 +121,7 @@ typedef struct ak_options {
     int32_t reserved[2];   /* must be zero */
 } ak_options;
 
-#define AK_MAX_PASSES 8
+#define AK_MAX_PASSES 16
 
 /* Test hook: no CTA owns the first tile of any radix pass, so every
  * look-back that reaches it waits until

@@ -18,12 +18,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("AK_SORT_LIB") or os.path.join(_HERE, "lib", "libak_sort.so")
 
 AK_U16, AK_I16, AK_U32, AK_I32, AK_U64, AK_I64, AK_F32, AK_F64, AK_F16, AK_BF16 = range(10)
+AK_I128, AK_U128 = 10, 11  # 128-bit keys: int64 tensors of shape (n, 2), [low word, high word]
 AK_ASCENDING, AK_DESCENDING = 0, 1
 AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED, AK_OP_SORTPERM_LOWMEM = range(5)
 AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK, AK_PATH_MERGE = range(5)
 AK_TILE_CONFIGS = 4
 AK_DEBUG_SKIP_FIRST_TILE = 1
-AK_MAX_PASSES = 8
+AK_MAX_PASSES = 16
 STATUS_NAMES = {0: "AK_OK", 1: "AK_ERR_INVALID_ARG", 2: "AK_ERR_UNSUPPORTED",
                 3: "AK_ERR_WORKSPACE_TOO_SMALL", 4: "AK_ERR_CUDA", 5: "AK_ERR_TIMEOUT",
                 6: "AK_ERR_INDEX_OVERFLOW"}
@@ -137,6 +138,18 @@ def dtype_code(t: torch.Tensor, as_unsigned: bool = False) -> int:
     return code
 
 
+def key_code(t: torch.Tensor, as_unsigned: bool = False, wide: bool = False) -> tuple[int, int]:
+    """(ak_dtype, key count) of a key tensor.  `wide`: 128-bit integer keys
+    held as a contiguous int64 tensor of shape (n, 2), each row the low and
+    the high 64-bit word (two's complement, little-endian: the layout of
+    __int128); `as_unsigned` then reads them as unsigned."""
+    if not wide:
+        return dtype_code(t, as_unsigned), t.numel()
+    if t.dtype != torch.int64 or t.dim() != 2 or t.shape[1] != 2:
+        raise TypeError("128-bit keys are an int64 tensor of shape (n, 2)")
+    return (AK_U128 if as_unsigned else AK_I128), t.shape[0]
+
+
 def order_code(order) -> int:
     if order in ("ascending", "asc", AK_ASCENDING, False):
         return AK_ASCENDING
@@ -201,11 +214,11 @@ def _temp_for(temp, op, n, kd, device, val_bytes=0, nseg=0, options=None):
 
 
 def ak_sort(keys: torch.Tensor, order="ascending", *, temp=None, stream=None, options=None,
-            unsigned: bool = False) -> torch.Tensor:
-    """Stable in-place sort of a 1-D CUDA tensor; returns `keys`."""
+            unsigned: bool = False, wide: bool = False) -> torch.Tensor:
+    """Stable in-place sort of a 1-D CUDA tensor (or of 128-bit keys, `wide`);
+    returns `keys`."""
     _contig_cuda(keys, "keys")
-    kd = dtype_code(keys, unsigned)
-    n = keys.numel()
+    kd, n = key_code(keys, unsigned, wide)
     temp = _temp_for(temp, AK_OP_SORT, n, kd, keys.device, options=options)
     _check(load().ak_sort(keys.data_ptr(), n, kd, order_code(order), temp.data_ptr(), temp.numel(),
                           _stream_ptr(stream), _opts(options)), "ak_sort")
@@ -213,11 +226,10 @@ def ak_sort(keys: torch.Tensor, order="ascending", *, temp=None, stream=None, op
 
 
 def ak_sortperm(keys: torch.Tensor, order="ascending", *, perm=None, temp=None, stream=None,
-                options=None, unsigned: bool = False) -> torch.Tensor:
+                options=None, unsigned: bool = False, wide: bool = False) -> torch.Tensor:
     """Stable sorting permutation as UInt32 bits in an int32 tensor (0-based)."""
     _contig_cuda(keys, "keys")
-    kd = dtype_code(keys, unsigned)
-    n = keys.numel()
+    kd, n = key_code(keys, unsigned, wide)
     if perm is None:
         perm = torch.empty(n, dtype=torch.int32, device=keys.device)
     _contig_cuda(perm, "perm")
@@ -229,12 +241,11 @@ def ak_sortperm(keys: torch.Tensor, order="ascending", *, perm=None, temp=None, 
 
 
 def ak_sortperm_lowmem(keys: torch.Tensor, order="ascending", *, perm=None, temp=None, stream=None,
-                       options=None, unsigned: bool = False) -> torch.Tensor:
+                       options=None, unsigned: bool = False, wide: bool = False) -> torch.Tensor:
     """ak_sortperm's permutation from a workspace without key copies (indices
     only; keys are read through them)."""
     _contig_cuda(keys, "keys")
-    kd = dtype_code(keys, unsigned)
-    n = keys.numel()
+    kd, n = key_code(keys, unsigned, wide)
     if perm is None:
         perm = torch.empty(n, dtype=torch.int32, device=keys.device)
     _contig_cuda(perm, "perm")
@@ -246,14 +257,13 @@ def ak_sortperm_lowmem(keys: torch.Tensor, order="ascending", *, perm=None, temp
 
 
 def ak_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, order="ascending", *, temp=None,
-                  stream=None, options=None, unsigned: bool = False):
+                  stream=None, options=None, unsigned: bool = False, wide: bool = False):
     """Stable in-place key-value sort; returns (keys, vals)."""
     _contig_cuda(keys, "keys")
     _contig_cuda(vals, "vals")
-    if vals.numel() != keys.numel():
+    kd, n = key_code(keys, unsigned, wide)
+    if vals.numel() != n:
         raise ValueError("keys and vals differ in length")
-    kd = dtype_code(keys, unsigned)
-    n = keys.numel()
     vb = vals.element_size()
     temp = _temp_for(temp, AK_OP_SORT_PAIRS, n, kd, keys.device, val_bytes=vb, options=options)
     _check(load().ak_sort_pairs(keys.data_ptr(), vals.data_ptr(), vb, n, kd, order_code(order),
@@ -279,36 +289,38 @@ def ak_sort_segmented(keys: torch.Tensor, offsets: torch.Tensor, order="ascendin
     return keys
 
 
-def _searchsorted(name: str, v: torch.Tensor, x: torch.Tensor, order, out, stream, unsigned: bool):
+def _searchsorted(name: str, v: torch.Tensor, x: torch.Tensor, order, out, stream, unsigned: bool,
+                  wide: bool = False):
     _contig_cuda(v, "v")
     _contig_cuda(x, "x")
     if x.dtype != v.dtype:
         raise TypeError(f"queries ({x.dtype}) and sorted keys ({v.dtype}) differ in dtype")
-    kd = dtype_code(v, unsigned)
+    kd, n = key_code(v, unsigned, wide)
+    _, m = key_code(x, unsigned, wide)
     if out is None:
-        out = torch.empty(x.numel(), dtype=torch.int64, device=x.device)
+        out = torch.empty(m, dtype=torch.int64, device=x.device)
     else:
         _contig_cuda(out, "out")
-        if out.dtype != torch.int64 or out.numel() != x.numel():
+        if out.dtype != torch.int64 or out.numel() != m:
             raise ValueError("out must be an int64 tensor with one element per query")
-    _check(getattr(load(), name)(v.data_ptr(), v.numel(), x.data_ptr(), x.numel(), kd, order_code(order),
+    _check(getattr(load(), name)(v.data_ptr(), n, x.data_ptr(), m, kd, order_code(order),
                                  out.data_ptr(), _stream_ptr(stream)), name)
     return out
 
 
 def ak_searchsortedfirst(v: torch.Tensor, x: torch.Tensor, order="ascending", *, out=None, stream=None,
-                         unsigned: bool = False) -> torch.Tensor:
+                         unsigned: bool = False, wide: bool = False) -> torch.Tensor:
     """0-based index of the first element of the sorted `v` not coming before
     each query (len(v) if none): Julia's searchsortedfirst minus one.  Fills
     `out` (int64, one per query) when given, else allocates it."""
-    return _searchsorted("ak_searchsortedfirst", v, x, order, out, stream, unsigned)
+    return _searchsorted("ak_searchsortedfirst", v, x, order, out, stream, unsigned, wide)
 
 
 def ak_searchsortedlast(v: torch.Tensor, x: torch.Tensor, order="ascending", *, out=None, stream=None,
-                        unsigned: bool = False) -> torch.Tensor:
+                        unsigned: bool = False, wide: bool = False) -> torch.Tensor:
     """0-based index of the last element of the sorted `v` that each query does
     not come before (-1 if none): Julia's searchsortedlast minus one."""
-    return _searchsorted("ak_searchsortedlast", v, x, order, out, stream, unsigned)
+    return _searchsorted("ak_searchsortedlast", v, x, order, out, stream, unsigned, wide)
 
 
 SCAN_OPS = {"add": 0, "max": 1, "min": 2}

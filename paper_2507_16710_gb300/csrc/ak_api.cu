@@ -53,8 +53,15 @@ static bool key_info(int kd, KeyInfo *ki) {
     case AK_F64: *ki = {8, KIND_FLOAT}; return true;
     case AK_F16: *ki = {2, KIND_FLOAT}; return true;
     case AK_BF16: *ki = {2, KIND_BF16}; return true;
+    case AK_U128: *ki = {16, KIND_UINT}; return true;
+    case AK_I128: *ki = {16, KIND_SINT}; return true;
   }
   return false;
+}
+
+// 128-bit keys take the radix path only (AUTO resolves to it).
+static bool path_supported(const KeyInfo &ki, const ak_options &o) {
+  return ki.bytes != 16 || o.path == AK_PATH_AUTO || o.path == AK_PATH_RADIX;
 }
 
 // Workspace of the radix path.
@@ -141,6 +148,8 @@ static cudaError_t radix_dispatch(int key_bytes, const RadixCall &c) {
       return c.kind == KIND_FLOAT  ? radix_launch_u32_float(c)
              : c.kind == KIND_SINT ? radix_launch_u32_sint(c)
                                    : radix_launch_u32_uint(c);
+    case 16:
+      return c.kind == KIND_SINT ? radix_launch_u128_sint(c) : radix_launch_u128_uint(c);
     default:
       return c.kind == KIND_FLOAT  ? radix_launch_u64_float(c)
              : c.kind == KIND_SINT ? radix_launch_u64_sint(c)
@@ -215,6 +224,7 @@ __global__ void iota_u32_kernel(uint32_t *p, int64_t n) {
 // radix otherwise.
 constexpr int64_t LEARNED_AUTO_MIN = int64_t(1) << 25;
 static int choose_path(int op, int64_t n, int key_bytes, int vb, const ak_options &o) {
+  if (key_bytes == 16) return AK_PATH_RADIX;
   if (o.path == AK_PATH_RADIX || o.path == AK_PATH_BLOCK || o.path == AK_PATH_MERGE) return o.path;
   if (o.path == AK_PATH_LEARNED) return n < (int64_t(1) << 32) ? AK_PATH_LEARNED : AK_PATH_RADIX;
   (void)op;
@@ -560,6 +570,7 @@ ak_status ak_sort_temp_bytes(int op, int64_t n, ak_dtype kd, int val_bytes, int6
   if (op == AK_OP_SORT_SEGMENTED && nseg < 0) return AK_ERR_INVALID_ARG;
   ak_options o;
   if (!resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
+  if (ki.bytes == 16 && (op == AK_OP_SORT_SEGMENTED || !path_supported(ki, o))) return AK_ERR_UNSUPPORTED;
   if (op != AK_OP_SORT_SEGMENTED && op != AK_OP_SORTPERM_LOWMEM) apply_tuning(op, kd, n, val_bytes, o);
   *bytes = temp_for(op, n, ki.bytes, val_bytes, nseg, o);
   return AK_OK;
@@ -570,6 +581,7 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order, void *d_
   KeyInfo ki;
   ak_options o;
   if (n < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
+  if (!path_supported(ki, o)) return AK_ERR_UNSUPPORTED;
   if (n == 0) return AK_OK;
   if (!d_keys || !aligned(d_keys, ki.bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
@@ -589,6 +601,7 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
   KeyInfo ki;
   ak_options o;
   if (n < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
+  if (!path_supported(ki, o)) return AK_ERR_UNSUPPORTED;
   if (n == 0) return AK_OK;
   if (n > int64_t(0xFFFFFFFFll)) return AK_ERR_INDEX_OVERFLOW;
   if (!d_keys || !d_perm || !aligned(d_keys, ki.bytes) || !aligned(d_perm, 4)) return AK_ERR_INVALID_ARG;
@@ -623,6 +636,7 @@ ak_status ak_sort_pairs(void *d_keys, void *d_vals, int val_bytes, int64_t n, ak
   ak_options o;
   if (n < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o)) return AK_ERR_INVALID_ARG;
   if (val_bytes != 1 && val_bytes != 2 && val_bytes != 4 && val_bytes != 8) return AK_ERR_INVALID_ARG;
+  if (!path_supported(ki, o)) return AK_ERR_UNSUPPORTED;
   if (n == 0) return AK_OK;
   if (!d_keys || !d_vals || !aligned(d_keys, ki.bytes) || !aligned(d_vals, val_bytes)) return AK_ERR_INVALID_ARG;
   if (d_temp && !aligned(d_temp, 256)) return AK_ERR_INVALID_ARG;
@@ -646,6 +660,7 @@ ak_status ak_sort_segmented(void *d_keys, const int64_t *d_offsets, int64_t nseg
   ak_options o;  // the segmented sort has no options of its own; malformed ones are still refused
   if (n < 0 || nseg < 0 || !key_info(kd, &ki) || !valid_order(order) || !resolve_options(opt, &o))
     return AK_ERR_INVALID_ARG;
+  if (ki.bytes == 16) return AK_ERR_UNSUPPORTED;
   if (n == 0 || nseg == 0) return AK_OK;
   if (n > int64_t(0xFFFFFFFFll) || nseg > int64_t(0xFFFFFFFFll)) return AK_ERR_UNSUPPORTED;
   if (!d_keys || !d_offsets || !aligned(d_keys, ki.bytes) || !aligned(d_offsets, 8)) return AK_ERR_INVALID_ARG;

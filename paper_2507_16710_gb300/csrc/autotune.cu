@@ -100,6 +100,7 @@ static int key_bytes_of(ak_dtype kd) {
     case AK_U16: case AK_I16: case AK_F16: case AK_BF16: return 2;
     case AK_U32: case AK_I32: case AK_F32: return 4;
     case AK_U64: case AK_I64: case AK_F64: return 8;
+    case AK_U128: case AK_I128: return 16;
   }
   return 0;
 }
@@ -111,6 +112,7 @@ static ak_status candidates(int op, int64_t n, ak_dtype kd, int val_bytes, std::
   if (op != AK_OP_SORT && op != AK_OP_SORTPERM && op != AK_OP_SORT_PAIRS) return AK_ERR_INVALID_ARG;
   const int kb = key_bytes_of(kd);
   if (n <= 0 || kb == 0) return AK_ERR_INVALID_ARG;
+  if (kb == 16) return AK_ERR_UNSUPPORTED;  // 128-bit keys have one configuration: nothing to choose
   const int vb = (op == AK_OP_SORT_PAIRS) ? val_bytes : 0;
   if (op == AK_OP_SORT_PAIRS && vb != 1 && vb != 2 && vb != 4 && vb != 8) return AK_ERR_INVALID_ARG;
   cands->clear();

@@ -17,7 +17,7 @@ namespace ak {
 
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int MAX_PASSES = 8;
+constexpr int MAX_PASSES = 16;  // 128-bit keys
 
 // KIND_FLOAT: IEEE binary16/32/64 by the key width; KIND_BF16: bfloat16 (the
 // upper half of a binary32: 8 exponent bits), 16-bit keys only.
@@ -48,7 +48,9 @@ template <typename U>
 __device__ __forceinline__ U radix_key(U u, int kind, U flip) {
   constexpr U SIGN = U(U(1) << (8 * sizeof(U) - 1));
   U r;
-  if (is_float_kind(kind)) {
+  if constexpr (sizeof(U) > 8) {  // 128-bit keys are integers
+    r = kind == KIND_SINT ? U(u ^ SIGN) : u;
+  } else if (is_float_kind(kind)) {
     const U mag = U(u & U(~SIGN));
     r = (u & SIGN) ? U(~u) : U(u ^ SIGN);
     if (mag > (kind == KIND_BF16 ? float_exp<KIND_BF16, U>() : FloatBits<U>::EXP)) r = U(~U(0));
@@ -80,8 +82,13 @@ __device__ __forceinline__ U radix_key_t(U u, U flip) {
 
 template <typename U>
 __device__ __forceinline__ uint32_t digit_of(U r, int shift) {
-  return uint32_t(r >> shift) & (RADIX - 1);
+  if constexpr (sizeof(U) > 8)  // the 32-bit word that holds the digit
+    return (uint32_t(r >> (shift & ~31)) >> (shift & 31)) & (RADIX - 1);
+  else
+    return uint32_t(r >> shift) & (RADIX - 1);
 }
+
+using u128 = unsigned __int128;
 
 // ----------------------------------------------------------------- status word
 // Header at offset 0 of every workspace.  `status` holds the first device-side

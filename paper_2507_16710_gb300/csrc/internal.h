@@ -55,6 +55,8 @@ cudaError_t radix_launch_u32_float(const RadixCall &c);
 cudaError_t radix_launch_u64_uint(const RadixCall &c);
 cudaError_t radix_launch_u64_sint(const RadixCall &c);
 cudaError_t radix_launch_u64_float(const RadixCall &c);
+cudaError_t radix_launch_u128_uint(const RadixCall &c);
+cudaError_t radix_launch_u128_sint(const RadixCall &c);
 
 // Tile shapes of the digit-pass kernel.  Configuration c has CFG_BLOCK[c]
 // threads and a tile of about CFG_BYTES[c] bytes of keys+values (keys per

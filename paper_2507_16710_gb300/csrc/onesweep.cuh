@@ -152,8 +152,8 @@ static __global__ void __launch_bounds__(RADIX) plan_kernel(const unsigned long 
 
 // ---------------------------------------------------------------- digit pass
 // Digit of a key in a radix pass.  A 64-bit key's digit lies in one 32-bit
-// half (the same half for every key of a pass), so only that half is
-// transformed; the result equals digit_of(radix_key_t(k)).
+// half (a 128-bit key's in one 32-bit word, the same for every key of a pass),
+// so only that word is transformed; the result equals digit_of(radix_key_t(k)).
 template <int KIND, typename U>
 __device__ __forceinline__ uint32_t radix_digit(U k, U flip, int shift) {
   if constexpr (sizeof(U) == 8) {
@@ -170,6 +170,13 @@ __device__ __forceinline__ uint32_t radix_digit(U k, U flip, int shift) {
       if (mh > 0x7FF00000u || (mh == 0x7FF00000u && lo != 0u)) w = 0xFFFFFFFFu;  // NaN: all ones
     }
     return ((w ^ f) >> (shift & 31)) & uint32_t(RADIX - 1);
+  } else if constexpr (sizeof(U) == 16) {  // 128-bit integers: the 32-bit word of the digit
+    const int wi = shift >> 5;
+    uint32_t w = uint32_t(k >> (32 * wi)) ^ uint32_t(flip >> (32 * wi));
+    if constexpr (KIND == KIND_SINT) {
+      if (wi == 3) w ^= 0x80000000u;
+    }
+    return (w >> (shift & 31)) & uint32_t(RADIX - 1);
   } else {
     return digit_of(radix_key_t<KIND>(k, flip), shift);
   }

@@ -119,6 +119,16 @@ cudaError_t run_status(const RadixCall &c) {
   a.debug_skip = (c.debug_flags & AK_DEBUG_SKIP_FIRST_TILE) ? 1 : 0;
   a.gate = c.gate;
   a.gate_want = c.gate_want;
+  if constexpr (sizeof(U) == 16) {  // 128-bit keys: the default configuration only
+    if constexpr (HAS_V && std::is_same<V, uint32_t>::value) {
+      if (c.gather) {
+        if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, CFG_DEFAULT, DIGIT_GATHER>(c, a);
+        return run_passes<U, V, HAS_V, KIND, uint32_t, CFG_DEFAULT, DIGIT_GATHER>(c, a);
+      }
+    }
+    if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, CFG_DEFAULT>(c, a);
+    return run_passes<U, V, HAS_V, KIND, uint32_t, CFG_DEFAULT>(c, a);
+  } else {
   if constexpr (HAS_V && std::is_same<V, uint32_t>::value) {
     if (c.gather) {  // low-memory sortperm: the shared-memory-staged configurations only
       if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, 0, DIGIT_GATHER>(c, a);
@@ -138,6 +148,7 @@ cudaError_t run_status(const RadixCall &c) {
     case 2: return run_passes<U, V, HAS_V, KIND, uint32_t, 2>(c, a);
     case CFG_WS: return run_passes<U, V, HAS_V, KIND, uint32_t, CFG_WS>(c, a);
     default: return run_passes<U, V, HAS_V, KIND, uint32_t, 0>(c, a);
+  }
   }
 }
 

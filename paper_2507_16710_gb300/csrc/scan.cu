@@ -428,7 +428,8 @@ ak_status scan_dispatch(int kd, int op, ScanArgs &a, cudaStream_t st) {
 extern "C" {
 
 ak_status ak_accumulate_temp_bytes(int64_t n, ak_dtype kd, size_t *bytes) {
-  if (kd == AK_F16 || kd == AK_BF16) return AK_ERR_UNSUPPORTED;  // 16-bit float sums: no rounding defined
+  if (kd == AK_F16 || kd == AK_BF16 || kd == AK_I128 || kd == AK_U128)
+    return AK_ERR_UNSUPPORTED;  // 16-bit float sums: no rounding defined; 128-bit scans not built
   const int kb = ak::scan_key_bytes(int(kd));
   if (!bytes || n < 0 || kb == 0) return AK_ERR_INVALID_ARG;
   *bytes = ak::scan_layout(n, kb).total;
@@ -438,7 +439,8 @@ ak_status ak_accumulate_temp_bytes(int64_t n, ak_dtype kd, size_t *bytes) {
 ak_status ak_accumulate(const void *d_x, void *d_out, int64_t n, ak_dtype kd, ak_scan_op op, int inclusive,
                         const void *h_init, void *d_temp, size_t temp_bytes, ak_stream_t stream,
                         const ak_options *opt) {
-  if (kd == AK_F16 || kd == AK_BF16) return AK_ERR_UNSUPPORTED;  // 16-bit float sums: no rounding defined
+  if (kd == AK_F16 || kd == AK_BF16 || kd == AK_I128 || kd == AK_U128)
+    return AK_ERR_UNSUPPORTED;  // 16-bit float sums: no rounding defined; 128-bit scans not built
   const int kb = ak::scan_key_bytes(int(kd));
   ak_options o;
   if (n < 0 || kb == 0 || op < AK_SCAN_ADD || op > AK_SCAN_MIN || (inclusive != 0 && inclusive != 1) ||

@@ -15,8 +15,8 @@
 // scheme, any other tile by bisection per query.
 //
 // Bisection (unsorted tiles), two levels, latency-bound on GB300:
-//  * a table of K pivot keys in shared memory (16 KB: K = 8192, 4096, 2048 for
-//    2-, 4-, 8-byte keys), v at positions P_i = floor(i n / (K + 1)),
+//  * a table of K pivot keys in shared memory (16 KB: K = 8192, 4096, 2048, 1024 for
+//    2-, 4-, 8-, 16-byte keys), v at positions P_i = floor(i n / (K + 1)),
 //    i = 1..K, loaded once per CTA; the table narrows each query to the stretch
 //    (P_c, P_{c+1}] of about n / (K + 1) keys with no global access;
 //  * bisection in global memory over that stretch, log2(n / K) dependent loads,
@@ -286,6 +286,8 @@ ak_status ss_dispatch(const void *v, int64_t n, const void *x, int64_t m, int kd
     case AK_F64: return ss_launch<uint64_t, KIND_FLOAT, LAST>(v, n, x, m, desc, out, st);
     case AK_F16: return ss_launch<uint16_t, KIND_FLOAT, LAST>(v, n, x, m, desc, out, st);
     case AK_BF16: return ss_launch<uint16_t, KIND_BF16, LAST>(v, n, x, m, desc, out, st);
+    case AK_U128: return ss_launch<u128, KIND_UINT, LAST>(v, n, x, m, desc, out, st);
+    case AK_I128: return ss_launch<u128, KIND_SINT, LAST>(v, n, x, m, desc, out, st);
   }
   return AK_ERR_INVALID_ARG;
 }
@@ -295,6 +297,7 @@ int ss_key_bytes(int kd) {
     case AK_U16: case AK_I16: case AK_F16: case AK_BF16: return 2;
     case AK_U32: case AK_I32: case AK_F32: return 4;
     case AK_U64: case AK_I64: case AK_F64: return 8;
+    case AK_U128: case AK_I128: return 16;
   }
   return 0;
 }

@@ -135,7 +135,7 @@ def test_searchsorted_host_checks(lib):
         assert f(None, 0, None, 0, ak.AK_F64, 0, None, None) == 0
         assert f(v, -1, x, 5, ak.AK_F64, 0, out, None) == 1            # negative n
         assert f(v, 10, x, -5, ak.AK_F64, 0, out, None) == 1           # negative m
-        assert f(v, 10, x, 5, 10, 0, out, None) == 1                   # bad dtype
+        assert f(v, 10, x, 5, 12, 0, out, None) == 1                   # bad dtype
         assert f(v, 10, x, 5, ak.AK_F64, 2, out, None) == 1            # bad order
         assert f(v, 10, None, 5, ak.AK_F64, 0, out, None) == 1         # NULL queries
         assert f(v, 10, x, 5, ak.AK_F64, 0, None, None) == 1           # NULL output
@@ -153,14 +153,17 @@ def test_accumulate_host_checks(lib):
     tiles = (1 << 20) // 8192  # 32 KB tiles of float32
     assert out.value >= tiles * (4 + 8 + 8) and out.value % 256 == 0
     assert lib.ak_accumulate_temp_bytes(-1, ak.AK_F32, ctypes.byref(out)) == 1
-    assert lib.ak_accumulate_temp_bytes(10, 10, ctypes.byref(out)) == 1
+    assert lib.ak_accumulate_temp_bytes(10, 12, ctypes.byref(out)) == 1
+    for kd in (ak.AK_I128, ak.AK_U128):  # 128-bit scans are not built
+        assert lib.ak_accumulate_temp_bytes(10, kd, ctypes.byref(out)) == 2
     for kd in (ak.AK_F16, ak.AK_BF16):  # valid key types the scan does not take
         assert lib.ak_accumulate_temp_bytes(10, kd, ctypes.byref(out)) == 2
     x, y, t = ctypes.c_void_p(1 << 16), ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 24)
     f = lib.ak_accumulate
     assert f(None, None, 0, ak.AK_I32, 0, 1, None, None, 0, None, None) == 0        # n = 0: nothing to do
     assert f(x, y, -1, ak.AK_I32, 0, 1, None, t, 1 << 20, None, None) == 1          # negative n
-    assert f(x, y, 10, 10, 0, 1, None, t, 1 << 20, None, None) == 1                 # bad dtype
+    assert f(x, y, 10, 12, 0, 1, None, t, 1 << 20, None, None) == 1                 # bad dtype
+    assert f(x, y, 10, ak.AK_I128, 0, 1, None, t, 1 << 20, None, None) == 2         # unsupported
     assert f(x, y, 10, ak.AK_F16, 0, 1, None, t, 1 << 20, None, None) == 2          # unsupported
     assert f(x, y, 10, ak.AK_I32, 3, 1, None, t, 1 << 20, None, None) == 1          # bad operator
     assert f(x, y, 10, ak.AK_I32, 0, 2, None, t, 1 << 20, None, None) == 1          # bad inclusive flag
@@ -267,3 +270,42 @@ def test_sortperm_lowmem_workspace_is_smaller(lib):
         low = ak.temp_bytes(ak.AK_OP_SORTPERM_LOWMEM, n, kd)
         assert low + 2 * n * kb <= full, (kd, low, full)
         assert low < n * 4 + (n // 1000) * 1024 + (1 << 20), (kd, low)
+
+
+def test_int128_host_checks(lib):
+    """128-bit keys: the radix path's workspace is sized like any other key
+    width; the segmented sort, the learned / block / merge paths and the
+    tuner refuse them (AK_ERR_UNSUPPORTED) before any launch."""
+    import paper_2507_16710_gb300 as ak
+    out = ctypes.c_size_t(0)
+    for kd in (ak.AK_I128, ak.AK_U128):
+        for op, vb in ((ak.AK_OP_SORT, 0), (ak.AK_OP_SORTPERM, 0), (ak.AK_OP_SORT_PAIRS, 8), (ak.AK_OP_SORTPERM_LOWMEM, 0)):
+            assert lib.ak_sort_temp_bytes(op, 1 << 20, kd, vb, 0, None, ctypes.byref(out)) == 0
+            assert out.value > (1 << 20) * 16 or op == ak.AK_OP_SORTPERM_LOWMEM
+        assert lib.ak_sort_temp_bytes(ak.AK_OP_SORT_SEGMENTED, 1 << 20, kd, 0, 4, None, ctypes.byref(out)) == 2
+        for path in (ak.AK_PATH_LEARNED, ak.AK_PATH_BLOCK, ak.AK_PATH_MERGE):
+            o = ak.Options()
+            o.path = path
+            assert lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 1 << 20, kd, 0, 0, ctypes.byref(o), ctypes.byref(out)) == 2
+            assert lib.ak_sort(None, 0, kd, 0, None, 0, None, ctypes.byref(o)) == 2
+            assert lib.ak_sortperm(None, None, 0, kd, 0, None, 0, None, ctypes.byref(o)) == 2
+        o = ak.Options()
+        o.path = ak.AK_PATH_RADIX
+        assert lib.ak_sort(None, 0, kd, 0, None, 0, None, ctypes.byref(o)) == 0  # n = 0 on the radix path
+        assert lib.ak_sort_segmented(None, None, 0, 0, kd, 0, None, 0, None, None) == 2
+        assert lib.ak_autotune_temp_bytes(ak.AK_OP_SORT, 1 << 20, kd, 0, ctypes.byref(out)) == 2
+        assert lib.ak_autotune_segmented_temp_bytes(1 << 20, 4, kd, ctypes.byref(out)) == 2
+    assert lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 10, 12, 0, 0, None, ctypes.byref(out)) == 1  # past the last dtype
+
+
+def test_int128_binding_shapes():
+    """The binding reads 128-bit keys as int64 tensors of shape (n, 2)."""
+    import torch
+    import paper_2507_16710_gb300 as ak
+    t = torch.zeros((5, 2), dtype=torch.int64)
+    assert ak.key_code(t, wide=True) == (ak.AK_I128, 5)
+    assert ak.key_code(t, True, wide=True) == (ak.AK_U128, 5)
+    with pytest.raises(TypeError):
+        ak.key_code(torch.zeros(10, dtype=torch.int64), wide=True)
+    with pytest.raises(TypeError):
+        ak.key_code(torch.zeros((5, 2), dtype=torch.int32), wide=True)
