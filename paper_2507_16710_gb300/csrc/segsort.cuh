@@ -398,15 +398,24 @@ struct SegCta {
     for (int i = tid; i < (1 << SUB_BITS); i += BLOCK) sub[i] = 0u;
     const R r0 = R(rk(gk[0]));
     R lo = R(~R(0)), hi = 0, vary = 0;
-    for (int i = tid; i < len; i += BLOCK) {
-      const U k = gk[i];
+    auto stage = [&](int i, U k) {
       ak[i] = k;
-      if (HAS_V) av[i] = gv[i];
       const R r = R(rk(k));
       lo = r < lo ? r : lo;
       hi = r > hi ? r : hi;
       vary |= r ^ r0;
+    };
+    int i0 = tid;
+    for (; i0 + 3 * BLOCK < len; i0 += 4 * BLOCK) {  // four loads in flight before the stores
+      const U k0 = gk[i0], k1 = gk[i0 + BLOCK], k2 = gk[i0 + 2 * BLOCK], k3 = gk[i0 + 3 * BLOCK];
+      stage(i0, k0);
+      stage(i0 + BLOCK, k1);
+      stage(i0 + 2 * BLOCK, k2);
+      stage(i0 + 3 * BLOCK, k3);
     }
+    for (; i0 < len; i0 += BLOCK) stage(i0, gk[i0]);
+    if (HAS_V)
+      for (int i = tid; i < len; i += BLOCK) av[i] = gv[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const R l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -601,12 +610,18 @@ __global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
     nwork = nlong + nbuck + nshort;
   }
   uint32_t par = 0;  // work slot: the next pop writes the other one, so one barrier per pop
+  // thread 0 pops each item one item ahead: the atomic's round trip runs while
+  // the current item is sorted, and its value is stored only before the pop
+  // barrier
+  uint32_t next_w = 0;
+  if (c.tid == 0) next_w = atomicAdd(&a.hdr->work_counter[0], 1u);
   while (true) {
-    if (c.tid == 0) s_work[par] = atomicAdd(&a.hdr->work_counter[0], 1u);
+    if (c.tid == 0) s_work[par] = next_w;
     __syncthreads();  // also: the previous item's shared buffers are free
     const int64_t w = s_work[par];
     par ^= 1u;
     if (w >= nwork) break;
+    if (c.tid == 0) next_w = atomicAdd(&a.hdr->work_counter[0], 1u);
     if (w >= nlong && w < nlong + nbuck) {  // a bucket of a big segment: from the workspace copy into the keys
       const BucketItem it = a.buckets[w - nlong];
       const int64_t g = a.seg_base + it.lo;
