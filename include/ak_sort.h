@@ -146,7 +146,12 @@ typedef struct ak_info {
     float loss_after;        /* learned: training loss after the MLP residual is trained */
     int64_t sample_size;     /* learned: sample keys drawn */
     int64_t coordinate;      /* learned: model input, 0 radix key, 1 value of a float key */
-    int64_t reserved[3];
+    int32_t mlp_used;        /* learned: 1 when the bucket table holds the trained MLP residual,
+                                0 when the piecewise-linear CDF alone gave the sorted sample a
+                                smaller (or equal) largest bucket, or nothing was trained */
+    int32_t reserved0;
+    int64_t sample_max_pl;   /* learned: most sample keys in one bucket, piecewise-linear table */
+    int64_t sample_max_mlp;  /* learned: the same with the MLP residual (0: not trained) */
 } ak_info;
 
 /*

@@ -61,10 +61,11 @@ class Info(ctypes.Structure):
                 ("overfull_keys", ctypes.c_int64), ("max_bucket", ctypes.c_int64),
                 ("loss_before", ctypes.c_float), ("loss_after", ctypes.c_float),
                 ("sample_size", ctypes.c_int64), ("coordinate", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("mlp_used", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("sample_max_pl", ctypes.c_int64), ("sample_max_mlp", ctypes.c_int64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved0"}
 
 
 _lock = threading.Lock()

@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(1024) lm_table_kernel(LearnedModel *md, int us
     md->nbuckets = nbuckets;
     md->bbits = bbits;
   }
+  if (use_mlp == 2) use_mlp = int(md->mlp_used);
   __shared__ float p[LM_PARAMS], c[LM_KNOTS];
   __shared__ float run[1024];
   constexpr int PER = (LM_TABLE + 1 + 1023) / 1024;  // values per thread (5)
@@ -351,6 +352,40 @@ __global__ void __launch_bounds__(1024) lm_table_kernel(LearnedModel *md, int us
       md->tk[k] = make_float2(T, __uint_as_float(K));
     }
   }
+}
+
+__global__ void lm_sample_runs_kernel(const float *xs, const float *xs_v, uint32_t m, LearnedModel *md, int slot,
+                                      const uint32_t *gate) {
+  if (gate && *gate) return;
+  const float *x = (md->coord && xs_v) ? xs_v : xs;  // the model's coordinate of the sorted sample
+  const uint32_t nb = md->nbuckets;
+  uint32_t best = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const uint32_t b = lm_bucket(md->tk, x[i], nb);
+    if (i + 1 < m && lm_bucket(md->tk, x[i + 1], nb) == b) continue;  // not the last key of its run
+    uint32_t lo = 0, hi = i;  // first index of the run: the first j with bucket(x[j]) == b
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (lm_bucket(md->tk, x[mid], nb) < b) lo = mid + 1;
+      else hi = mid;
+    }
+    const uint32_t len = i - lo + 1;
+    best = len > best ? len : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t other = __shfl_xor_sync(0xffffffffu, best, o);
+    best = other > best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(&md->sample_max[slot], best);
+}
+
+__global__ void lm_pick_kernel(LearnedModel *md, DevHeader *hdr, const uint32_t *gate) {
+  if (gate && *gate) return;
+  const uint32_t use = md->sample_max[1] != 0 && md->sample_max[1] < md->sample_max[0] ? 1u : 0u;
+  md->mlp_used = use;
+  hdr->info.mlp_used = int32_t(use);
+  hdr->info.sample_max_pl = int64_t(md->sample_max[0]);
+  hdr->info.sample_max_mlp = int64_t(md->sample_max[1]);
 }
 
 __global__ void __launch_bounds__(1024) lm_plan_kernel(const uint32_t *counts, int64_t n, LearnedModel *md,

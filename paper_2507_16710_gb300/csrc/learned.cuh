@@ -65,7 +65,8 @@ struct LearnedModel {
   uint32_t moderate[2];       // sample windows overloaded above LM_MODERATE: radix, value coordinate
   uint32_t heavy[2];          // sample windows overloaded above LM_HEAVY, per coordinate
   float lo_f, inv_f;          // value coordinate: sample minimum, 1 / sample range
-  uint32_t pad[3];
+  uint32_t sample_max[2];     // largest run of one bucket in the sorted sample: PL table, PL + MLP table
+  uint32_t mlp_used;          // 1: the bucket table holds the MLP residual
   float c_v[LM_KNOTS];        // knots of the value coordinate
   float c[LM_KNOTS];          // PL knots xi_j (x-hat of sample order statistics)
   float params[LM_PARAMS];
@@ -293,7 +294,16 @@ __global__ void lm_grad_partial_kernel(const float *x, const float *y, int64_t m
 __global__ void lm_grad_reduce_kernel(const float *partials, int nparts, int64_t m, float *grad, float *loss);
 
 // Table T[k] = running max of clamp(F(k/M)), K[k] = min(B-1, floor(B T[k])).
+// use_mlp: 0 the piecewise-linear CDF alone, 1 with the MLP residual, 2 as
+// md->mlp_used says.
 __global__ void lm_table_kernel(LearnedModel *md, int use_mlp, uint32_t nbuckets, uint32_t bbits,
                                 const uint32_t *gate);
+// Largest number of sorted-sample keys in one bucket under the current table
+// (the sample's buckets are non-decreasing): max-reduced into md->sample_max[slot].
+__global__ void lm_sample_runs_kernel(const float *xs, const float *xs_v, uint32_t m, LearnedModel *md, int slot,
+                                      const uint32_t *gate);
+// The MLP residual is kept only when it strictly shrinks the sample's largest
+// bucket; records the choice in md->mlp_used and the ak_info.
+__global__ void lm_pick_kernel(LearnedModel *md, DevHeader *hdr, const uint32_t *gate);
 
 }  // namespace ak

@@ -215,8 +215,20 @@ cudaError_t learned_launch(const RadixCall &c, const LearnedCall &lc) {
         cudaSuccess)
       return e;
   }
-  lm_table_kernel<<<1, 1024, 0, c.stream>>>(lc.model, lc.train_steps > 0 ? 1 : 0, lc.nbuckets, lc.bucket_bits,
-                                            fallback);
+  // the bucket table: the piecewise-linear CDF alone, or with the trained
+  // residual when that gives the sorted sample a strictly smaller largest
+  // bucket (the loss is a mean; the sort pays for the largest bucket)
+  const float *xs_v = VBYTES ? lc.xs_v : nullptr;
+  const int rg = int(std::min<int64_t>((lc.m + 255) / 256, int64_t(sms) * 8));
+  lm_table_kernel<<<1, 1024, 0, c.stream>>>(lc.model, 0, lc.nbuckets, lc.bucket_bits, fallback);
+  lm_sample_runs_kernel<<<rg, 256, 0, c.stream>>>(lc.xs, xs_v, lc.m, lc.model, 0, fallback);
+  if (lc.train_steps > 0) {
+    lm_table_kernel<<<1, 1024, 0, c.stream>>>(lc.model, 1, lc.nbuckets, lc.bucket_bits, fallback);
+    lm_sample_runs_kernel<<<rg, 256, 0, c.stream>>>(lc.xs, xs_v, lc.m, lc.model, 1, fallback);
+  }
+  lm_pick_kernel<<<1, 1, 0, c.stream>>>(lc.model, c.hdr, fallback);
+  if (lc.train_steps > 0)  // the table of the choice (the PL one was overwritten)
+    lm_table_kernel<<<1, 1024, 0, c.stream>>>(lc.model, 2, lc.nbuckets, lc.bucket_bits, fallback);
   // 4. bucket histogram, plan, learned passes (all skip themselves on fallback)
   switch (c.val_bytes) {
     case 0: e = lm_passes_s<U, uint32_t, false, KIND>(c, lc); break;

@@ -590,8 +590,11 @@ struct SegCta {
   }
 };
 
+// Two CTAs per SM: the register cap (64) spills a few hundred bytes in the
+// kernels with values, and still beats one CTA per SM at their ~100 registers
+// (learned sortperm / pairs of 2^28 int64 keys 5-10% faster, keys-only 14%).
 template <typename U, typename V, bool HAS_V, int KIND, int BLOCK, int ITEMS, int CAP>
-__global__ void __launch_bounds__(BLOCK) segsort_kernel(SegArgs<U, V> a) {
+__global__ void __launch_bounds__(BLOCK, 2) segsort_kernel(SegArgs<U, V> a) {
   using C = SegCta<U, V, HAS_V, KIND, BLOCK, ITEMS, CAP>;
   if (a.gate && *a.gate != a.gate_want) return;
   extern __shared__ __align__(128) uint8_t smem[];

@@ -143,8 +143,28 @@ def test_mlp_residual_gain_over_piecewise_linear(ak):
         assert_bits_equal(to_host(t, np.float64), np.sort(keys), "pareto sort")
     pl, mlp = res[-1], res[64]
     assert mlp["loss_after"] < mlp["loss_before"], mlp
+    # the sample chose the residual: its largest sample bucket is strictly smaller
+    assert mlp["mlp_used"] == 1 and 0 < mlp["sample_max_mlp"] < mlp["sample_max_pl"], mlp
+    assert pl["mlp_used"] == 0 and pl["sample_max_mlp"] == 0 and pl["sample_max_pl"] > 0, pl
     assert mlp["max_bucket"] < pl["max_bucket"], (mlp, pl)
     assert mlp["max_bucket"] < 0.75 * pl["max_bucket"], (mlp["max_bucket"], pl["max_bucket"])
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal", "lognormal"])
+def test_mlp_table_choice_follows_the_sample(ak, dist):
+    """The bucket table keeps the trained residual only when it strictly
+    shrinks the sorted sample's largest bucket; either way the sort is exact."""
+    n = 1 << 22
+    keys = synth.dist_f64(n, dist, seed=10 + synth.F64_DISTS.index(dist))
+    opts = _learned(ak, train_steps=32)
+    t, _ = to_dev(keys)
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, n, ak.AK_F64, options=opts), t.device)
+    ak.ak_sort(t, temp=temp, options=opts)
+    info = ak.ak_last_info(temp)
+    assert info["path"] == ak.AK_PATH_LEARNED, info
+    assert info["sample_max_pl"] > 0 and info["sample_max_mlp"] > 0, info
+    assert info["mlp_used"] == (1 if info["sample_max_mlp"] < info["sample_max_pl"] else 0), info
+    assert_bits_equal(to_host(t, np.float64), np.sort(keys), f"{dist} sort")
 
 
 def test_auto_takes_learned_for_large_64bit_keys(ak):
