@@ -123,3 +123,21 @@ def test_refused_operations(ak):
     assert rc == 2
     x = torch.zeros((10, 2), dtype=torch.int64, device="cuda")
     assert lib.ak_accumulate(x.data_ptr(), x.data_ptr(), 10, ak.AK_I128, 0, 1, None, None, 0, None, None) == 2
+
+
+@pytest.mark.slow
+def test_int128_large_properties(ak):
+    """2^26 signed 128-bit keys (1 GiB) over all bit patterns: the sorted keys
+    are in order and the same multiset; the sortperm is a permutation listing
+    them in order with ties (none expected) by index; keys[perm] == sorted."""
+    n = 1 << 26
+    lo, hi = synth.splitmix64(9500, n), synth.splitmix64(9501, n)
+    k = oracle.int128_from_words(lo, hi)
+    t = _dev(k)
+    perm = ak.ak_sortperm(t, wide=True).cpu().numpy().view(np.uint32).astype(np.int64)
+    ak.ak_sort(t, wide=True)
+    s = t.cpu().numpy().view(np.uint64)
+    sl, sh = s[:, 0], s[:, 1].view(np.int64)
+    assert np.all((sh[1:] > sh[:-1]) | ((sh[1:] == sh[:-1]) & (sl[1:] >= sl[:-1])))
+    assert np.array_equal(np.bincount(perm, minlength=n), np.ones(n, dtype=np.int64))
+    assert np.array_equal(sl, lo[perm]) and np.array_equal(s[:, 1], hi[perm])

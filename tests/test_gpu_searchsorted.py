@@ -186,3 +186,22 @@ def test_mixed_sorted_and_unsorted_tiles(ak):
             vv = oracle.sort(v, order)
             got = _search(ak, vv, x, side, order)
             np.testing.assert_array_equal(got, oracle.searchsorted(vv, x, side, order), err_msg=f"{side} {order}")
+
+
+@pytest.mark.slow
+def test_full_size_ascending_queries_sampled(ak):
+    """The benchmark's ascending shape: 2^24 ascending float64 queries in 2^27
+    ascending keys (1 GiB): every tile takes the shared-window path; 20,000
+    sampled answers against the oracle, every answer in range and monotone."""
+    n, m = 1 << 27, 1 << 24
+    v = synth.ascending_f64(n, seed=40)
+    x = synth.ascending_f64(m, seed=93)
+    x *= v[-1] / x[-1]
+    tv, tx = torch.from_numpy(v).cuda(), torch.from_numpy(x).cuda()
+    first = ak.ak_searchsortedfirst(tv, tx).cpu().numpy()
+    last = ak.ak_searchsortedlast(tv, tx).cpu().numpy()
+    pick = (synth.splitmix64(94, 20_000) % np.uint64(m)).astype(np.int64)
+    np.testing.assert_array_equal(first[pick], oracle.searchsorted(v, x[pick], "first"))
+    np.testing.assert_array_equal(last[pick], oracle.searchsorted(v, x[pick], "last"))
+    assert first.min() >= 0 and first.max() <= n and last.min() >= -1 and last.max() <= n - 1
+    assert np.all(np.diff(first) >= 0) and np.all(np.diff(last) >= 0)
