@@ -24,7 +24,7 @@
 // Sorted tiles: the answers of the tile lie between those of its first and
 // last query.  Those two come from the table and then a 256-way search by
 // half of the CTA each (a round of 256 independent loads narrows a stretch
-// 257-fold: two rounds for 2^27 keys); the keys of v between them are read
+// 257-fold: two rounds for 2^27 keys; SS_HALF-way in general); the keys of v between them are read
 // once, coalesced, into a 64 KB shared window, chunk after chunk, and each
 // query bisects the chunk that holds its answer.  v is then read about once
 // over all the tiles: HBM bound instead of latency bound.  A stretch above
@@ -43,9 +43,12 @@
 namespace ak {
 
 constexpr int SS_BLOCK = 512;
+constexpr int SS_MIN_BLOCKS = 2;            // CTAs per SM the registers are sized for
 constexpr int SS_TABLE_BYTES = 16384;
 constexpr int SS_TILE = 4096;               // queries per CTA iteration
 constexpr int SS_WINDOW_BYTES = 65536;      // shared window of v for a sorted tile
+constexpr int SS_HALF = SS_BLOCK / 2;       // probes per round of a tile-bound search
+constexpr int SS_PARTS = SS_HALF + 1;       // a round narrows a stretch SS_PARTS-fold
 constexpr int SS_WINDOW_CHUNKS = 8;         // windows a sorted tile reads before it bisects in global memory
 
 template <typename U>
@@ -101,7 +104,7 @@ __device__ __forceinline__ int64_t ss_bisect_global(const U *__restrict__ v, U f
 }
 
 template <typename U, int KIND, bool LAST>
-__global__ void __launch_bounds__(SS_BLOCK, 2) searchsorted_kernel(const U *__restrict__ v, int64_t n,
+__global__ void __launch_bounds__(SS_BLOCK, SS_MIN_BLOCKS) searchsorted_kernel(const U *__restrict__ v, int64_t n,
                                                                    const U *__restrict__ x, int64_t m, U flip, int K,
                                                                    int64_t *__restrict__ out) {
   constexpr int WINDOW = SS_WINDOW_BYTES / int(sizeof(U));
@@ -134,9 +137,9 @@ __global__ void __launch_bounds__(SS_BLOCK, 2) searchsorted_kernel(const U *__re
       }
       continue;
     }
-    // answers of the first and last query: table, then 256-way rounds (threads
-    // 0..255 for the first, 256..511 for the last)
-    const int g = tid >> 8, j = tid & 255;
+    // answers of the first and last query: table, then SS_HALF-way rounds (the
+    // first half of the threads for the first query, the second for the last)
+    const int g = tid / SS_HALF, j = tid % SS_HALF;
     const U gkey = s_x[g ? cnt - 1 : 0];
     if (j == 0) {
       int64_t lo, hi;
@@ -151,9 +154,10 @@ __global__ void __launch_bounds__(SS_BLOCK, 2) searchsorted_kernel(const U *__re
       const bool live = len > 0;
       bool p = false;
       if (live) {
-        // len <= 256: probe every key; else 256 probes at a + floor((j+1) len / 257)
-        const int64_t pos = len <= 256 ? a + j : a + ((j + 1) * len) / 257;
-        if (len > 256 || j < len) p = ss_in_prefix<LAST>(radix_key_t<KIND>(v[pos], flip), gkey);
+        // len <= SS_HALF: probe every key; else SS_HALF probes at
+        // a + floor((j+1) len / SS_PARTS), strictly increasing, all below a + len
+        const int64_t pos = len <= SS_HALF ? a + j : a + ((j + 1) * len) / SS_PARTS;
+        if (len > SS_HALF || j < len) p = ss_in_prefix<LAST>(radix_key_t<KIND>(v[pos], flip), gkey);
       }
       const uint32_t b = __ballot_sync(0xffffffffu, p);
       if (lane == 0 && b) atomicAdd(&s_cnt[g], __popc(b));
@@ -161,12 +165,12 @@ __global__ void __launch_bounds__(SS_BLOCK, 2) searchsorted_kernel(const U *__re
       if (!any_live) break;
       if (j == 0 && live) {  // probes 0..c-1 are in the prefix, probe c is not
         const int c = s_cnt[g];
-        if (len <= 256) {
+        if (len <= SS_HALF) {
           s_lo[g] = a + c;
           s_hi[g] = a + c;
         } else {
-          const int64_t nlo = c == 0 ? a : a + (int64_t(c) * len) / 257 + 1;
-          const int64_t nhi = c == 256 ? a + len : a + (int64_t(c + 1) * len) / 257;
+          const int64_t nlo = c == 0 ? a : a + (int64_t(c) * len) / SS_PARTS + 1;
+          const int64_t nhi = c == SS_HALF ? a + len : a + (int64_t(c + 1) * len) / SS_PARTS;
           s_lo[g] = nlo;
           s_hi[g] = nhi;
         }
