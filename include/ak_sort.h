@@ -94,7 +94,7 @@ typedef enum ak_path {
 typedef struct ak_options {
     int32_t path;          /* ak_path */
     int32_t tile_config;   /* digit-pass variant, 0 = default (1), else 1..AK_TILE_CONFIGS:
-                              1 persistent 512-thread CTAs, 32 KB tiles; 2 persistent
+                              1 persistent 512-thread CTAs, 40 KB tiles; 2 persistent
                               384-thread CTAs, 24 KB tiles; 3 one 512-thread CTA per
                               32 KB tile with an L2 prefetch one wave ahead; 4 persistent
                               512-thread CTAs whose last warp does the look-back while
