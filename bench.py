@@ -43,7 +43,7 @@ NOMINAL_HBM_GBS = 8000.0
 # (keys per array, bytes per launch).  Traffic grows in proportion to the keys,
 # so it is scaled to the run's n.  None whenever the digit-pass kernel has
 # changed since the counters were taken.
-NCU_TRAFFIC = None
+NCU_TRAFFIC = (67_108_864, 1_087_983_722)  # profiles/onesweep_pass_traffic_67M.md
 
 
 def parse_args():
