@@ -77,6 +77,41 @@ def test_pairs_match_oracle(ak, dtype, vdtype, desc):
     assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), "pair values")
 
 
+def _default_tile(kb, vb):
+    """Keys per tile of the default configuration: 512 threads, about 40 KB of
+    keys+values per tile, 2..12 keys per thread."""
+    return 512 * min(max(40960 // (512 * (kb + vb)), 2), 12)
+
+
+@pytest.mark.parametrize("dtype", [np.uint16, np.int32, np.float32, np.int64, np.float64])
+@pytest.mark.parametrize("vdtype", [None, np.uint8, np.uint32, np.uint64])
+def test_default_config_tile_boundaries(ak, dtype, vdtype):
+    """The default configuration (40 KB tiles): sort, sortperm and pairs at one
+    tile -1/0/+1 and many tiles with a ragged tail, both orders, on keys with
+    long runs of equal digits."""
+    kb = np.dtype(dtype).itemsize
+    vb = 0 if vdtype is None else np.dtype(vdtype).itemsize
+    tile = _default_tile(kb, vb if vdtype is not None else 0)
+    ptile = _default_tile(kb, 4)  # sortperm carries u32 indices
+    rad = {"path": ak.AK_PATH_RADIX}
+    for n in sorted({tile - 1, tile, tile + 1, ptile - 1, ptile + 1, 37 * tile + 11}):
+        keys = synth.random_keys(n, dtype, seed=7300 + n + kb, mode="dups" if n % 2 else "bits")
+        for desc in (False, True):
+            order = "descending" if desc else "ascending"
+            p = oracle_perm(keys, desc)
+            if vdtype is None:
+                assert_bits_equal(_run_sort(ak, keys, desc, rad), oracle.gather(keys, p), f"sort n={n}")
+                assert np.array_equal(_run_perm(ak, keys, desc, rad), p.astype(np.uint32)), f"sortperm n={n}"
+            else:
+                vals = synth.splitmix64(7301, n).astype(vdtype)
+                kt, ku = to_dev(keys)
+                vt, _ = to_dev(vals)
+                ak.ak_sort_pairs(kt, vt, order, options=rad, unsigned=ku)
+                torch.cuda.synchronize()
+                assert_bits_equal(to_host(kt, keys.dtype), oracle.gather(keys, p), f"pair keys n={n}")
+                assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), f"pair values n={n}")
+
+
 @pytest.mark.parametrize("cfg", [1, 2, 3, 4])
 @pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float32, np.uint16])
 def test_every_tile_config(ak, cfg, dtype):
