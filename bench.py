@@ -895,10 +895,11 @@ def run_int128(args, torch, ak, synth, dev, stream, flush, peak):
 
 def run_accumulate(args, torch, ak, synth, dev, stream, flush, peak):
     """Inclusive + scan (Sec. II-B accumulate) of 268,435,456 int64 keys (2 GiB
-    in, 2 GiB out) and of the same bits as float64.  value = bytes read and
-    written per second by the scan kernel (the HBM roofline's own units)."""
+    in, 2 GiB out; --n another size) and of the same bits as float64.  value =
+    algorithmic bytes (read once, written once) per second of the whole scan,
+    its three launches together (the HBM roofline's own units)."""
     import oracle
-    n = 1 << 28
+    n = args.n if args.n != FULL_N else 1 << 28
     xh = synth.uniform_i64(n, seed=117)
     x = torch.from_numpy(xh).to(dev)
     out = torch.empty_like(x)
