@@ -44,6 +44,9 @@ NOMINAL_HBM_GBS = 8000.0
 # so it is scaled to the run's n.  None whenever the digit-pass kernel has
 # changed since the counters were taken.
 NCU_TRAFFIC = (67_108_864, 1_087_983_722)  # profiles/onesweep_pass_traffic_67M.md
+# ncu DRAM read + write bytes of one int64 accumulate call (keys, bytes), from
+# profiles/scan_kernels_accumulate_268M_launch_list.md
+ACC_NCU_TRAFFIC = (268_435_456, 6_404_700_000)
 
 
 def parse_args():
@@ -931,7 +934,11 @@ def run_accumulate(args, torch, ak, synth, dev, stream, flush, peak):
           gbs, {"metric": "accumulate GB/s read + written (device-timed, 1 GB300)", "dtype": "i64",
                 "results": res,
                 "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                             "frac": round(gbs / peak, 4), "traffic": None},
+                             "frac": round(gbs / peak, 4),
+                             # DRAM bytes of one int64 call (reduce + carry + scan launches),
+                             # scaled from the 2^28-key launch list to this n
+                             "traffic": int(ACC_NCU_TRAFFIC[1] * n / ACC_NCU_TRAFFIC[0]),
+                             "traffic_per": "call (3 launches; the input is read twice by design)"},
                 "cpu_baseline": cpu})
 
 
