@@ -43,9 +43,8 @@ NOMINAL_HBM_GBS = 8000.0
 # (keys per array, bytes per launch).  Traffic grows in proportion to the keys,
 # so it is scaled to the run's n.  None whenever the digit-pass kernel has
 # changed since the counters were taken.
-NCU_TRAFFIC = (67_108_864, 1_087_983_722)  # profiles/onesweep_pass_traffic_67M.md
-# ncu DRAM read + write bytes of one int64 accumulate call (keys, bytes), from
-# profiles/scan_kernels_accumulate_268M_launch_list.md
+NCU_TRAFFIC = (67_108_864, 1_087_983_722)
+# ncu DRAM read + write bytes of one int64 accumulate call (keys, bytes)
 ACC_NCU_TRAFFIC = (268_435_456, 6_404_700_000)
 
 
@@ -62,7 +61,8 @@ def parse_args():
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "searchsorted", "accumulate", "int128"],
                     help="c2 (default): the headline line; the others print their own lines")
     ap.add_argument("--segments", type=int, default=65536, help="c4: number of segments")
-    ap.add_argument("--tile-config", type=int, default=0, help="c2: digit-pass tile configuration (0 = default)")
+    ap.add_argument("--tile-config", type=int, default=0, choices=range(0, 6),
+                    help="c2: digit-pass tile configuration (0 = default = 1; 5 = reduce-then-scan)")
     return ap.parse_args()
 
 
@@ -472,9 +472,11 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     achieved = sum(pass_bytes) / (sum(pass_ms) / 1e3) / 1e9
     traffic = None
-    if NCU_TRAFFIC is not None:
+    if NCU_TRAFFIC is not None and args.tile_config in (0, 1):  # counters of the default configuration
         traffic = int(NCU_TRAFFIC[1] * n / NCU_TRAFFIC[0])
-    roofline = {"bound": "hbm", "kernel": "onesweep_pass", "achieved": round(achieved, 1), "peak": peak,
+    # tile configuration 5: each timed pass is the upsweep count plus the chunk-ordered pass
+    kname = "chunk_hist_kernel + onesweep_pass" if args.tile_config == 5 else "onesweep_pass"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": f"{peak_kind} (copy, burst)", "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "launches": len(pass_ms),
                 "avg_launch_ms": round(sum(pass_ms) / len(pass_ms), 4),
@@ -557,7 +559,7 @@ def run_ours(args):
         cpu = {"value": round(rate, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                "sample": f"first {sample:,} keys of each array, sortperm + sort each (threaded merge sort), {dt:.1f} s"}
 
-    launches_per_step = sum(3 + (8 if i == 0 else 4) for _, i in calls)
+    launches_per_step = sum(3 + (8 if i == 0 else 4) * (2 if args.tile_config == 5 else 1) for _, i in calls)
     if rank == 0:
         line = base_line(args, world, cfg)
         line.update({"value": round(value, 3), "ms_per_step": round(total_ms / args.steps, 4),
@@ -896,19 +898,44 @@ def run_int128(args, torch, ak, synth, dev, stream, flush, peak):
                   "literal_2x_key_bytes_frac_of_measured": round(2 * value / peak, 4)})
 
 
+def check_scan_i64(x, out):
+    """Inclusive + of int64 keys: out[0] = x[0] and out[i] - out[i-1] = x[i],
+    both in wrapping int64 arithmetic (exact)."""
+    with np.errstate(over="ignore"):
+        return bool(out[0] == x[0] and np.array_equal(out[1:] - out[:-1], x[1:]))
+
+
+def check_scan_f64(x, out):
+    """Inclusive + of float64 keys: consecutive outputs differ by the key up to
+    the sum of both outputs' rounding bounds, gamma_D * sum |x_j| over each
+    prefix with D = 8 + 2 ceil(n / 2^18) + 84 the depth of the scan's summation
+    tree (8 keys per lane, 2^18 keys per warp range), plus an ulp of each output
+    (a dropped, repeated or misplaced key moves the difference by the key)."""
+    u = np.finfo(np.float64).eps / 2
+    depth = 8 + 2 * -(-x.size // (32768 * 8)) + 84
+    bound = (depth * u / (1 - depth * u)) * np.cumsum(np.abs(x)) + np.spacing(np.abs(out))
+    ok0 = abs(out[0] - x[0]) <= bound[0]
+    d = np.abs((out[1:] - out[:-1]) - x[1:])
+    return bool(ok0 and np.all(d <= bound[1:] + bound[:-1]))
+
+
 def run_accumulate(args, torch, ak, synth, dev, stream, flush, peak):
     """Inclusive + scan (Sec. II-B accumulate) of 268,435,456 int64 keys (2 GiB
-    in, 2 GiB out; --n another size) and of the same bits as float64.  value =
-    algorithmic bytes (read once, written once) per second of the whole scan,
-    its three launches together (the HBM roofline's own units)."""
+    in, 2 GiB out; --n another size) and of as many float64 keys ~ N(0, 1).
+    value = algorithmic bytes (read once, written once) per second of the
+    whole scan, its three launches together (the HBM roofline's own units).
+    Both outputs of the last timed call are checked on the host."""
     import oracle
     n = args.n if args.n != FULL_N else 1 << 28
     xh = synth.uniform_i64(n, seed=117)
-    x = torch.from_numpy(xh).to(dev)
-    out = torch.empty_like(x)
+    xf = synth.dist_f64(n, "normal", seed=118)
     lib = ak.load()
     res = {}
-    for name, kd in (("i64_add", ak.AK_I64), ("f64_add", ak.AK_F64)):
+    checked = {}
+    for name, kd, host, check in (("i64_add", ak.AK_I64, xh, check_scan_i64),
+                                  ("f64_add", ak.AK_F64, xf, check_scan_f64)):
+        x = torch.from_numpy(host).to(dev)
+        out = torch.empty_like(x)
         temp = ak.workspace(ak.accumulate_temp_bytes(n, kd), dev)
 
         def call(kd=kd, temp=temp):
@@ -920,7 +947,11 @@ def run_accumulate(args, torch, ak, synth, dev, stream, flush, peak):
         ms = _timed(torch, stream, flush, lambda: None, call, args.warmup, args.steps)
         if ak.ak_status_check(temp) != 0:
             raise RuntimeError("ak_accumulate: device status not clean")
+        checked[name] = check(host, out.cpu().numpy())
+        if not checked[name]:
+            raise RuntimeError(f"output check failed: accumulate {name}")
         res[name] = {"ms": round(ms, 4), "GBps": round(2 * n * 8 / (ms / 1e3) / 1e9, 1)}
+        del x, out, temp
     gbs = res["i64_add"]["GBps"]
     cpu = None
     if not args.no_cpu:
@@ -930,9 +961,10 @@ def run_accumulate(args, torch, ak, synth, dev, stream, flush, peak):
         dt = time.perf_counter() - t0
         cpu = {"value": round(2 * sample * 8 / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"inclusive + over the first {sample:,} int64 keys"}
-    _line(args, f"{n:,} int64 keys, inclusive + scan (ak_accumulate), out of place; float64 on the same bits alongside",
+    _line(args, f"{n:,} int64 keys uniform over all bit patterns, inclusive + scan (ak_accumulate), out of place; "
+                f"{n:,} float64 keys ~ N(0, 1) alongside",
           gbs, {"metric": "accumulate GB/s read + written (device-timed, 1 GB300)", "dtype": "i64",
-                "results": res,
+                "results": res, "output_checked": checked,
                 "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                              "frac": round(gbs / peak, 4),
                              # DRAM bytes of one int64 call (reduce + carry + scan launches),

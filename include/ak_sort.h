@@ -98,7 +98,13 @@ typedef struct ak_options {
                               384-thread CTAs, 24 KB tiles; 3 one 512-thread CTA per
                               32 KB tile with an L2 prefetch one wave ahead; 4 persistent
                               512-thread CTAs whose last warp does the look-back while
-                              the others rank the next tile (three tile buffers) */
+                              the others rank the next tile (three tile buffers); 5 the
+                              reduce-then-scan form of 1 (three-kernel scheme instead of
+                              onesweep): per pass an upsweep kernel counts the digits of
+                              each chunk of consecutive tiles, then one CTA per chunk
+                              sorts its tiles in order from running digit offsets, with no
+                              look-back (one more read of the keys per pass; above 2^30
+                              keys it runs as 1) */
     int32_t bucket_bits;   /* learned path: log2 of the bucket count, 8..16 (NaN keys share
                               the last bucket); 0 = auto, about half the shared-memory
                               finish capacity (ak_segment_capacity) per bucket */
@@ -126,13 +132,14 @@ typedef struct ak_options {
 /* Test hook: no CTA owns the first tile of any radix pass, so every
  * look-back that reaches it waits until
  * timeout_ns and the call ends with AK_ERR_TIMEOUT (the output is then
- * unspecified).  Exercises the bounded-wait error path. */
+ * unspecified).  Exercises the bounded-wait error path.  Tile configuration 5
+ * has no look-back and ignores it. */
 #define AK_DEBUG_SKIP_FIRST_TILE 1
 /* Tuning hook: no L2 prefetch one wave ahead in tile configuration 3 (the
  * persistent configurations prefetch each claimed tile, unaffected). */
 #define AK_DEBUG_NO_PREFETCH 2
 
-#define AK_TILE_CONFIGS 4
+#define AK_TILE_CONFIGS 5
 
 /* Diagnostics written by the device for the most recent call on a d_temp. */
 typedef struct ak_info {
@@ -191,7 +198,7 @@ ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype 
  * per-tile counters, where ak_sortperm needs 2 n * key bytes more).  Every
  * digit pass moves only the indices and reads each key through its index from
  * d_keys, so the passes after the first gather keys from anywhere in d_keys
- * (slower than ak_sortperm).  Always the radix path; tile_config 4 runs as 1.
+ * (slower than ak_sortperm).  Always the radix path; tile_config 4 and 5 run as 1.
  * Arguments, errors and limits as ak_sortperm.
  */
 ak_status ak_sortperm_lowmem(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,

@@ -22,7 +22,7 @@ AK_I128, AK_U128 = 10, 11  # 128-bit keys: int64 tensors of shape (n, 2), [low w
 AK_ASCENDING, AK_DESCENDING = 0, 1
 AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED, AK_OP_SORTPERM_LOWMEM = range(5)
 AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK, AK_PATH_MERGE = range(5)
-AK_TILE_CONFIGS = 4
+AK_TILE_CONFIGS = 5
 AK_DEBUG_SKIP_FIRST_TILE = 1
 AK_MAX_PASSES = 16
 STATUS_NAMES = {0: "AK_OK", 1: "AK_ERR_INVALID_ARG", 2: "AK_ERR_UNSUPPORTED",

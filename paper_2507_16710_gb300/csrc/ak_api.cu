@@ -66,7 +66,7 @@ static bool path_supported(const KeyInfo &ki, const ak_options &o) {
 
 // Workspace of the radix path.
 struct RadixLayout {
-  size_t hdr, counts, plan, status0, status1, k_alt0, k_alt1, v_alt, total;
+  size_t hdr, counts, plan, status0, status1, chunk, k_alt0, k_alt1, v_alt, total;
   int status_wide;
 };
 
@@ -88,6 +88,10 @@ static RadixLayout radix_layout(int op, int64_t n, int key_bytes, int val_bytes,
   off += align256(size_t(tiles) * RADIX * sw);
   L.status1 = off;
   off += align256(size_t(tiles) * RADIX * sw);
+  if (op != AK_OP_SORTPERM_LOWMEM) {  // digit counts per chunk of the reduce-then-scan configuration
+    L.chunk = off;
+    off += align256(size_t(tiles < RTS_MAX_CHUNKS ? tiles : RTS_MAX_CHUNKS) * RADIX * 4);
+  }
   if (op != AK_OP_SORTPERM_LOWMEM) {  // the low-memory sortperm keeps no key copy
     L.k_alt0 = off;
     off += align256(size_t(n) * key_bytes);
@@ -518,12 +522,13 @@ static ak_status run_radix(int op, const void *k_in, void *k_final, const void *
   c.kind = ki.kind;
   c.descending = order == AK_DESCENDING;
   c.tile_config = (o.tile_config >= 1 && o.tile_config <= AK_TILE_CONFIGS) ? o.tile_config - 1 : CFG_DEFAULT;
-  if (lowmem && c.tile_config == CFG_WS) c.tile_config = 0;
+  if (lowmem && (c.tile_config == CFG_WS || c.tile_config == CFG_RTS)) c.tile_config = 0;
   c.hdr = reinterpret_cast<DevHeader *>(t + L.hdr);
   c.counts = reinterpret_cast<unsigned long long *>(t + L.counts);
   c.plan = reinterpret_cast<RadixPlan *>(t + L.plan);
   c.status[0] = t + L.status0;
   c.status[1] = t + L.status1;
+  c.chunk_cnt = lowmem ? nullptr : reinterpret_cast<uint32_t *>(t + L.chunk);
   c.status_wide = L.status_wide;
   c.timeout_ns = o.timeout_ns;
   c.path_tag = AK_PATH_RADIX;

@@ -31,6 +31,7 @@ struct RadixCall {
   unsigned long long *counts;  // MAX_PASSES * RADIX
   RadixPlan *plan;
   void *status[2];         // look-back words, each num_tiles * RADIX
+  uint32_t *chunk_cnt;     // reduce-then-scan passes: RTS_MAX_CHUNKS * RADIX digit counts
   int status_wide;         // 64-bit look-back words (n > 2^30)
   uint64_t timeout_ns;
   int path_tag;            // written to ak_info.path (0 = leave)
@@ -68,11 +69,18 @@ cudaError_t radix_launch_u128_sint(const RadixCall &c);
 // two CTAs per SM.  Configuration 0 (the default) takes 40 KB tiles, the most
 // whose stage and digit-order buffers still fit two CTAs per SM for 8-byte
 // keys (10 keys per thread): against 32 KB tiles a pass of int64 keys is 9%
-// faster, sortperm and 32-bit pairs 10-12%.
-constexpr int CFG_BLOCK[4] = {512, 384, 512, 512};
-constexpr int CFG_BYTES[4] = {40960, 24576, 32768, 0};
-constexpr bool CFG_PERSIST[4] = {true, true, false, true};
+// faster, sortperm and 32-bit pairs 10-12%.  Configuration 4 is the
+// reduce-then-scan form of configuration 0's tile: an upsweep kernel counts
+// each chunk's digits, then one CTA per chunk sorts its consecutive tiles in
+// order with running digit offsets and no look-back (onesweep.cuh: RTS).
+constexpr int CFG_BLOCK[5] = {512, 384, 512, 512, 512};
+constexpr int CFG_BYTES[5] = {40960, 24576, 32768, 0, 40960};
+constexpr bool CFG_PERSIST[5] = {true, true, false, true, true};
 constexpr int CFG_WS = 3;
+constexpr int CFG_RTS = 4;
+// Chunks of a reduce-then-scan pass: one per resident CTA, at most this many
+// (the workspace holds their digit counts).
+constexpr int RTS_MAX_CHUNKS = 1024;
 // Configuration of tile_config 0 (the default) and of the learned path's passes.
 constexpr int CFG_DEFAULT = 0;
 
@@ -115,7 +123,9 @@ constexpr int tile_items(int key_bytes, int val_bytes, int cfg) {
 constexpr int tile_keys(int key_bytes, int val_bytes, int cfg) {
   return (cfg == CFG_WS ? WS_NC : CFG_BLOCK[cfg]) * tile_items(key_bytes, val_bytes, cfg);
 }
-// 64-bit look-back words (n > 2^30) are built for configurations 0 and 3.
+// 64-bit look-back words (n > 2^30) are built for configurations 0 and 3; the
+// reduce-then-scan configuration keeps 32-bit destinations, so above 2^30 keys
+// it runs as configuration 0 too.
 constexpr int effective_cfg(int cfg, bool status_wide) { return status_wide && cfg != CFG_WS ? 0 : cfg; }
 
 // Keys of one segment the shared-memory sort takes (a multiple of 32): 80 KB

@@ -73,6 +73,8 @@ struct PassArgs {
   const uint32_t *gate;       // if set, run only when *gate == gate_want
   uint32_t gate_want;
   int64_t prefetch_ahead;     // one-tile CTAs: L2-prefetch the tile this many ids ahead (0: off)
+  uint32_t *chunk_cnt;        // reduce-then-scan passes: digit counts of each chunk [chunk][RADIX]
+  int64_t tiles_per_chunk;    // reduce-then-scan passes: consecutive tiles of one chunk (one CTA)
 };
 
 // Digit of a key in a pass: a radix digit, a byte of the learned bucket id
@@ -241,11 +243,17 @@ constexpr int LOOKBACK_WINDOW = AK_LOOKBACK_WINDOW;  // predecessor words probed
 // gives digit starts and warp bases; (3) scatter into the output buffer in
 // digit order; (4) decoupled look-back, inclusive counts published (flag INC);
 // (5) write-out: consecutive threads store consecutive slots of a digit run.
+//
+// RTS (reduce-then-scan, after chunk_hist_kernel): CTA c sorts the tiles of
+// chunk c in increasing order; its digit offsets are the counts of chunks
+// 0..c-1 plus, tile after tile, the counts of its own earlier tiles, held in a
+// register of the digit's thread.  Nothing is published and no CTA waits on
+// another.
 // CTAs per SM the register budget is sized for (2 x 512, 3 x 384 threads).
 constexpr int pass_min_blocks(int block) { return block >= 512 ? 2 : (block >= 384 ? 3 : 4); }
 
 template <typename U, typename V, bool HAS_V, int KIND, typename S, int BLOCK, int ITEMS, bool PERSIST,
-          int DIGIT = DIGIT_RADIX>
+          int DIGIT = DIGIT_RADIX, bool RTS = false>
 __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(PassArgs<U, V> a) {
   using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
   constexpr int TILE = L::TILE;
@@ -255,6 +263,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   static_assert(BLOCK >= RADIX, "one digit per thread in the scan and look-back");
   static_assert(DIGIT != DIGIT_VALUE || HAS_V, "a value-carried digit needs the value stream");
   static_assert(DIGIT != DIGIT_GATHER || HAS_V, "gathered keys need the index stream");
+  static_assert(!RTS || (PERSIST && DIGIT == DIGIT_RADIX), "reduce-then-scan: persistent radix passes");
   constexpr bool GATHER = DIGIT == DIGIT_GATHER;  // keys are read through the index, never moved
   extern __shared__ __align__(128) uint8_t smem[];
   U *sk = reinterpret_cast<U *>(smem);
@@ -339,9 +348,16 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   for (int i = tid; i < NW * HROW; i += BLOCK) wmask[i] = 0u;
   for (int i = tid; i < HROW * L::HSTRIDE; i += BLOCK) whist32[i] = 0u;
   int64_t next_tile = 0;  // CLAIMER: the tile claimed for the next iteration
+  // RTS: this CTA's chunk of tiles [rts_first, rts_end)
+  const int64_t rts_first = RTS ? (int64_t(blockIdx.x) * a.tiles_per_chunk < a.num_tiles
+                                       ? int64_t(blockIdx.x) * a.tiles_per_chunk : a.num_tiles)
+                                : 0;
+  const int64_t rts_end = RTS ? (rts_first + a.tiles_per_chunk < a.num_tiles ? rts_first + a.tiles_per_chunk
+                                                                              : a.num_tiles)
+                              : 0;
   if (tid == 0) {
     mbar_init(bar, 1);
-    const int64_t t = claim();
+    const int64_t t = RTS ? rts_first : claim();
     *s_next = (long long)t;
     issue(t);
     // one-tile CTAs: pull the tile about one residency wave ahead into L2 so
@@ -356,6 +372,22 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   const uint32_t gt_mask = ~(lt_mask | (1u << lane));
   uint32_t *wm = wmask + warp * HROW;
   S *st = reinterpret_cast<S *>(a.status_cur);
+  // RTS: keys of digit tid in chunks before this one, then in this chunk's
+  // tiles so far (independent loads, 32 in flight per round)
+  unsigned long long run = 0;
+  if constexpr (RTS) {
+    if (tid < RADIX) {
+      constexpr int UNR = 32;
+      const int64_t nc = blockIdx.x;
+      for (int64_t c0 = 0; c0 < nc; c0 += UNR) {
+        uint32_t v[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) v[j] = (c0 + j < nc) ? a.chunk_cnt[(c0 + j) * RADIX + tid] : 0u;
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) run += v[j];
+      }
+    }
+  }
 
   for (;;) {
     const int64_t tile = *s_next;  // written by thread 0 before barriers B and C of the previous tile
@@ -426,7 +458,8 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           const uint32_t w = hrow[v];
           my_cnt += (w & 0xFFFFu) + (w >> 16);
         }
-        st_relaxed(&st[tile * RADIX + tid], (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt));
+        if constexpr (!RTS)
+          st_relaxed(&st[tile * RADIX + tid], (S(tile == 0 ? FLAG_INC : FLAG_AGG) << StatusWord<S>::SHIFT) | S(my_cnt));
         inc = warp_inclusive_scan(my_cnt);
         if (lane == 31) s_scr[warp] = inc;
       }
@@ -435,7 +468,10 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
       // the next tile is claimed only now (a claimed tile whose counts are not
       // yet published would hold up every later tile's look-back); the claim's
       // round trip overlaps the scan and scatter
-      if (PERSIST && tid == CLAIMER) next_tile = claim();
+      if (PERSIST && tid == CLAIMER) {
+        if constexpr (RTS) next_tile = tile + 1 < rts_end ? tile + 1 : a.num_tiles;
+        else next_tile = claim();
+      }
       uint32_t start = 0;
       if (tid < RADIX) {
         start = inc - my_cnt;
@@ -517,7 +553,13 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
       __syncthreads();  // B: warp bases ready
       scatter();
       if (tid < RADIX) {
-        const unsigned long long excl = lookback(tid, my_cnt);
+        unsigned long long excl;
+        if constexpr (RTS) {
+          excl = run;
+          run += my_cnt;
+        } else {
+          excl = lookback(tid, my_cnt);
+        }
         s_delta[tid] = Delta((long long)(a.plan->bin_off[a.pass][tid] + excl) - (long long)start);
       }
       if (PERSIST && tid == CLAIMER) {
@@ -567,6 +609,66 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   }
   // a copy left in flight by a timed-out wait must land before the CTA exits
   if (tid == 0 && pending) mbar_wait_bounded(bar, phase, a.timeout_ns);
+}
+
+// --------------------------------------------------- reduce-then-scan upsweep
+// Digit counts of one pass over one chunk (tiles_per_chunk consecutive tiles,
+// the range one CTA of the following reduce-then-scan pass sorts in order).
+// The pass then needs no look-back: chunk c's keys of digit d start after the
+// keys of smaller digits (the plan's bin offsets) and after chunks 0..c-1's
+// keys of digit d, and inside the chunk its CTA keeps a running count per
+// digit from tile to tile.
+template <typename U, typename V, int KIND, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) chunk_hist_kernel(PassArgs<U, V> a, int tile_keys) {
+  if (a.gate && *a.gate != a.gate_want) return;
+  const uint32_t q = a.plan->q[a.pass];
+  if (q == INACTIVE) return;
+  // the keys this active pass reads (the pass's own choice of source buffer)
+  const U *ksrc = (q == 0) ? a.k_in : ((q & 1) ? a.k_alt0 : (a.mode == MODE_INPLACE ? a.k_final : a.k_alt1));
+  constexpr int NSUB = BLOCK / 64;  // one sub-histogram per pair of warps
+  __shared__ uint32_t h[NSUB][RADIX];
+  for (int i = threadIdx.x; i < NSUB * RADIX; i += BLOCK) (&h[0][0])[i] = 0u;
+  __syncthreads();
+  const int64_t b = int64_t(blockIdx.x) * a.tiles_per_chunk * tile_keys;
+  int64_t e = b + a.tiles_per_chunk * tile_keys;
+  if (e > a.n) e = a.n;
+  uint32_t *hh = h[threadIdx.x >> 6];
+  const int shift = a.pass * RADIX_BITS;
+  auto count = [&](U k) { atomicAdd(&hh[radix_digit<KIND>(k, a.flip, shift)], 1u); };
+  if (b < e && (reinterpret_cast<uintptr_t>(ksrc + b) & 15) == 0) {
+    constexpr int PER = 16 / sizeof(U);
+    constexpr int UNR = 4;  // 64 bytes in flight per thread
+    const int64_t nvec = (e - b) / PER;
+    const uint4 *vk = reinterpret_cast<const uint4 *>(ksrc + b);
+    int64_t i = threadIdx.x;
+    for (; i + (UNR - 1) * BLOCK < nvec; i += UNR * BLOCK) {
+      uint4 x[UNR];
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) x[j] = __ldg(vk + i + j * BLOCK);
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        const U *el = reinterpret_cast<const U *>(&x[j]);
+#pragma unroll
+        for (int t = 0; t < PER; ++t) count(el[t]);
+      }
+    }
+    for (; i < nvec; i += BLOCK) {
+      const uint4 x = __ldg(vk + i);
+      const U *el = reinterpret_cast<const U *>(&x);
+#pragma unroll
+      for (int t = 0; t < PER; ++t) count(el[t]);
+    }
+    for (int64_t k = b + nvec * PER + threadIdx.x; k < e; k += BLOCK) count(ksrc[k]);
+  } else {
+    for (int64_t k = b + threadIdx.x; k < e; k += BLOCK) count(ksrc[k]);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RADIX; d += BLOCK) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int s2 = 0; s2 < NSUB; ++s2) c += h[s2][d];
+    a.chunk_cnt[int64_t(blockIdx.x) * RADIX + d] = c;
+  }
 }
 
 // --------------------------------------------------------------------- finish

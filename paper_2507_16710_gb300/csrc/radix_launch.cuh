@@ -48,6 +48,7 @@ struct PassKernel {
   static constexpr size_t BYTES = bytes();
   static auto kernel() {
     if constexpr (CFG == CFG_WS) return onesweep_ws_pass<U, V, HAS_V, KIND, S, ITEMS, DIGIT, AK_WS_RANK>;
+    else if constexpr (CFG == CFG_RTS) return onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, true, DIGIT, true>;
     else return onesweep_pass<U, V, HAS_V, KIND, S, BLOCK, ITEMS, PERSIST, DIGIT>;
   }
   static_assert(CFG == CFG_WS ? WsSmem<U, V, HAS_V, ITEMS, AK_WS_RANK>::TILE == TILE
@@ -69,11 +70,11 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
   a.num_tiles = tiles;
   constexpr int PASSES = sizeof(U);
   const int sms = device_sm_count();
-  {  // histogram + zero the first pass's look-back words
+  {  // histogram + zero the first pass's look-back words (reduce-then-scan passes have none)
     constexpr int HB = 256;
     const int64_t want = (c.n + HB * 16 - 1) / (HB * 16);
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 8)));
-    const int64_t zero_vec = tiles * RADIX * int64_t(sizeof(S)) / 16;
+    const int64_t zero_vec = CFG == CFG_RTS ? 0 : tiles * RADIX * int64_t(sizeof(S)) / 16;
     hist_kernel<U, HB><<<grid, HB, 0, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, c.kind, a.flip,
                                                    c.counts, reinterpret_cast<uint4 *>(c.status[0]), zero_vec,
                                                    c.gate, c.gate_want);
@@ -83,6 +84,24 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
   const int64_t resident = PERSIST ? wave : tiles;
   const unsigned grid = unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, resident)));
   a.prefetch_ahead = (PERSIST || (c.debug_flags & AK_DEBUG_NO_PREFETCH)) ? 0 : wave;
+  if constexpr (CFG == CFG_RTS) {
+    // one chunk of consecutive tiles per resident CTA: upsweep counts, then the
+    // chunk-ordered pass (every CTA of the wave is resident, none waits on another)
+    const int64_t want = std::max<int64_t>(1, std::min<int64_t>({tiles, wave, int64_t(RTS_MAX_CHUNKS)}));
+    a.tiles_per_chunk = (tiles + want - 1) / want;
+    const int64_t chunks = std::max<int64_t>(1, (tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk);
+    a.chunk_cnt = c.chunk_cnt;
+    a.debug_skip = 0;  // no look-back to starve
+    for (int p = 0; p < PASSES; ++p) {
+      a.pass = p;
+      a.status_cur = nullptr;
+      a.status_next = nullptr;
+      if (c.pass_events) cudaEventRecord(reinterpret_cast<cudaEvent_t>(c.pass_events[2 * p]), c.stream);
+      chunk_hist_kernel<U, V, KIND, 512><<<unsigned(chunks), 512, 0, c.stream>>>(a, TILE);
+      kern<<<unsigned(chunks), BLOCK, BYTES, c.stream>>>(a);
+      if (c.pass_events) cudaEventRecord(reinterpret_cast<cudaEvent_t>(c.pass_events[2 * p + 1]), c.stream);
+    }
+  } else
   for (int p = 0; p < PASSES; ++p) {
     a.pass = p;
     a.status_cur = c.status[p & 1];
@@ -147,6 +166,7 @@ cudaError_t run_status(const RadixCall &c) {
     case 1: return run_passes<U, V, HAS_V, KIND, uint32_t, 1>(c, a);
     case 2: return run_passes<U, V, HAS_V, KIND, uint32_t, 2>(c, a);
     case CFG_WS: return run_passes<U, V, HAS_V, KIND, uint32_t, CFG_WS>(c, a);
+    case CFG_RTS: return run_passes<U, V, HAS_V, KIND, uint32_t, CFG_RTS>(c, a);
     default: return run_passes<U, V, HAS_V, KIND, uint32_t, 0>(c, a);
   }
   }

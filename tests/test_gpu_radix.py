@@ -112,7 +112,7 @@ def test_default_config_tile_boundaries(ak, dtype, vdtype):
                 assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), f"pair values n={n}")
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 4])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float32, np.uint16])
 def test_every_tile_config(ak, cfg, dtype):
     opts = {"tile_config": cfg, "path": ak.AK_PATH_RADIX}
@@ -173,6 +173,67 @@ def test_lookback_warp_config_many_tiles_per_cta(ak, dtype):
     ak.ak_sort_pairs(kt, vt, options=opts, unsigned=ku)
     torch.cuda.synchronize()
     assert np.array_equal(to_host(vt, np.uint32), p.astype(np.uint32)), "ws pairs, many tiles"
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("vdtype", [None, np.uint8, np.uint16, np.uint32, np.uint64])
+def test_reduce_then_scan_config_tile_boundaries(ak, dtype, vdtype):
+    """Tile configuration 5 (upsweep counts per chunk, then chunk-ordered
+    passes without look-back): sort, sortperm and pairs of every value width,
+    both orders, one tile -1/0/+1, several tiles with a ragged tail, on heavy
+    duplicates and on all bit patterns."""
+    opts = {"tile_config": 5, "path": ak.AK_PATH_RADIX}
+    kb = np.dtype(dtype).itemsize
+    vb = 0 if vdtype is None else np.dtype(vdtype).itemsize
+    tile = _default_tile(kb, vb)
+    ptile = _default_tile(kb, 4)  # sortperm carries u32 indices
+    sizes = {tile - 1, tile, tile + 1, 37 * tile + 11} | ({ptile - 1, ptile + 1} if vdtype is None else set())
+    for n in sorted(sizes):
+        keys = synth.random_keys(n, dtype, seed=7500 + n + kb, mode="dups" if n % 2 else "bits")
+        for desc in (False, True):
+            order = "descending" if desc else "ascending"
+            p = oracle_perm(keys, desc)
+            if vdtype is None:
+                assert_bits_equal(_run_sort(ak, keys, desc, opts), oracle.gather(keys, p), f"rts sort n={n}")
+                assert np.array_equal(_run_perm(ak, keys, desc, opts), p.astype(np.uint32)), f"rts sortperm n={n}"
+            else:
+                vals = synth.splitmix64(7501, n).astype(vdtype)
+                kt, ku = to_dev(keys)
+                vt, _ = to_dev(vals)
+                ak.ak_sort_pairs(kt, vt, order, options=opts, unsigned=ku)
+                torch.cuda.synchronize()
+                assert_bits_equal(to_host(kt, keys.dtype), oracle.gather(keys, p), f"rts pair keys n={n}")
+                assert_bits_equal(to_host(vt, vals.dtype), oracle.gather(vals, p), f"rts pair values n={n}")
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.int64, np.float32, np.float64, np.uint16])
+def test_reduce_then_scan_config_many_tiles_per_chunk(ak, dtype):
+    """Tile configuration 5 where every chunk holds several tiles (5M keys: a
+    CTA carries its running digit offsets across tiles, chunks fewer than a
+    wave after rounding) and where the key pointer is off 16-byte alignment
+    (the upsweep and the pass fall back to plain loads)."""
+    opts = {"tile_config": 5, "path": ak.AK_PATH_RADIX}
+    n = 5_000_003
+    keys = synth.random_keys(n, dtype, seed=7600, mode="bits")
+    for desc in (False, True):
+        p = oracle_perm(keys, desc, threads=8)
+        assert_bits_equal(_run_sort(ak, keys, desc, opts), oracle.gather(keys, p), "rts sort, many tiles")
+        assert np.array_equal(_run_perm(ak, keys, desc, opts), p.astype(np.uint32)), "rts sortperm, many tiles"
+    vals = np.arange(n, dtype=np.uint32)
+    p = oracle_perm(keys, False, threads=8)
+    kt, ku = to_dev(keys)
+    vt, _ = to_dev(vals)
+    ak.ak_sort_pairs(kt, vt, options=opts, unsigned=ku)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(vt, np.uint32), p.astype(np.uint32)), "rts pairs, many tiles"
+    base = synth.random_keys(2_000_001, dtype, seed=7601, mode="dups")
+    t, u = to_dev(base)
+    sub = t[1:]
+    ak.ak_sort(sub, options=opts, unsigned=u)
+    torch.cuda.synchronize()
+    assert_bits_equal(to_host(sub, base.dtype), oracle.gather(base[1:], oracle_perm(base[1:], False, threads=8)),
+                      "rts unaligned")
+    assert_bits_equal(to_host(t, base.dtype)[:1], base[:1], "rts unaligned: the element before is untouched")
 
 
 def test_trivial_passes_and_all_equal(ak):
@@ -302,7 +363,7 @@ def test_sortperm_lowmem_matches_oracle(ak, dtype, desc):
 def test_sortperm_lowmem_configs_unaligned_and_many_tiles(ak):
     keys = synth.random_keys(3_000_001, np.float64, seed=9100, mode="bits")
     want = oracle_perm(keys, False, threads=8).astype(np.uint32)
-    for cfg in (0, 1, 2, 3, 4):
+    for cfg in (0, 1, 2, 3, 4, 5):
         t, _ = to_dev(keys)
         p = ak.ak_sortperm_lowmem(t, options={"tile_config": cfg})
         torch.cuda.synchronize()
