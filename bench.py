@@ -151,14 +151,23 @@ def gpu_target(torch, dev: int):
         return vis.split(",")[dev] if vis else str(dev)
 
 
-def onesweep_bytes(op: str, n: int, w: int, passes: int) -> list[int]:
-    """Algorithmic bytes of each digit pass (the dominant kernel) of one call."""
+def onesweep_bytes(op: str, n: int, w: int, passes: int, packed: bool = False) -> list[int]:
+    """Algorithmic bytes of each digit pass (the dominant kernel) of one call,
+    every pass active.  packed: a sortperm of 8-byte keys whose upper-half
+    passes move (upper key half, index) words of 8 bytes."""
     if op == "sort":
         return [2 * n * w] * passes
     out = []
+    half = passes // 2
     for q in range(passes):
         if q == 0:
             out.append(2 * n * w + 4 * n)          # read keys, write keys + generated index
+        elif packed and q == half - 1:
+            out.append(n * w + 4 * n + 8 * n)      # read keys + index, write packed words
+        elif packed and q == passes - 1:
+            out.append(8 * n + 4 * n)              # read packed words, write the index
+        elif packed and q >= half:
+            out.append(16 * n)                     # packed words in and out
         elif q == passes - 1:
             out.append(n * w + 8 * n)              # read keys + perm, write perm only
         else:
@@ -452,7 +461,8 @@ def run_ours(args):
             torch.cuda.synchronize(dev)  # pass events are reused by the next call
             evs.append((e0, e1))
             npass = a["w"]
-            pb = onesweep_bytes(op, n, a["w"], npass)
+            packed = a["w"] == 8 and args.tile_config in (0, 1) and n <= (1 << 30)
+            pb = onesweep_bytes(op, n, a["w"], npass, packed)
             for p in range(npass):
                 pass_ms.append(pass_ev[2 * p].elapsed_time(pass_ev[2 * p + 1]))
                 pass_bytes.append(pb[p] if passes[(op, i)] == npass else 0)
@@ -559,7 +569,12 @@ def run_ours(args):
         cpu = {"value": round(rate, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                "sample": f"first {sample:,} keys of each array, sortperm + sort each (threaded merge sort), {dt:.1f} s"}
 
-    launches_per_step = sum(3 + (8 if i == 0 else 4) * (2 if args.tile_config == 5 else 1) for _, i in calls)
+    def pass_launches(op, i):
+        w = 8 if i == 0 else 4
+        if op == "sortperm" and w == 8 and args.tile_config in (0, 1) and n <= (1 << 30):
+            return 2 * w + w // 2  # plain and packing variant per pass, packed-word variant in the upper half
+        return w * (2 if args.tile_config == 5 else 1)  # tile configuration 5: upsweep + pass
+    launches_per_step = sum(3 + pass_launches(op, i) for op, i in calls)
     if rank == 0:
         line = base_line(args, world, cfg)
         line.update({"value": round(value, 3), "ms_per_step": round(total_ms / args.steps, 4),

@@ -138,6 +138,11 @@ typedef struct ak_options {
 /* Tuning hook: no L2 prefetch one wave ahead in tile configuration 3 (the
  * persistent configurations prefetch each claimed tile, unaffected). */
 #define AK_DEBUG_NO_PREFETCH 2
+/* Tuning hook: ak_sortperm of 8-byte keys moves key and index through every
+ * digit pass, instead of packing the upper half of the key and the index into
+ * one 8-byte word for the passes of the upper key half (the default for tile
+ * configuration 1 up to 2^30 keys).  The permutation is the same. */
+#define AK_DEBUG_NO_PACK 4
 
 #define AK_TILE_CONFIGS 5
 

@@ -24,6 +24,8 @@ AK_OP_SORT, AK_OP_SORTPERM, AK_OP_SORT_PAIRS, AK_OP_SORT_SEGMENTED, AK_OP_SORTPE
 AK_PATH_AUTO, AK_PATH_RADIX, AK_PATH_LEARNED, AK_PATH_BLOCK, AK_PATH_MERGE = range(5)
 AK_TILE_CONFIGS = 5
 AK_DEBUG_SKIP_FIRST_TILE = 1
+AK_DEBUG_NO_PREFETCH = 2
+AK_DEBUG_NO_PACK = 4
 AK_MAX_PASSES = 16
 STATUS_NAMES = {0: "AK_OK", 1: "AK_ERR_INVALID_ARG", 2: "AK_ERR_UNSUPPORTED",
                 3: "AK_ERR_WORKSPACE_TOO_SMALL", 4: "AK_ERR_CUDA", 5: "AK_ERR_TIMEOUT",

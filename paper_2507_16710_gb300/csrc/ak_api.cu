@@ -121,7 +121,7 @@ bool resolve_options(const ak_options *opt, ak_options *o) {
   if (o->tile_config < 0 || o->tile_config > AK_TILE_CONFIGS) return false;
   if (o->bucket_bits != 0 && (o->bucket_bits < 8 || o->bucket_bits > 16)) return false;
   if (o->train_steps < -1) return false;
-  if (o->debug_flags & ~(AK_DEBUG_SKIP_FIRST_TILE | AK_DEBUG_NO_PREFETCH)) return false;
+  if (o->debug_flags & ~(AK_DEBUG_SKIP_FIRST_TILE | AK_DEBUG_NO_PREFETCH | AK_DEBUG_NO_PACK)) return false;
   if (o->digit_bits != 0 && o->digit_bits != RADIX_BITS) return false;
   if (o->split_caps < -1 || o->split_caps > 1024) return false;
   for (int r : o->reserved)

@@ -31,11 +31,21 @@ constexpr uint32_t INACTIVE = 0xFFFFFFFFu;
 struct RadixPlan {
   uint32_t m;                    // passes that move data
   uint32_t q[MAX_PASSES];        // active index of each pass, or INACTIVE
+  uint32_t fmt[MAX_PASSES];      // packed sortperm of 8-byte keys: the data format of each pass (PassFormat)
   uint32_t pad[7];
   unsigned long long bin_off[MAX_PASSES][RADIX];  // exclusive digit offsets
 };
 
 enum SortMode : int { MODE_INPLACE = 0, MODE_PERM = 1 };
+
+// What a sortperm pass of 8-byte keys reads and writes.  Once the passes of
+// the low 32 key bits are done, the sort needs only the upper 32 bits of each
+// radix key, and those and the 32-bit index fit one 8-byte word.  So the last
+// active pass of the low half writes (upper radix-key half << 32 | index)
+// words (PACK_OUT) and the passes of the upper half move those 8-byte words
+// alone, keys only, and the last one writes the index (PACKED_IN): 16 instead
+// of 24 bytes per key and pass.  PLAIN: key and index, as every other sort.
+enum PassFormat : int { FMT_PLAIN = 0, FMT_PACK_OUT = 1, FMT_PACKED_IN = 2 };
 
 // Look-back status word: 2 flag bits over a 30-bit (u32) or 62-bit (u64) count.
 template <typename S> struct StatusWord;
@@ -75,6 +85,7 @@ struct PassArgs {
   int64_t prefetch_ahead;     // one-tile CTAs: L2-prefetch the tile this many ids ahead (0: off)
   uint32_t *chunk_cnt;        // reduce-then-scan passes: digit counts of each chunk [chunk][RADIX]
   int64_t tiles_per_chunk;    // reduce-then-scan passes: consecutive tiles of one chunk (one CTA)
+  int fmt_check;              // packed sortperm: run only when plan->fmt[pass] is this kernel's format
 };
 
 // Digit of a key in a pass: a radix digit, a byte of the learned bucket id
@@ -129,7 +140,8 @@ __global__ void __launch_bounds__(BLOCK) hist_kernel(const U *__restrict__ keys,
 // One CTA of RADIX threads.
 static __global__ void __launch_bounds__(RADIX) plan_kernel(const unsigned long long *counts, int64_t n,
                                                      int passes, RadixPlan *plan, DevHeader *hdr,
-                                                     int path_tag, const uint32_t *gate, uint32_t gate_want) {
+                                                     int path_tag, const uint32_t *gate, uint32_t gate_want,
+                                                     int pack_half = 0) {
   if (gate && *gate != gate_want) return;
   __shared__ unsigned long long scratch[RADIX / 32 + 1];
   __shared__ int triv[MAX_PASSES];
@@ -147,6 +159,28 @@ static __global__ void __launch_bounds__(RADIX) plan_kernel(const unsigned long 
     uint32_t m = 0;
     for (int p = 0; p < MAX_PASSES; ++p) plan->q[p] = (p < passes && !triv[p]) ? m++ : INACTIVE;
     plan->m = m;
+    // packed sortperm (pack_half = passes of the low half): the last active
+    // pass below pack_half packs, every active pass above it reads packed
+    // words.  With no active low pass the first active upper pass packs,
+    // unless it is the only one (then it writes the index directly).
+    for (int p = 0; p < MAX_PASSES; ++p) plan->fmt[p] = FMT_PLAIN;
+    if (pack_half > 0) {
+      int low_last = -1, first_high = -1, last_active = -1;
+      for (int p = 0; p < passes; ++p) {
+        if (triv[p]) continue;
+        last_active = p;
+        if (p < pack_half) low_last = p;
+        else if (first_high < 0) first_high = p;
+      }
+      if (first_high >= 0) {
+        const int start = low_last >= 0 ? low_last : (first_high != last_active ? first_high : -1);
+        if (start >= 0) {
+          plan->fmt[start] = FMT_PACK_OUT;
+          for (int p = start + 1; p < passes; ++p)
+            if (!triv[p]) plan->fmt[p] = FMT_PACKED_IN;
+        }
+      }
+    }
     hdr->info.radix_passes = int32_t(m);
     if (path_tag) hdr->info.path = path_tag;
   }
@@ -253,7 +287,7 @@ constexpr int LOOKBACK_WINDOW = AK_LOOKBACK_WINDOW;  // predecessor words probed
 constexpr int pass_min_blocks(int block) { return block >= 512 ? 2 : (block >= 384 ? 3 : 4); }
 
 template <typename U, typename V, bool HAS_V, int KIND, typename S, int BLOCK, int ITEMS, bool PERSIST,
-          int DIGIT = DIGIT_RADIX, bool RTS = false>
+          int DIGIT = DIGIT_RADIX, bool RTS = false, int FMT = FMT_PLAIN>
 __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(PassArgs<U, V> a) {
   using L = PassSmem<U, V, HAS_V, BLOCK, ITEMS>;
   constexpr int TILE = L::TILE;
@@ -264,6 +298,9 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   static_assert(DIGIT != DIGIT_VALUE || HAS_V, "a value-carried digit needs the value stream");
   static_assert(DIGIT != DIGIT_GATHER || HAS_V, "gathered keys need the index stream");
   static_assert(!RTS || (PERSIST && DIGIT == DIGIT_RADIX), "reduce-then-scan: persistent radix passes");
+  static_assert(FMT == FMT_PLAIN || (sizeof(U) == 8 && std::is_same<V, uint32_t>::value && !RTS &&
+                                     DIGIT == DIGIT_RADIX && HAS_V == (FMT == FMT_PACK_OUT)),
+                "packed sortperm: 8-byte keys, u32 indices");
   constexpr bool GATHER = DIGIT == DIGIT_GATHER;  // keys are read through the index, never moved
   extern __shared__ __align__(128) uint8_t smem[];
   U *sk = reinterpret_cast<U *>(smem);
@@ -283,6 +320,8 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   uint8_t *s_dig = smem + L::OFF_DIG;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (a.gate && *a.gate != a.gate_want) return;
+  // packed sortperm: the variants of a pass are all launched; the plan's one runs
+  if (a.fmt_check && a.plan->fmt[a.pass] != uint32_t(FMT)) return;
 
   // Clear the next pass's look-back rows (the grid covers rows blockIdx.x + k*gridDim.x).
   if (a.status_next) {
@@ -368,6 +407,11 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
   __syncthreads();
 
   const int shift = a.pass * RADIX_BITS;
+  // FMT_PACK_OUT: the upper half of the radix key over the index
+  auto pack_word = [&](U k, V idx) -> U {
+    if constexpr (sizeof(U) == 8) return U((uint64_t(radix_key_t<KIND>(k, a.flip)) & 0xFFFFFFFF00000000ull) | uint64_t(idx));
+    else return k;
+  };
   const uint32_t lt_mask = lanemask_lt();
   const uint32_t gt_mask = ~(lt_mask | (1u << lane));
   uint32_t *wm = wmask + warp * HROW;
@@ -589,16 +633,26 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks(BLOCK)) onesweep_pass(P
           }
 #pragma unroll
           for (int r = 0; r < WB; ++r) {
-            if (write_keys) kdst[dst[r]] = k[r];
-            if (HAS_V) vdst[dst[r]] = ov[(r0 + r) * BLOCK + tid];
+            if constexpr (FMT == FMT_PACK_OUT) {
+              kdst[dst[r]] = pack_word(k[r], ov[(r0 + r) * BLOCK + tid]);
+            } else {
+              if (write_keys) kdst[dst[r]] = k[r];
+              else if constexpr (FMT == FMT_PACKED_IN) a.v_final[dst[r]] = V(k[r]);  // the index half
+              if (HAS_V) vdst[dst[r]] = ov[(r0 + r) * BLOCK + tid];
+            }
           }
         }
       } else {
         for (int i = tid; i < tile_n; i += BLOCK) {
           const U k = GATHER ? U(0) : ok[i];
           const long long dst = (long long)s_delta[s_dig[i]] + i;
-          if (write_keys) kdst[dst] = k;
-          if (HAS_V) vdst[dst] = ov[i];
+          if constexpr (FMT == FMT_PACK_OUT) {
+            kdst[dst] = pack_word(k, ov[i]);
+          } else {
+            if (write_keys) kdst[dst] = k;
+            else if constexpr (FMT == FMT_PACKED_IN) a.v_final[dst] = V(k);
+            if (HAS_V) vdst[dst] = ov[i];
+          }
         }
       }
     };

@@ -118,6 +118,71 @@ cudaError_t run_passes(const RadixCall &c, PassArgs<U, V> a) {
   return cudaGetLastError();
 }
 
+// Sortperm of 8-byte keys in the default configuration with 32-bit look-back
+// words: every pass launches the plain kernel and the packing one, and the
+// passes of the upper key half also the kernel over packed words; the plan
+// kernel says which format each pass has (onesweep.cuh: PassFormat) and only
+// that variant runs, the others return at once.
+template <typename U, int KIND>
+cudaError_t run_passes_packed(const RadixCall &c, PassArgs<U, uint32_t> a) {
+  using V = uint32_t;
+  using P1 = PassKernel<U, V, true, KIND, uint32_t, CFG_DEFAULT>;   // key + index
+  using P3 = PassKernel<U, V, false, KIND_UINT, uint32_t, CFG_DEFAULT>;  // packed words (tile shape)
+  constexpr int BLOCK = P1::BLOCK;
+  static_assert(P1::PERSIST && P3::BLOCK == BLOCK, "persistent default configuration");
+  auto k1 = P1::kernel();
+  auto k2 = onesweep_pass<U, V, true, KIND, uint32_t, BLOCK, P1::ITEMS, true, DIGIT_RADIX, false, FMT_PACK_OUT>;
+  auto k3 = onesweep_pass<U, V, false, KIND_UINT, uint32_t, BLOCK, P3::ITEMS, true, DIGIT_RADIX, false, FMT_PACKED_IN>;
+  cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(P1::BYTES));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(P1::BYTES));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, int(P3::BYTES));
+  if (e != cudaSuccess) return e;
+  constexpr int PASSES = sizeof(U);
+  const int64_t tiles1 = (c.n + P1::TILE - 1) / P1::TILE;  // the larger count: its rows cover both shapes
+  const int64_t tiles3 = (c.n + P3::TILE - 1) / P3::TILE;
+  const int sms = device_sm_count();
+  {
+    constexpr int HB = 256;
+    const int64_t want = (c.n + HB * 16 - 1) / (HB * 16);
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 8)));
+    const int64_t zero_vec = tiles1 * RADIX * int64_t(sizeof(uint32_t)) / 16;
+    hist_kernel<U, HB><<<grid, HB, 0, c.stream>>>(reinterpret_cast<const U *>(c.k_in), c.n, c.kind, a.flip,
+                                                   c.counts, reinterpret_cast<uint4 *>(c.status[0]), zero_vec,
+                                                   c.gate, c.gate_want);
+  }
+  plan_kernel<<<1, RADIX, 0, c.stream>>>(c.counts, c.n, PASSES, c.plan, c.hdr, c.path_tag, c.gate, c.gate_want,
+                                         PASSES / 2);
+  const unsigned g1 = unsigned(std::max<int64_t>(
+      1, std::min<int64_t>(tiles1, int64_t(resident_ctas(k1, BLOCK, P1::BYTES)) * sms)));
+  const unsigned g2 = unsigned(std::max<int64_t>(
+      1, std::min<int64_t>(tiles1, int64_t(resident_ctas(k2, BLOCK, P1::BYTES)) * sms)));
+  const unsigned g3 = unsigned(std::max<int64_t>(
+      1, std::min<int64_t>(tiles3, int64_t(resident_ctas(k3, BLOCK, P3::BYTES)) * sms)));
+  a.num_tiles = tiles1;
+  a.prefetch_ahead = 0;
+  a.fmt_check = 1;
+  PassArgs<U, V> a3 = a;  // packed words: already transformed (no flip), unsigned digits
+  a3.flip = U(0);
+  a3.kind = KIND_UINT;
+  a3.num_tiles = tiles3;
+  for (int p = 0; p < PASSES; ++p) {
+    a.pass = a3.pass = p;
+    a.status_cur = a3.status_cur = c.status[p & 1];
+    a.status_next = a3.status_next = (p + 1 < PASSES) ? c.status[(p + 1) & 1] : nullptr;
+    if (c.pass_events) cudaEventRecord(reinterpret_cast<cudaEvent_t>(c.pass_events[2 * p]), c.stream);
+    k1<<<g1, BLOCK, P1::BYTES, c.stream>>>(a);
+    k2<<<g2, BLOCK, P1::BYTES, c.stream>>>(a);
+    if (p >= PASSES / 2) k3<<<g3, BLOCK, P3::BYTES, c.stream>>>(a3);
+    if (c.pass_events) cudaEventRecord(reinterpret_cast<cudaEvent_t>(c.pass_events[2 * p + 1]), c.stream);
+  }
+  {
+    const int64_t want = (c.n + 1023) / 1024;
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 4)));
+    finish_kernel<U, V, true><<<g, 256, 0, c.stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 template <typename U, typename V, bool HAS_V, int KIND>
 cudaError_t run_status(const RadixCall &c) {
   PassArgs<U, V> a{};
@@ -148,6 +213,11 @@ cudaError_t run_status(const RadixCall &c) {
     if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, CFG_DEFAULT>(c, a);
     return run_passes<U, V, HAS_V, KIND, uint32_t, CFG_DEFAULT>(c, a);
   } else {
+  if constexpr (HAS_V && std::is_same<V, uint32_t>::value && sizeof(U) == 8) {
+    if (c.mode == MODE_PERM && !c.gather && !c.status_wide && c.tile_config == CFG_DEFAULT &&
+        !(c.debug_flags & AK_DEBUG_NO_PACK))
+      return run_passes_packed<U, KIND>(c, a);
+  }
   if constexpr (HAS_V && std::is_same<V, uint32_t>::value) {
     if (c.gather) {  // low-memory sortperm: the shared-memory-staged configurations only
       if (c.status_wide) return run_passes<U, V, HAS_V, KIND, unsigned long long, 0, DIGIT_GATHER>(c, a);

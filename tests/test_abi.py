@@ -74,11 +74,12 @@ def test_options_out_of_range_are_refused(lib):
         return lib.ak_sort_temp_bytes(ak.AK_OP_SORT, 1 << 20, ak.AK_F64, 0, 0, ctypes.byref(o), ctypes.byref(out))
 
     for good in ({}, {"path": ak.AK_PATH_MERGE}, {"tile_config": 3}, {"tile_config": 4}, {"tile_config": 5}, {"bucket_bits": 8}, {"bucket_bits": 16},
-                 {"train_steps": -1}, {"debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE | 2}, {"timeout_ns": 5},
+                 {"train_steps": -1}, {"debug_flags": ak.AK_DEBUG_SKIP_FIRST_TILE | 2}, {"debug_flags": ak.AK_DEBUG_NO_PACK},
+                 {"timeout_ns": 5},
                  {"digit_bits": 8}, {"split_caps": -1}, {"split_caps": 1}, {"split_caps": 1024}):
         assert query(**good) == 0, good
     for bad in ({"path": 5}, {"path": -1}, {"tile_config": 6}, {"tile_config": -1}, {"bucket_bits": 7}, {"bucket_bits": 17},
-                {"train_steps": -2}, {"debug_flags": 4}, {"digit_bits": 11}, {"digit_bits": 4},
+                {"train_steps": -2}, {"debug_flags": 8}, {"digit_bits": 11}, {"digit_bits": 4},
                 {"split_caps": -2}, {"split_caps": 1025}):
         assert query(**bad) == 1, bad
     o = ak.Options()

@@ -49,3 +49,24 @@ def test_checks_reject_planted_mistakes():
     assert not bench.check_perm(keys, r.astype(np.uint32))
     # a permutation whose gather disagrees with the returned keys
     assert not bench.check_perm(keys, p.astype(np.uint32), sorted_out=dup)
+
+
+def test_scan_checks_accept_the_oracle_and_reject_planted_mistakes():
+    """The accumulate workload's output checks: the oracle's inclusive + passes
+    both; a dropped key, a repeated key and two swapped outputs fail."""
+    x = synth.uniform_i64(50_021, seed=117)
+    good = oracle.accumulate(x, "add")
+    assert bench.check_scan_i64(x, good)
+    dropped = good.copy()
+    with np.errstate(over="ignore"):
+        dropped[300:] -= x[300]
+    assert not bench.check_scan_i64(x, dropped)
+    xf = synth.dist_f64(50_021, "normal", seed=118)
+    gf = oracle.accumulate(xf, "add")
+    assert bench.check_scan_f64(xf, gf)
+    rep = gf.copy()
+    rep[7000:] += xf[6999]  # key 6999 counted twice
+    assert not bench.check_scan_f64(xf, rep)
+    sw = gf.copy()
+    sw[[40, 41]] = sw[[41, 40]]
+    assert not bench.check_scan_f64(xf, sw)

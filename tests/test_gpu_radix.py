@@ -236,6 +236,67 @@ def test_reduce_then_scan_config_many_tiles_per_chunk(ak, dtype):
     assert_bits_equal(to_host(t, base.dtype)[:1], base[:1], "rts unaligned: the element before is untouched")
 
 
+def _packed_patterns(n, dtype, seed):
+    """8-byte keys whose active digit passes fall in every arrangement the
+    packed sortperm plans for: all passes; only the upper half (the first
+    upper pass packs); one upper pass alone (no packing); one lower and one
+    upper pass; only the lower half (no upper pass); special values."""
+    r = synth.splitmix64(seed, n)
+    u = np.dtype(dtype)
+    bits = {
+        "all": r,
+        # floats: positive and finite, so the radix key's lower half stays zero
+        "upper_only": r & np.uint64(0x3FFFFFFF00000000 if u.kind == "f" else 0xFFFFFFFF00000000),
+        "one_upper": (r & np.uint64(0x0000FF0000000000)) | np.uint64(0x4010000000000000),
+        "one_lower_one_upper": (r & np.uint64(0x00FF0000000000FF)) | np.uint64(0x3FF0000000000000),
+        "lower_only": (r & np.uint64(0x00000000FFFFFFFF)) | np.uint64(0x4000000000000000),
+        "dups": r % np.uint64(7) << np.uint64(37),
+    }
+    out = {k: v.view(u) for k, v in bits.items()}
+    if u.kind == "f":
+        out["specials"] = np.resize(synth.special_values(dtype), n)
+    return out
+
+
+@pytest.mark.parametrize("dtype", [np.int64, np.uint64, np.float64])
+@pytest.mark.parametrize("desc", [False, True])
+def test_sortperm_packed_upper_passes(ak, dtype, desc):
+    """ak_sortperm of 8-byte keys packs (upper radix-key half, index) into one
+    word for the passes of the upper half: the permutation equals the oracle's
+    for every arrangement of active passes, across both tile shapes (3,072
+    keys with an index, 5,120 packed words), and equals the unpacked run
+    (AK_DEBUG_NO_PACK)."""
+    rad = {"path": ak.AK_PATH_RADIX}
+    nopack = {"path": ak.AK_PATH_RADIX, "debug_flags": ak.AK_DEBUG_NO_PACK}
+    for n in (1, 2, 3071, 3073, 5119, 5121, 200_003):
+        for name, keys in _packed_patterns(n, dtype, seed=8800 + n).items():
+            want = oracle_perm(keys, desc).astype(np.uint32)
+            got = _run_perm(ak, keys, desc, rad)
+            assert np.array_equal(got, want), (name, n)
+            if n == 200_003:
+                assert np.array_equal(_run_perm(ak, keys, desc, nopack), want), (name, n, "no pack")
+
+
+@pytest.mark.parametrize("dtype", [np.int64, np.float64])
+def test_sortperm_packed_many_tiles_per_cta(ak, dtype):
+    """Packed sortperm with several tiles per persistent CTA in both tile
+    shapes (5M keys), all passes active and upper half only, and the info
+    block's pass count."""
+    n = 5_000_003
+    pats = _packed_patterns(n, dtype, seed=8900)
+    for name in ("all", "upper_only"):
+        keys = pats[name]
+        want = oracle_perm(keys, False, threads=8).astype(np.uint32)
+        t, u = to_dev(keys)
+        rad = {"path": ak.AK_PATH_RADIX}
+        temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORTPERM, n, ak.AK_I64, options=rad), t.device)
+        p = ak.ak_sortperm(t, temp=temp, options=rad, unsigned=u)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(p, np.uint32), want), name
+        assert ak.ak_status_check(temp) == 0
+        assert ak.ak_last_info(temp)["radix_passes"] == (8 if name == "all" else 4)
+
+
 def test_trivial_passes_and_all_equal(ak):
     # every key equal: all passes trivial; sortperm must be the identity
     keys = np.full(70000, 7, dtype=np.int64)
