@@ -224,18 +224,19 @@ __global__ void iota_u32_kernel(uint32_t *p, int64_t n) {
 // Which path serves a sort/sortperm/pairs call.
 // AUTO: one CTA for what fits it; up to eight such tiles, the merge path; learned buckets for large arrays of 64-bit
 // keys (2 bucket passes and a shared-memory finish instead of up to 8 radix
-// passes, with the on-device fallback for keys the model cannot spread);
-// radix otherwise.
+// passes, with the on-device fallback for keys the model cannot spread),
+// except the sortperm of up to 2^30 of them, whose packed radix passes are
+// faster (268M int64 keys: 14.8 ms radix, 15.7 ms learned); radix otherwise.
 constexpr int64_t LEARNED_AUTO_MIN = int64_t(1) << 25;
 static int choose_path(int op, int64_t n, int key_bytes, int vb, const ak_options &o) {
   if (key_bytes == 16) return AK_PATH_RADIX;
   if (o.path == AK_PATH_RADIX || o.path == AK_PATH_BLOCK || o.path == AK_PATH_MERGE) return o.path;
   if (o.path == AK_PATH_LEARNED) return n < (int64_t(1) << 32) ? AK_PATH_LEARNED : AK_PATH_RADIX;
-  (void)op;
   if (n <= seg_cap(key_bytes, vb)) return AK_PATH_BLOCK;
   // a few tiles: tile sort + up to three merge rounds beat the radix launches
   // (float64 100K keys 96 vs 112 us; u32 32K 57 vs 71 us)
   if (n <= 8 * int64_t(seg_cap(key_bytes, vb))) return AK_PATH_MERGE;
+  if (key_bytes == 8 && op == AK_OP_SORTPERM && n <= (int64_t(1) << 30)) return AK_PATH_RADIX;
   if (key_bytes == 8 && n >= LEARNED_AUTO_MIN && n < (int64_t(1) << 32)) return AK_PATH_LEARNED;
   return AK_PATH_RADIX;
 }

@@ -183,3 +183,16 @@ def test_auto_takes_learned_for_large_64bit_keys(ak):
     temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORT, small.size, ak.AK_I64), t.device)
     ak.ak_sort(t, temp=temp)
     assert ak.ak_last_info(temp)["path"] == ak.AK_PATH_RADIX
+
+
+def test_auto_sortperm_of_64bit_keys_takes_packed_radix(ak):
+    """AK_PATH_AUTO sortperm of 2^25 64-bit keys: the packed radix passes (faster
+    than the learned buckets for a permutation up to 2^30 keys), exact."""
+    n = 1 << 25
+    keys = synth.uniform_i64(n, seed=8)
+    t, _ = to_dev(keys)
+    temp = ak.workspace(ak.temp_bytes(ak.AK_OP_SORTPERM, n, ak.AK_I64), t.device)
+    p = ak.ak_sortperm(t, temp=temp)
+    torch.cuda.synchronize()
+    assert ak.ak_last_info(temp)["path"] == ak.AK_PATH_RADIX
+    assert np.array_equal(to_host(p, np.uint32), oracle_perm(keys, False, threads=8).astype(np.uint32))
