@@ -43,7 +43,7 @@ NOMINAL_HBM_GBS = 8000.0
 # (keys per array, bytes per launch).  Traffic grows in proportion to the keys,
 # so it is scaled to the run's n.  None whenever the digit-pass kernel has
 # changed since the counters were taken.
-NCU_TRAFFIC = (67_108_864, 1_087_983_722)
+NCU_TRAFFIC = (67_108_864, 995_233_738)
 # ncu DRAM read + write bytes of one int64 accumulate call (keys, bytes)
 ACC_NCU_TRAFFIC = (268_435_456, 6_404_700_000)
 
