@@ -191,7 +191,10 @@ ak_status ak_sort(void *d_keys, int64_t n, ak_dtype kd, ak_order order,
  * Stable sorting permutation (Sec. II-B "sortperm"): d_perm[i] is the 0-based
  * index of the key that belongs at position i.  d_keys is read only.  Indices are
  * UInt32, so n >= 2^32 returns AK_ERR_INDEX_OVERFLOW.  d_perm must not overlap
- * d_keys or d_temp.
+ * d_keys or d_temp.  For 8-byte keys (up to 2^30, default tile configuration)
+ * the radix passes over the upper 32 key bits move one 8-byte word per key,
+ * the upper half of the order-preserving key over the index, instead of the key
+ * and the index; AUTO takes that radix path for them.
  */
 ak_status ak_sortperm(const void *d_keys, uint32_t *d_perm, int64_t n, ak_dtype kd, ak_order order,
                       void *d_temp, size_t temp_bytes, ak_stream_t stream, const ak_options *opt);
