@@ -151,6 +151,35 @@ def gpu_target(torch, dev: int):
         return vis.split(",")[dev] if vis else str(dev)
 
 
+def _cpulist(text: str) -> set[int]:
+    """CPU ids of a sysfs list such as '0-71,144-215'."""
+    out = set()
+    for part in text.strip().split(","):
+        if part:
+            a, _, b = part.partition("-")
+            out.update(range(int(a), int(b or a) + 1))
+    return out
+
+
+def bind_to_gpu_node(torch, dev: int) -> dict:
+    """Keep this process on the CPUs next to the GPU (its PCI device's local
+    CPU list), so that the pinned host buffers of the end-to-end leg come from
+    the memory attached to the GPU rather than another socket's.  Leaves the
+    affinity alone when the list is missing or shares no CPU with it."""
+    try:
+        allowed = os.sched_getaffinity(0)
+        p = torch.cuda.get_device_properties(dev)
+        path = f"/sys/bus/pci/devices/{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0/local_cpulist"
+        with open(path) as f:
+            local = _cpulist(f.read())
+        use = local & allowed
+        if use and use != allowed:
+            os.sched_setaffinity(0, use)
+        return {"gpu_local_cpus": len(local), "allowed_cpus": len(allowed), "bound_cpus": len(use or allowed)}
+    except Exception as e:  # no sysfs entry or no affinity call: measure unbound
+        return {"unbound": type(e).__name__}
+
+
 def onesweep_bytes(op: str, n: int, w: int, passes: int, packed: bool = False) -> list[int]:
     """Algorithmic bytes of each digit pass (the dominant kernel) of one call,
     every pass active.  packed: a sortperm of 8-byte keys whose upper-half
@@ -386,6 +415,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    host_binding = bind_to_gpu_node(torch, dev.index)  # before any large host allocation
     n = args.n
     cfg = workload_config(n)
 
@@ -509,6 +539,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         extra["host_link_GBps"] = host_link_bandwidth(torch, dev)
+        extra["host_binding"] = host_binding
         # the call a user makes (default options: the library's own path choice), then the
         # plain radix path the device-timed value uses
         e2e = measure_e2e(args, torch, ak, lib, dev, stream, k64, k32, None, n)
@@ -563,7 +594,7 @@ def run_ours(args):
 
     cpu = None
     if world == 1 and not args.no_cpu:
-        threads = os.cpu_count() or 1
+        threads = len(os.sched_getaffinity(0)) or 1
         sample = min(n, 1 << 24)
         rate, dt = cpu_oracle_rate(k64, k32, sample, threads)
         cpu = {"value": round(rate, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
