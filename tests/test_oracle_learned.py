@@ -31,6 +31,34 @@ def test_gradient_matches_central_differences(seed):
     assert err.max() < 1e-4
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_gradient_matches_central_differences_away_from_kinks(seed):
+    """The same gradient at 1e-6 relative: on points whose 32 pre-activations
+    all lie at least 1e-2 from zero, a step of 1e-3 in any one parameter moves
+    no pre-activation across zero (it moves one by at most 1e-3 times a weight
+    or activation below 1), so the ReLU pattern is fixed.  The residual is then
+    linear in each single parameter and the loss quadratic in it, and central
+    differences are exact up to rounding.  Dead units: both sides exactly 0."""
+    p = _params(seed)
+    x = synth.u01_f64(150 + seed, 4000)
+    y = np.sort(synth.u01_f64(160 + seed, 4000))
+    c = np.sort(synth.u01_f64(170 + seed, L.N_KNOTS))
+    _, (_, a1, _, a2, _) = L.mlp_forward(p, x)
+    keep = (np.abs(a1).min(axis=1) > 1e-2) & (np.abs(a2).min(axis=1) > 1e-2)
+    assert keep.sum() >= 100
+    x, y = x[keep], y[keep]
+    _, g = L.loss_and_grad(p, x, y, c)
+    h = 1e-3
+    num = np.empty_like(g)
+    for i in range(L.N_PARAMS):
+        e = np.zeros(L.N_PARAMS)
+        e[i] = h
+        num[i] = (L.loss_and_grad(p + e, x, y, c)[0] - L.loss_and_grad(p - e, x, y, c)[0]) / (2 * h)
+    nz = g != 0
+    assert np.all(num[~nz] == 0.0)
+    assert (np.abs(num[nz] - g[nz]) / np.abs(g[nz])).max() < 1e-6
+
+
 def test_zero_output_layer_reduces_to_pl_plus_bias():
     p = _params(4)
     p[L.P_W3:L.P_B3] = 0.0
