@@ -70,3 +70,24 @@ def test_scan_checks_accept_the_oracle_and_reject_planted_mistakes():
     sw = gf.copy()
     sw[[40, 41]] = sw[[41, 40]]
     assert not bench.check_scan_f64(xf, sw)
+
+
+def test_cpu_list_parsing_and_unbound_fallback():
+    """The GPU-local CPU list of sysfs ('0-3,8,10-11'), and the binding that
+    leaves the process alone when the device has no sysfs entry."""
+    assert bench._cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench._cpulist("") == set()
+
+    class Props:
+        pci_domain_id, pci_bus_id, pci_device_id = 0x7FFF, 0xFE, 0x1F
+
+    class FakeTorch:
+        class cuda:
+            @staticmethod
+            def get_device_properties(dev):
+                return Props()
+
+    import os
+    before = os.sched_getaffinity(0)
+    assert "unbound" in bench.bind_to_gpu_node(FakeTorch, 0)
+    assert os.sched_getaffinity(0) == before
