@@ -310,3 +310,42 @@ def test_int128_binding_shapes():
         ak.key_code(torch.zeros(10, dtype=torch.int64), wide=True)
     with pytest.raises(TypeError):
         ak.key_code(torch.zeros((5, 2), dtype=torch.int32), wide=True)
+
+
+def test_workspace_is_the_same_for_every_tile_configuration(lib):
+    """A caller sizes d_temp once; AUTO, the tuner or an explicit option may then
+    pick any tile configuration (including the reduce-then-scan one with its
+    chunk counts), so the radix workspace must not depend on the choice."""
+    import paper_2507_16710_gb300 as ak
+    for kd in (ak.AK_U16, ak.AK_F32, ak.AK_I64, ak.AK_U128):
+        for op, vb in ((ak.AK_OP_SORT, 0), (ak.AK_OP_SORTPERM, 0), (ak.AK_OP_SORT_PAIRS, 4),
+                       (ak.AK_OP_SORT_PAIRS, 8), (ak.AK_OP_SORTPERM_LOWMEM, 0)):
+            for n in (1, 1000, 6145, 1 << 20, (1 << 30) + 7, 3 << 30):
+                if op in (ak.AK_OP_SORTPERM, ak.AK_OP_SORTPERM_LOWMEM) and n >= (1 << 32):
+                    continue
+                sizes = {ak.temp_bytes(op, n, kd, vb, options={"path": ak.AK_PATH_RADIX, "tile_config": tc})
+                         for tc in range(0, ak.AK_TILE_CONFIGS + 1)}
+                assert len(sizes) == 1, (kd, op, vb, n, sizes)
+
+
+def test_auto_workspace_follows_the_path_rule(lib):
+    """AK_PATH_AUTO's workspace is the one of the path it will take (host
+    only): sortperm of 8-byte keys up to 2^30 takes the packed radix passes,
+    above that the learned buckets; the sort of 2^25+ 8-byte keys takes the
+    learned buckets; 4-byte keys stay on radix."""
+    import paper_2507_16710_gb300 as ak
+    ak.ak_autotune_clear()
+    rad = {"path": ak.AK_PATH_RADIX}
+    lrn = {"path": ak.AK_PATH_LEARNED}
+    for kd in (ak.AK_I64, ak.AK_F64, ak.AK_U64):
+        for n in (1 << 25, 1 << 28, 1 << 30):
+            # the two paths' workspaces differ, so equality names the path
+            assert ak.temp_bytes(ak.AK_OP_SORTPERM, n, kd, options=rad) != \
+                ak.temp_bytes(ak.AK_OP_SORTPERM, n, kd, options=lrn)
+            assert ak.temp_bytes(ak.AK_OP_SORTPERM, n, kd) == ak.temp_bytes(ak.AK_OP_SORTPERM, n, kd, options=rad)
+            assert ak.temp_bytes(ak.AK_OP_SORT, n, kd) == ak.temp_bytes(ak.AK_OP_SORT, n, kd, options=lrn)
+        n = (1 << 30) + 7
+        assert ak.temp_bytes(ak.AK_OP_SORTPERM, n, kd) == ak.temp_bytes(ak.AK_OP_SORTPERM, n, kd, options=lrn)
+    for n in (1 << 25, 1 << 28):
+        assert ak.temp_bytes(ak.AK_OP_SORTPERM, n, ak.AK_F32) == \
+            ak.temp_bytes(ak.AK_OP_SORTPERM, n, ak.AK_F32, options=rad)
